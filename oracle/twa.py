@@ -1,0 +1,376 @@
+"""FP64 three-weight ADMM iteration over the planning factor graph
+(test infrastructure only).
+
+Factor graph (Section 3.3): one equality node per break-point variable
+x_i(s), i in [p], s = 0..eta.  Nodes s = 0 and s = eta hold the fixed start
+and goal; each carries a position factor that always sends weight infinity
+(the endpoints are constants, Section 3).  Minimizer nodes:
+
+* kinetic factor (i, s), s < eta: f = c_{i,s} |x_i(s) - x_i(s+1)|^2 with
+  c_{i,s} = C_{i,s} / (p eta) (Eq. velo_cost_pair_wise); weight rho0 always;
+* collision factor (s, i < j): f^coll_{r_i, r_j} on the four nodes
+  (i,s), (i,s+1), (j,s), (j,s+1) (Eq. f_coll_def); weight 0 or rho0;
+* wall factor (w, i, s): f^wall for wall w (Eq. wall_minimizer); 0 or rho0.
+
+One iteration is the seven steps of Appendix B, in order.  Readings where the
+text is silent or its figure is missing (the special u and back-weight rules of
+Fig. special_update_rules):
+
+* back weights (step 6): infinity at a node if any incoming weight is
+  infinity; 0 if all incoming weights are 0; rho0 otherwise;
+* u step (step 7): u += alpha (x - z) on an edge whose forward and back
+  weights are both rho0 (the scaled-dual form; identical to the printed
+  alpha/rho0 form when rho0 = 1); every other edge resets u to 0, or keeps u
+  unchanged under ``u_keep``;
+* ties inside a minimizer go to the lowest energy, then the smallest angle
+  (see ``oracle.prox``);
+* initial state: z = start for every break-point except the goal node,
+  u = 0, back weights rho0 inside and infinity at the fixed ends.
+
+Weights are kept as classes 0 (zero), 1 (rho0), 2 (infinity).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+from . import prox
+
+W0, WR, WI = 0, 1, 2
+INF = math.inf
+
+
+@dataclass
+class Problem:
+    p: int
+    eta: int
+    start: np.ndarray          # (p, 2)
+    goal: np.ndarray           # (p, 2)
+    radius: np.ndarray         # (p,)
+    cost: np.ndarray           # (p, eta) C_{i,s}
+    walls: np.ndarray          # (n_walls, 4)
+    rho0: float = 1.0
+    alpha: float = 0.1
+    u_keep: bool = False
+    cost_unnorm: bool = False
+    warm_iters: int = 0
+    warm_rho: float = 0.0
+
+    @property
+    def n_walls(self):
+        return int(self.walls.shape[0])
+
+    def c(self):
+        """Per-factor kinetic coefficients c_{i,s}, shape (p, eta)."""
+        if self.cost_unnorm:
+            return self.cost.astype(np.float64)
+        return self.cost.astype(np.float64) / (self.p * self.eta)
+
+    def rho_at(self, k):
+        """rho0 in force at iteration k (optional warm-up schedule of Section 4)."""
+        return self.warm_rho if k < self.warm_iters else self.rho0
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        cost = np.asarray(inst.cost_w, dtype=np.float64)
+        if cost.ndim == 1:
+            cost = np.repeat(cost[:, None], inst.eta, axis=1)
+        return cls(p=inst.p, eta=inst.eta, start=np.asarray(inst.start, dtype=np.float64),
+                   goal=np.asarray(inst.goal, dtype=np.float64),
+                   radius=np.asarray(inst.radius, dtype=np.float64), cost=cost,
+                   walls=np.asarray(inst.walls, dtype=np.float64).reshape(-1, 4),
+                   rho0=float(inst.rho0), alpha=float(inst.alpha), **kw)
+
+
+@dataclass
+class State:
+    z: np.ndarray              # (p, eta+1, 2)
+    u_coll: np.ndarray         # (eta, P, 4, 2) edges (i,s), (i,s+1), (j,s), (j,s+1)
+    u_kin: np.ndarray          # (eta, p, 2, 2) edges (i,s), (i,s+1)
+    u_wall: np.ndarray         # (n_walls, eta, p, 2, 2)
+    wback: np.ndarray          # (p, eta+1) back-weight class
+    k: int = 0
+
+    def copy(self):
+        return State(self.z.copy(), self.u_coll.copy(), self.u_kin.copy(), self.u_wall.copy(),
+                     self.wback.copy(), self.k)
+
+
+@dataclass
+class Info:
+    active_coll: np.ndarray    # (eta, P) bool: forward weight rho0
+    active_wall: np.ndarray    # (n_walls, eta, p) bool
+    residual: float            # max(primal, dz) of this iteration
+    primal: float              # max over weighted edges |x - z^{k+1}|_inf
+    dz: float                  # max |z^{k+1} - z^k|_inf
+    extra: dict = field(default_factory=dict)
+
+
+def pairs(p):
+    """Collision-factor pair list, lexicographic (i < j)."""
+    return np.triu_indices(p, 1)
+
+
+def initial_state(prob: Problem) -> State:
+    """z^0 = start at every break-point but the goal node; u^0 = 0; back
+    weights rho0 inside, infinity at the fixed ends (Section 4)."""
+    p, eta = prob.p, prob.eta
+    z = np.repeat(prob.start[:, None, :], eta + 1, axis=1).copy()
+    z[:, eta] = prob.goal
+    P = p * (p - 1) // 2
+    wback = np.full((p, eta + 1), WR, dtype=np.int8)
+    wback[:, 0] = WI
+    wback[:, eta] = WI
+    return State(z=z, u_coll=np.zeros((eta, P, 4, 2)), u_kin=np.zeros((eta, p, 2, 2)),
+                 u_wall=np.zeros((prob.n_walls, eta, p, 2, 2)), wback=wback, k=0)
+
+
+def _wnum(cls, rho0):
+    return 0.0 if cls == W0 else (rho0 if cls == WR else INF)
+
+
+def iterate(prob: Problem, st: State, record_edges: bool = False):
+    """One TWA iteration (Appendix B steps 1-7).  Returns (new_state, Info)."""
+    p, eta = prob.p, prob.eta
+    rho0 = prob.rho_at(st.k)
+    z = st.z
+    wb = st.wback
+    cc = prob.c()
+    iu, ju = pairs(p)
+    Rpair = prob.radius[iu] + prob.radius[ju]
+    pinned = np.zeros((p, eta + 1), dtype=bool)
+    pinned[:, 0] = True
+    pinned[:, eta] = True
+
+    num = np.zeros((p, eta + 1, 2))    # sum of rho * m over finite positive weights
+    den = np.zeros((p, eta + 1))       # sum of those weights
+    edges = []                         # (node_i, node_s, m, weight) for record_edges
+
+    # --- kinetic factors: steps 1-4 -------------------------------------
+    x_kin = np.empty_like(st.u_kin)
+    n_kin = np.empty_like(st.u_kin)
+    for s in range(eta):
+        n_kin[s, :, 0] = z[:, s] - st.u_kin[s, :, 0]
+        n_kin[s, :, 1] = z[:, s + 1] - st.u_kin[s, :, 1]
+        for i in range(p):
+            x_kin[s, i, 0], x_kin[s, i, 1] = prox.energy_prox(
+                n_kin[s, i, 0], n_kin[s, i, 1], _wnum(wb[i, s], rho0),
+                _wnum(wb[i, s + 1], rho0), cc[i, s])
+    m_kin = x_kin + st.u_kin
+    for s in range(eta):
+        for e, ss in ((0, s), (1, s + 1)):
+            num[:, ss] += rho0 * m_kin[s, :, e]
+            den[:, ss] += rho0
+            if record_edges:
+                for i in range(p):
+                    edges.append((i, ss, m_kin[s, i, e].copy(), rho0))
+
+    # --- collision factors ----------------------------------------------
+    active_coll = np.zeros((eta, iu.shape[0]), dtype=bool)
+    coll_x = []  # per s: (indices, x (nact, 4, 2))
+    for s in range(eta):
+        u = st.u_coll[s]
+        n = np.stack([z[iu, s], z[iu, s + 1], z[ju, s], z[ju, s + 1]], axis=1) - u
+        c_lo = n[:, 2] - n[:, 0]
+        c_hi = n[:, 3] - n[:, 1]
+        act = prox.dist_point_segment(np.zeros_like(c_lo), c_lo, c_hi) < Rpair
+        idx = np.nonzero(act)[0]
+        xa = np.empty((idx.shape[0], 4, 2))
+        for k, q in enumerate(idx):
+            i, j = iu[q], ju[q]
+            out = prox.coll_prox(n[q, 0], n[q, 1], n[q, 2], n[q, 3],
+                                 _wnum(wb[i, s], rho0), _wnum(wb[i, s + 1], rho0),
+                                 _wnum(wb[j, s], rho0), _wnum(wb[j, s + 1], rho0), Rpair[q])
+            assert out[4], "activity test disagrees with the minimizer's own test"
+            xa[k] = np.stack(out[:4])
+        active_coll[s] = act
+        coll_x.append((idx, xa))
+        if idx.shape[0]:
+            ma = xa + u[idx]
+            nodes_i = (iu[idx], iu[idx], ju[idx], ju[idx])
+            nodes_s = (s, s + 1, s, s + 1)
+            for e in range(4):
+                np.add.at(num, (nodes_i[e], nodes_s[e]), rho0 * ma[:, e])
+                np.add.at(den, (nodes_i[e], nodes_s[e]), rho0)
+                if record_edges:
+                    for k in range(idx.shape[0]):
+                        edges.append((int(nodes_i[e][k]), nodes_s[e], ma[k, e].copy(), rho0))
+
+    # --- wall factors ------------------------------------------------------
+    nw = prob.n_walls
+    active_wall = np.zeros((nw, eta, p), dtype=bool)
+    wall_x = {}
+    for w in range(nw):
+        xL = prob.walls[w, :2]
+        xR = prob.walls[w, 2:]
+        for s in range(eta):
+            u = st.u_wall[w, s]
+            n_lo = z[:, s] - u[:, 0]
+            n_hi = z[:, s + 1] - u[:, 1]
+            act = prox.dist_segment_segment(n_lo, n_hi, xL[None, :], xR[None, :]) < prob.radius
+            for i in np.nonzero(act)[0]:
+                x_lo, x_hi, a = prox.wall_prox(n_lo[i], n_hi[i], _wnum(wb[i, s], rho0),
+                                               _wnum(wb[i, s + 1], rho0), xL, xR, prob.radius[i])
+                assert a
+                wall_x[(w, s, i)] = (x_lo, x_hi)
+                for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):
+                    mv = xv + u[i, e]
+                    num[i, ss] += rho0 * mv
+                    den[i, ss] += rho0
+                    if record_edges:
+                        edges.append((i, ss, mv.copy(), rho0))
+            active_wall[w, s] = act
+
+    # --- step 5: consensus z ----------------------------------------------
+    z_new = np.empty_like(z)
+    pos = den > 0
+    z_new[pos] = num[pos] / den[pos][:, None]
+    # all incoming weights zero: treat them as 1, i.e. the plain mean of every
+    # incoming m.  An inactive factor returns x = n, so its m = n + u = z^k.
+    zero_nodes = (~pos) & (~pinned)
+    if np.any(zero_nodes):
+        z_new[zero_nodes] = _plain_mean_all_edges(prob, st, zero_nodes, m_kin, coll_x, wall_x)
+    z_new[:, 0] = prob.start
+    z_new[:, eta] = prob.goal
+
+    # --- step 6: back weights ---------------------------------------------
+    wb_new = np.where(pos, WR, W0).astype(np.int8)
+    wb_new[:, 0] = WI
+    wb_new[:, eta] = WI
+
+    # --- step 7: u update -------------------------------------------------
+    a = prob.alpha
+    primal = 0.0
+    new = st.copy()
+    new.z = z_new
+    new.wback = wb_new
+    new.k = st.k + 1
+
+    def upd(u_old, x, i_node, s_node, fwd_active):
+        """u for one edge family; arrays broadcast over leading dims."""
+        ok = fwd_active & (wb_new[i_node, s_node] == WR)
+        step = u_old + a * (x - z_new[i_node, s_node])
+        reset = u_old if prob.u_keep else np.zeros_like(u_old)
+        return np.where(ok[..., None], step, reset)
+
+    # kinetic: forward weight always rho0
+    for s in range(eta):
+        allp = np.arange(p)
+        for e, ss in ((0, s), (1, s + 1)):
+            new.u_kin[s, :, e] = upd(st.u_kin[s, :, e], x_kin[s, :, e], allp, np.full(p, ss),
+                                     np.ones(p, dtype=bool))
+            primal = max(primal, float(np.max(np.abs(x_kin[s, :, e] - z_new[:, ss]), initial=0.0)))
+    # collision: inactive factors have x = n and forward weight 0
+    for s in range(eta):
+        idx, xa = coll_x[s]
+        u = st.u_coll[s]
+        new.u_coll[s] = u if prob.u_keep else 0.0
+        if idx.shape[0]:
+            nodes_i = (iu[idx], iu[idx], ju[idx], ju[idx])
+            nodes_s = (s, s + 1, s, s + 1)
+            for e in range(4):
+                si = np.full(idx.shape[0], nodes_s[e])
+                new.u_coll[s][idx, e] = upd(u[idx, e], xa[:, e], nodes_i[e], si,
+                                            np.ones(idx.shape[0], dtype=bool))
+                primal = max(primal, float(np.max(np.abs(xa[:, e] - z_new[nodes_i[e], nodes_s[e]]))))
+    # walls
+    for w in range(nw):
+        for s in range(eta):
+            if not prob.u_keep:
+                new.u_wall[w, s] = 0.0
+        for (w_, s, i), (x_lo, x_hi) in wall_x.items():
+            if w_ != w:
+                continue
+            for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):
+                new.u_wall[w, s, i, e] = upd(st.u_wall[w, s, i, e][None], xv[None],
+                                             np.array([i]), np.array([ss]),
+                                             np.array([True]))[0]
+                primal = max(primal, float(np.max(np.abs(xv - z_new[i, ss]))))
+    dz = float(np.max(np.abs(z_new - z)))
+    info = Info(active_coll=active_coll, active_wall=active_wall, residual=max(primal, dz),
+                primal=primal, dz=dz)
+    if record_edges:
+        info.extra["edges"] = edges
+        info.extra["x_kin"] = x_kin
+        info.extra["coll_x"] = coll_x
+    return new, info
+
+
+def _plain_mean_all_edges(prob, st, mask, m_kin, coll_x, wall_x):
+    """Step 5's all-zero rule for the nodes in ``mask``: the plain mean of
+    every incoming m.  Only reachable without a kinetic cost term."""
+    p, eta = prob.p, prob.eta
+    iu, ju = pairs(p)
+    tot = np.zeros((p, eta + 1, 2))
+    cnt = np.zeros((p, eta + 1))
+    for s in range(eta):
+        for e, ss in ((0, s), (1, s + 1)):
+            tot[:, ss] += m_kin[s, :, e]
+            cnt[:, ss] += 1
+        # collision factors: m = x + u, with x = n for the inactive ones
+        u = st.u_coll[s]
+        m = np.stack([st.z[iu, s], st.z[iu, s + 1], st.z[ju, s], st.z[ju, s + 1]], axis=1)
+        idx, xa = coll_x[s]
+        if idx.shape[0]:
+            m[idx] = xa + u[idx]
+        for e, (ni, ss) in enumerate(((iu, s), (iu, s + 1), (ju, s), (ju, s + 1))):
+            np.add.at(tot, (ni, ss), m[:, e])
+            np.add.at(cnt, (ni, ss), 1)
+    for w in range(prob.n_walls):
+        for s in range(eta):
+            for i in range(p):
+                for e, ss in ((0, s), (1, s + 1)):
+                    xv = wall_x.get((w, s, i), (None, None))[e]
+                    mv = st.z[i, ss] if xv is None else xv + st.u_wall[w, s, i, e]
+                    tot[i, ss] += mv
+                    cnt[i, ss] += 1
+    return tot[mask] / cnt[mask][:, None]
+
+
+def solve(prob: Problem, tol: float, max_iter: int, st: State | None = None):
+    """Iterate until the residual of an iteration drops below tol (or
+    max_iter iterations).  Returns (state, iterations, last residual)."""
+    st = initial_state(prob) if st is None else st
+    res = INF
+    for it in range(max_iter):
+        st, info = iterate(prob, st)
+        res = info.residual
+        if res < tol:
+            return st, it + 1, res
+    return st, max_iter, res
+
+
+def total_cost(prob: Problem, z: np.ndarray) -> float:
+    """f^cost of Eq. velo_cost_pair_wise at the break-points z (p, eta+1, 2)."""
+    d = z[:, 1:] - z[:, :-1]
+    return float(np.sum(prob.c() * np.sum(d * d, axis=-1)))
+
+
+def min_clearance(prob: Problem, z: np.ndarray):
+    """Smallest ratio dist / (r_i + r_j) over every pair and segment, and the
+    smallest dist / r_i over every agent, segment and wall (1 = touching)."""
+    p, eta = prob.p, prob.eta
+    iu, ju = pairs(p)
+    R = prob.radius[iu] + prob.radius[ju]
+    worst = INF
+    for s in range(eta):
+        c_lo = z[ju, s] - z[iu, s]
+        c_hi = z[ju, s + 1] - z[iu, s + 1]
+        if iu.shape[0]:
+            d = prox.dist_point_segment(np.zeros_like(c_lo), c_lo, c_hi)
+            worst = min(worst, float(np.min(d / R)))
+    wworst = INF
+    for w in range(prob.n_walls):
+        for s in range(eta):
+            d = prox.dist_segment_segment(z[:, s], z[:, s + 1], prob.walls[w, None, :2],
+                                          prob.walls[w, None, 2:])
+            wworst = min(wworst, float(np.min(d / prob.radius)))
+    return worst, wworst
+
+
+def straight_lines(prob: Problem) -> np.ndarray:
+    """Constant-velocity lines from start to goal, (p, eta+1, 2)."""
+    t = np.arange(prob.eta + 1) / prob.eta
+    return prob.start[:, None, :] + t[None, :, None] * (prob.goal - prob.start)[:, None, :]
