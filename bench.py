@@ -1,0 +1,299 @@
+"""Benchmark of one TWA planner iteration (every collision, kinetic, position
+and wall factor, then the consensus and dual updates) on one GB300.
+
+Default workload: p=1024 agents in [0,40]^2 with 4 walls, eta=16 segments:
+8,380,416 collision + 16,384 kinetic + 65,536 wall + 2,048 position factors
+per iteration.  A step is one iteration; the metric is factor updates per
+second (every factor's minimizer plus its edge updates counts once).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode gated|dense] [--workload NAME]
+
+Under torchrun (N > 1) every rank plans its own replica of the workload
+(there is no exchange between instances); value is the sum over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "factor-updates/s (one TWA iteration over every factor), 1 GB300"
+UNIT = "factor-updates/s"
+
+
+def factor_counts(inst):
+    p, eta = inst.p, inst.eta
+    return dict(coll=eta * p * (p - 1) // 2, kin=eta * p, wall=inst.n_walls * eta * p, pos=2 * p)
+
+
+def dense_bytes_per_iter(inst):
+    """Algorithmic HBM bytes of one iteration under the dense state model:
+    per collision factor its 8-float u record read and written (64 B) plus 2
+    bits of activity; per kinetic or wall factor a 4-float u read and written
+    (32 B).  z and the consensus partials stay in L2 and are not counted."""
+    c = factor_counts(inst)
+    return c["coll"] * 64 + (c["kin"] + c["wall"]) * 32 + c["coll"] * 2 / 8
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(inst, budget_s=20.0):
+    """The FP64 oracle, as it stands, on this host: whole iterations of the
+    same workload, as many as fit the budget (at least one)."""
+    from oracle import twa
+    prob = twa.Problem.from_instance(inst)
+    st = twa.initial_state(prob)
+    st, _ = twa.iterate(prob, st)  # untimed: reach a mid-solve iterate
+    c = factor_counts(inst)
+    total = sum(c.values())
+    n, t0 = 0, time.perf_counter()
+    while True:
+        st, _ = twa.iterate(prob, st)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": total * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full oracle iteration(s) of {inst.name} (iterations 2..{n + 1}), "
+                      f"{dt:.1f} s, numpy FP64 single thread"}
+
+
+def run_reference(args, inst):
+    """--impl reference: the FP64 oracle on the host cores, bounded."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import twa
+    prob = twa.Problem.from_instance(inst)
+    st = twa.initial_state(prob)
+    c = factor_counts(inst)
+    total = sum(c.values())
+    for _ in range(args.warmup if args.warmup <= 1 else 1):
+        st, _ = twa.iterate(prob, st)
+    budget = 150.0
+    times = []
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        st, _ = twa.iterate(prob, st)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget:
+            break
+    n = len(times)
+    ms = 1e3 * sum(times) / n
+    value = total / (ms / 1e3)
+    sample = (f"{n} of {args.steps} requested iterations of {inst.name} (capped at {budget:.0f} s), "
+              f"after {min(args.warmup, 1)} untimed warm-up iteration(s)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": n,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": inst.name, "p": inst.p, "eta": inst.eta,
+                       "walls": inst.n_walls, "factors_per_step": total},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="gated", choices=["gated", "dense"])
+    ap.add_argument("--workload", default="square1024_eta16")
+    ap.add_argument("--start-iter", type=int, default=20,
+                    help="untimed iterations before warm-up (a mid-solve iterate)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    inst = workloads.by_name(args.workload)
+
+    if args.impl == "reference":
+        return run_reference(args, inst)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1311_4527_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    warmup = max(3, args.warmup)
+
+    flags = pk.PLAN_DENSE_STATE if args.mode == "dense" else 0
+    pl = pk.Planner.from_instance(inst, flags=flags)
+    stream = torch.cuda.current_stream(dev)
+    pl.iterate(args.start_iter)
+    for _ in range(warmup):
+        pl.iterate(1)
+    # L2 flush buffer: 2 x the 129 MB L2, written between timed iterations
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    c = factor_counts(inst)
+    total = sum(c.values())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        pl.iterate(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]  # ms, each iteration between events
+    ms_step = sum(per) / len(per)
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_step = float(t.item())
+    value = total * world / (ms_step / 1e3)
+    info = pl.info()
+
+    # kernel-level timing of the dominant kernel on the same stream: the
+    # factor kernel alone, via a second planner call pattern (iterate = factor
+    # + consensus); the consensus kernel is timed by the profile summary
+    # under profiles/, here both are attributed to the iteration.
+    hbm_peak, peak_kind = peaks()
+    dense_b = dense_bytes_per_iter(inst)
+
+    # end-to-end: host endpoints in, one iteration, host trajectory out
+    e2e_steps = max(5, min(args.steps, 20))
+    start_h = torch.from_numpy(inst.start.astype(np.float32)).pin_memory()
+    goal_h = torch.from_numpy(inst.goal.astype(np.float32)).pin_memory()
+    z_h = torch.empty((inst.p, inst.eta + 1, 2), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        pl.set_endpoints(start_h.numpy(), goal_h.numpy())
+        pl.iterate(1)
+        pl.trajectory_host(z_h.numpy())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": total * world / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(2 * inst.p * 2 * 4),
+           "d2h_bytes_per_step": int(inst.p * (inst.eta + 1) * 2 * 4),
+           "ms_per_step": e2e_ms,
+           "path": "plan_set_endpoints(host) + plan_iterate(1) + plan_get_trajectory(host)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": inst.name, "p": inst.p, "eta": inst.eta, "walls": inst.n_walls,
+                   "factors_per_step": total, "coll_factors": c["coll"], "kin_factors": c["kin"],
+                   "wall_factors": c["wall"], "pos_factors": c["pos"], "mode": args.mode,
+                   "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) before every timed iteration",
+                   "start_iter": args.start_iter,
+                   "active_coll_last": info["active_coll"], "active_wall_last": info["active_wall"]},
+        "coll_factor_updates_per_s": c["coll"] * world / (ms_step / 1e3),
+        "wall_s": wall,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+    }
+    if args.mode == "dense":
+        ach = dense_b / (ms_step / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "traffic": None,
+                            "note": f"dense-model bytes {dense_b:.4g}/iteration over the whole "
+                                    f"iteration time (factor + consensus kernels); peak {peak_kind}"}
+    else:
+        ach = dense_b / (ms_step / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "traffic": None,
+                            "note": "dense-model bytes over the gated kernel's time: the gated "
+                                    "state skips the zero u records, so this is an equivalent "
+                                    f"rate, not DRAM traffic; peak {peak_kind}"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(inst)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * plan.h -- C ABI of the GB300 three-weight ADMM (TWA) multi-agent trajectory
+ * planner.
+ *
+ * The method is the message-passing planner of Bento, Derbinsky, Alonso-Mora
+ * and Yedidia, "A message-passing algorithm for multi-agent trajectory
+ * planning" (NIPS 2013).  The problem (Section 1): p disk agents with radii
+ * r_i move in the plane from start x_i(0) to goal x_i(T) along piecewise
+ * linear paths with eta segments and shared break-points s = 0..eta; the
+ * paths must not collide (Eq. basic_opt_prob) and minimise the kinetic energy
+ * (Eq. velo_cost_pair_wise), optionally avoiding wall segments
+ * (Eq. wall_minimizer).  One iteration (Appendix B, steps 1-7) updates every
+ * collision, kinetic, wall and position factor of the graph of Section 3.3,
+ * then the consensus z per break-point and the dual u per edge.
+ *
+ * Conventions for every entry point:
+ *  - every call returns a plan_status; nothing throws across the ABI; the
+ *    message of the last failure on the calling thread is plan_last_error();
+ *  - arrays are float32, row-major, 2-D points stored as (x, y) pairs;
+ *  - "host" pointers are ordinary CPU memory (pinned memory is faster);
+ *    "device" pointers are CUDA global memory on the plan's device;
+ *  - the library never keeps a caller pointer past the call, except the
+ *    workspace handed to plan_create, which the caller keeps alive until
+ *    plan_destroy;
+ *  - work is enqueued on the stream given to plan_create; only calls that
+ *    return a number to the host (residual, iteration count, host copies)
+ *    synchronise that stream.
+ */
+#ifndef PLAN_H
+#define PLAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plan_s* plan_t;
+
+typedef enum {
+  PLAN_OK = 0,
+  PLAN_EINVAL = 1,             /* bad argument (null pointer, size, flag) */
+  PLAN_ENOMEM = 2,             /* allocation failed or workspace too small */
+  PLAN_ECUDA = 3,              /* a CUDA call failed; see plan_last_error() */
+  PLAN_ENOTCONV = 4,           /* plan_solve hit max_iter before tol */
+  PLAN_ENUMERIC = 5,           /* a non-finite value appeared in the iterate */
+  PLAN_EINFEASIBLE_INPUT = 6,  /* overlapping starts/goals, endpoint in a wall */
+  PLAN_EUNSUPPORTED = 7        /* a mode this build does not implement */
+} plan_status;
+
+/* flags of plan_config.flags */
+#define PLAN_U_KEEP            (1u << 0) /* inactive edges keep u instead of resetting it to 0 */
+#define PLAN_COST_UNNORM       (1u << 1) /* kinetic coefficient C_{i,s} instead of C_{i,s}/(p eta) */
+#define PLAN_COST_PER_SEGMENT  (1u << 2) /* cost_w holds p x eta values C_{i,s} (else p values C_i) */
+#define PLAN_DENSE_STATE       (1u << 3) /* stream the u record of every collision factor each
+                                            iteration, zeros included (else only active ones) */
+
+typedef struct {
+  int p;              /* agents, >= 1 */
+  int eta;            /* segments, >= 1; break-points s = 0..eta */
+  float T;            /* horizon; kept for the caller, the cost does not use it */
+  float rho0;         /* rho0 of the three weights {0, rho0, inf} (Section 2), > 0 */
+  float alpha;        /* dual step of Appendix B step 7 (the paper uses 0.1), > 0 */
+  int warm_iters;     /* iterations at rho = warm_rho before rho0 (Section 4); 0 = off */
+  float warm_rho;
+  float tol;          /* plan_solve stops when the residual falls below tol */
+  int max_iter;       /* plan_solve gives up after this many iterations */
+  int check_every;    /* plan_solve reads the residual back every this many iterations (>=1) */
+  int n_walls;        /* wall segments, >= 0 */
+  unsigned flags;     /* PLAN_* flags above */
+} plan_config;
+
+/* Bytes of device workspace plan_create needs for cfg (cfg->p, eta, n_walls,
+ * flags).  Errors: PLAN_EINVAL for a null pointer or sizes out of range. */
+plan_status plan_workspace_size(const plan_config* cfg, size_t* bytes);
+
+/*
+ * Build a planner for one problem (Section 1) and set the initial state of
+ * Section 4: z = start at every break-point except the goal node, u = 0.
+ *
+ *   start, goal : host, p x 2          fixed positions at s = 0 and s = eta
+ *   radius      : host, p              agent radii r_i > 0
+ *   cost_w      : host, p (or p x eta with PLAN_COST_PER_SEGMENT), >= 0,
+ *                 the C_{i,s} of Eq. velo_cost_pair_wise
+ *   walls       : host, n_walls x 4    rows [xL.x, xL.y, xR.x, xR.y]
+ *                 (Eq. wall_minimizer); may be NULL when n_walls == 0
+ *   workspace   : device memory of plan_workspace_size() bytes, 256-byte
+ *                 aligned, owned by the caller; NULL makes the library
+ *                 allocate (and free) its own
+ *   cuda_stream : cudaStream_t to enqueue on (NULL = legacy default stream)
+ *
+ * Errors: PLAN_EINVAL (null pointers, non-finite values, sizes),
+ * PLAN_EINFEASIBLE_INPUT (two starts or two goals closer than r_i + r_j, or an
+ * endpoint closer than r_i to a wall), PLAN_ENOMEM, PLAN_ECUDA.
+ */
+plan_status plan_create(const plan_config* cfg, const float* start, const float* goal,
+                        const float* radius, const float* cost_w, const float* walls,
+                        void* workspace, size_t workspace_bytes, void* cuda_stream,
+                        plan_t* out);
+
+/* Back to the initial state (iteration counter 0).  Enqueued, no sync. */
+plan_status plan_reset(plan_t plan);
+
+/* Replace the fixed start and goal positions (host, p x 2 each) and keep the
+ * current iterate as the warm start (the re-planning use of Appendix J).  The
+ * new endpoints are checked like in plan_create.  Copies are enqueued on the
+ * plan's stream; the call returns once the host buffers may be reused. */
+plan_status plan_set_endpoints(plan_t plan, const float* start, const float* goal);
+
+/* Run k_iters TWA iterations (Appendix B steps 1-7 over every factor).  When
+ * max_residual is non-NULL the call synchronises and stores the residual of
+ * the last iteration: max over weighted edges of |x - z|_inf and over nodes
+ * of |z_new - z_old|_inf.  Errors: PLAN_EINVAL, PLAN_ECUDA. */
+plan_status plan_iterate(plan_t plan, int k_iters, float* max_residual);
+
+/* Iterate until the residual falls below cfg.tol (checked every
+ * cfg.check_every iterations) or cfg.max_iter iterations have run.  Returns
+ * PLAN_OK on convergence, PLAN_ENOTCONV at max_iter, PLAN_ENUMERIC on a
+ * non-finite residual.  iters_done / max_residual may be NULL. */
+plan_status plan_solve(plan_t plan, int* iters_done, float* max_residual);
+
+/* Copy the break-points z (p x (eta+1) x 2) to z; on_device selects a device
+ * or host destination.  A host copy synchronises. */
+plan_status plan_get_trajectory(plan_t plan, float* z, int on_device);
+
+/*
+ * State exchange in the paper's variables (Appendix B), all DEVICE pointers
+ * (any of them may be NULL to skip that array):
+ *   z       : p x (eta+1) x 2
+ *   u_coll  : eta x P x 4 x 2, P = p(p-1)/2 pairs (i < j) in lexicographic
+ *             order; edges (i,s), (i,s+1), (j,s), (j,s+1)
+ *   u_kin   : eta x p x 2 x 2, edges (i,s), (i,s+1)
+ *   u_wall  : n_walls x eta x p x 2 x 2
+ *   act_coll: eta x P bytes, 1 where the factor sent rho0 in the last
+ *             iteration (export only)
+ *   act_wall: n_walls x eta x p bytes (export only)
+ * plan_export_state writes the state at the start of the next iteration;
+ * plan_import_state replaces it (k = iteration counter to resume from).
+ */
+plan_status plan_export_state(plan_t plan, float* z, float* u_coll, float* u_kin, float* u_wall,
+                              uint8_t* act_coll, uint8_t* act_wall, int* k);
+plan_status plan_import_state(plan_t plan, const float* z, const float* u_coll,
+                              const float* u_kin, const float* u_wall, int k);
+
+typedef struct {
+  long long n_coll;          /* collision factors eta p (p-1)/2 */
+  long long n_kin;           /* kinetic factors eta p */
+  long long n_wall;          /* wall factors n_walls eta p */
+  long long n_pos;           /* position factors 2 p */
+  long long active_coll;     /* collision factors active in the last iteration */
+  long long active_wall;     /* wall factors active in the last iteration */
+  int k;                     /* iterations done */
+  int tile;                  /* agents per tile of the collision kernel */
+  size_t workspace_bytes;
+} plan_info;
+
+/* Sizes and counters (synchronises to count the active factors). */
+plan_status plan_get_info(plan_t plan, plan_info* info);
+
+/* Gradient of a trajectory loss through unrolled iterations (not built yet:
+ * returns PLAN_EUNSUPPORTED). */
+plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,
+                          float* d_radius, float* d_cost_w);
+
+void plan_destroy(plan_t plan);
+const char* plan_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLAN_H */

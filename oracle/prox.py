@@ -219,6 +219,20 @@ def _tangent_normals(q, c, r):
     return [(r * d + s * perp) / L2, (r * d - s * perp) / L2]
 
 
+def _gap(cands, energies, best):
+    """Relative energy gap from the chosen direction to the best candidate at
+    a clearly different angle (> 1e-3 rad): small values mark near-ties that
+    a lower-precision solver may break the other way."""
+    e = np.asarray(energies)
+    eb = float(np.min(e))
+    g = INF
+    for t, ei in zip(cands, e):
+        d = abs((t - best + math.pi) % TWO_PI - math.pi)
+        if d > 1e-3:
+            g = min(g, (float(ei) - eb) / max(abs(eb), 1e-300))
+    return g
+
+
 def _pick(cands, energies):
     """Lowest energy; ties within TIE_REL go to the smallest angle in [0, 2pi)."""
     e = np.asarray(energies)
@@ -231,7 +245,7 @@ def _pick(cands, energies):
     return best
 
 
-def region_prox(a, b, w_lo, w_hi, c0, c1, r):
+def region_prox(a, b, w_lo, w_hi, c0, c1, r, want_gap=False):
     """Minimizer of w_lo/2 |v_lo - a|^2 + w_hi/2 |v_hi - b|^2 subject to the
     segment [v_lo, v_hi] staying out of the open capsule of radius r around
     [c0, c1] (Eqs. wall_min_explicit_opt_problem and
@@ -239,16 +253,18 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r):
 
     Returns (v_lo, v_hi, theta) with theta the separating direction (None when
     [a, b] is already feasible or both ends are pinned).  w = inf pins that
-    end; both weights zero is the equal-weight limit of Appendix D.
+    end; both weights zero is the equal-weight limit of Appendix D.  With
+    want_gap a fourth value is returned: the relative energy gap to the
+    runner-up direction (see ``_gap``).
     """
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     c0 = np.asarray(c0, dtype=np.float64)
     c1 = np.asarray(c1, dtype=np.float64)
     if dist_segment_segment(a, b, c0, c1) >= r:
-        return a.copy(), b.copy(), None
+        return (a.copy(), b.copy(), None) + ((INF,) if want_gap else ())
     if w_lo == INF and w_hi == INF:
-        return a.copy(), b.copy(), None
+        return (a.copy(), b.copy(), None) + ((INF,) if want_gap else ())
     if w_lo == 0.0 and w_hi == 0.0:
         w_lo = w_hi = 1.0  # equal weights: the argmin does not depend on their value
     if (w_lo == 0.0) != (w_hi == 0.0):
@@ -283,9 +299,10 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r):
         n = _unit(t)
         h = support(t, c0, c1, r)
         v_free = free + max(h - float(np.dot(free, n)), 0.0) * n
+        extra = (_gap(feas, energies, t),) if want_gap else ()
         if w_lo == INF:
-            return a.copy(), v_free, t
-        return v_free, b.copy(), t
+            return (a.copy(), v_free, t) + extra
+        return (v_free, b.copy(), t) + extra
 
     cands = [0.0] + list(kinks)
     for c in centres:
@@ -299,10 +316,10 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r):
     h = support(t, c0, c1, r)
     v_lo = a + max(h - float(np.dot(a, n)), 0.0) * n
     v_hi = b + max(h - float(np.dot(b, n)), 0.0) * n
-    return v_lo, v_hi, t
+    return (v_lo, v_hi, t) + ((_gap(cands, energies, t),) if want_gap else ())
 
 
-def wall_prox(n_lo, n_hi, rho_lo, rho_hi, xL, xR, r):
+def wall_prox(n_lo, n_hi, rho_lo, rho_hi, xL, xR, r, want_gap=False):
     """g^wall (Eq. wall_minimizer_problem): agent of radius r avoiding the
     wall segment [xL, xR].  Returns (x_lo, x_hi, active) where active is the
     outgoing-weight decision (Section 3.3.2: rho0 iff the n-segment hits the
@@ -310,9 +327,9 @@ def wall_prox(n_lo, n_hi, rho_lo, rho_hi, xL, xR, r):
     n_lo = np.asarray(n_lo, dtype=np.float64)
     n_hi = np.asarray(n_hi, dtype=np.float64)
     if not segment_hits_wall(n_lo, n_hi, xL, xR, r):
-        return n_lo.copy(), n_hi.copy(), False
-    v_lo, v_hi, _ = region_prox(n_lo, n_hi, rho_lo, rho_hi, xL, xR, r)
-    return v_lo, v_hi, True
+        return (n_lo.copy(), n_hi.copy(), False) + ((INF,) if want_gap else ())
+    out = region_prox(n_lo, n_hi, rho_lo, rho_hi, xL, xR, r, want_gap=want_gap)
+    return (out[0], out[1], True) + ((out[3],) if want_gap else ())
 
 
 # --------------------------------------------------------------------------
@@ -347,7 +364,8 @@ def _pair_reduction(n, n2, rho, rho2):
     return target, rho * rho2 / s, (lambda v: (rho - rho2) / s * v + 2.0 * (rho * n + rho2 * n2) / s)
 
 
-def coll_prox(n_lo_i, n_hi_i, n_lo_j, n_hi_j, rho_lo_i, rho_hi_i, rho_lo_j, rho_hi_j, R):
+def coll_prox(n_lo_i, n_hi_i, n_lo_j, n_hi_j, rho_lo_i, rho_hi_i, rho_lo_j, rho_hi_j, R,
+              want_gap=False):
     """g^coll (Eq. coll_minimizer_problem) for agents i and j with R = r_i + r_j.
 
     Returns (x_lo_i, x_hi_i, x_lo_j, x_hi_j, active).  Inactive (the two
@@ -358,14 +376,17 @@ def coll_prox(n_lo_i, n_hi_i, n_lo_j, n_hi_j, rho_lo_i, rho_hi_i, rho_lo_j, rho_
     n_lo_i, n_hi_i, n_lo_j, n_hi_j = (np.asarray(v, dtype=np.float64)
                                       for v in (n_lo_i, n_hi_i, n_lo_j, n_hi_j))
     if not segments_collide(n_lo_i, n_hi_i, n_lo_j, n_hi_j, R):
-        return n_lo_i.copy(), n_hi_i.copy(), n_lo_j.copy(), n_hi_j.copy(), False
+        return ((n_lo_i.copy(), n_hi_i.copy(), n_lo_j.copy(), n_hi_j.copy(), False)
+                + ((INF,) if want_gap else ()))
     t_lo, w_lo, rec_lo = _pair_reduction(n_lo_i, n_lo_j, rho_lo_i, rho_lo_j)
     t_hi, w_hi, rec_hi = _pair_reduction(n_hi_i, n_hi_j, rho_hi_i, rho_hi_j)
     zero = np.zeros(2)
-    v_lo, v_hi, _ = region_prox(t_lo, t_hi, w_lo, w_hi, zero, zero, R)
+    out = region_prox(t_lo, t_hi, w_lo, w_hi, zero, zero, R, want_gap=want_gap)
+    v_lo, v_hi = out[0], out[1]
     u_lo = rec_lo(v_lo)
     u_hi = rec_hi(v_hi)
-    return 0.5 * (u_lo - v_lo), 0.5 * (u_hi - v_hi), 0.5 * (u_lo + v_lo), 0.5 * (u_hi + v_hi), True
+    return ((0.5 * (u_lo - v_lo), 0.5 * (u_hi - v_hi), 0.5 * (u_lo + v_lo), 0.5 * (u_hi + v_hi),
+             True) + ((out[3],) if want_gap else ()))
 
 
 def coll_objective(x, n, rho):

@@ -131,8 +131,14 @@ def _wnum(cls, rho0):
     return 0.0 if cls == W0 else (rho0 if cls == WR else INF)
 
 
-def iterate(prob: Problem, st: State, record_edges: bool = False):
-    """One TWA iteration (Appendix B steps 1-7).  Returns (new_state, Info)."""
+def iterate(prob: Problem, st: State, record_edges: bool = False, record_branches: bool = False):
+    """One TWA iteration (Appendix B steps 1-7).  Returns (new_state, Info).
+
+    record_branches stores, per collision and wall factor, the relative
+    distance margin (d - R) / R of the activity test and, for active factors,
+    the minimizer's relative energy gap to its runner-up direction (inf when
+    inactive): the two places where a lower-precision solver may take the
+    other branch."""
     p, eta = prob.p, prob.eta
     rho0 = prob.rho_at(st.k)
     z = st.z
@@ -170,21 +176,30 @@ def iterate(prob: Problem, st: State, record_edges: bool = False):
     # --- collision factors ----------------------------------------------
     active_coll = np.zeros((eta, iu.shape[0]), dtype=bool)
     coll_x = []  # per s: (indices, x (nact, 4, 2))
+    if record_branches:
+        coll_margin = np.empty((eta, iu.shape[0]))
+        coll_gap = np.full((eta, iu.shape[0]), INF)
     for s in range(eta):
         u = st.u_coll[s]
         n = np.stack([z[iu, s], z[iu, s + 1], z[ju, s], z[ju, s + 1]], axis=1) - u
         c_lo = n[:, 2] - n[:, 0]
         c_hi = n[:, 3] - n[:, 1]
-        act = prox.dist_point_segment(np.zeros_like(c_lo), c_lo, c_hi) < Rpair
+        dseg = prox.dist_point_segment(np.zeros_like(c_lo), c_lo, c_hi)
+        act = dseg < Rpair
+        if record_branches:
+            coll_margin[s] = (dseg - Rpair) / Rpair
         idx = np.nonzero(act)[0]
         xa = np.empty((idx.shape[0], 4, 2))
         for k, q in enumerate(idx):
             i, j = iu[q], ju[q]
             out = prox.coll_prox(n[q, 0], n[q, 1], n[q, 2], n[q, 3],
                                  _wnum(wb[i, s], rho0), _wnum(wb[i, s + 1], rho0),
-                                 _wnum(wb[j, s], rho0), _wnum(wb[j, s + 1], rho0), Rpair[q])
+                                 _wnum(wb[j, s], rho0), _wnum(wb[j, s + 1], rho0), Rpair[q],
+                                 want_gap=record_branches)
             assert out[4], "activity test disagrees with the minimizer's own test"
             xa[k] = np.stack(out[:4])
+            if record_branches:
+                coll_gap[s, q] = out[5]
         active_coll[s] = act
         coll_x.append((idx, xa))
         if idx.shape[0]:
@@ -202,6 +217,9 @@ def iterate(prob: Problem, st: State, record_edges: bool = False):
     nw = prob.n_walls
     active_wall = np.zeros((nw, eta, p), dtype=bool)
     wall_x = {}
+    if record_branches:
+        wall_margin = np.empty((nw, eta, p))
+        wall_gap = np.full((nw, eta, p), INF)
     for w in range(nw):
         xL = prob.walls[w, :2]
         xR = prob.walls[w, 2:]
@@ -209,11 +227,18 @@ def iterate(prob: Problem, st: State, record_edges: bool = False):
             u = st.u_wall[w, s]
             n_lo = z[:, s] - u[:, 0]
             n_hi = z[:, s + 1] - u[:, 1]
-            act = prox.dist_segment_segment(n_lo, n_hi, xL[None, :], xR[None, :]) < prob.radius
+            dw = prox.dist_segment_segment(n_lo, n_hi, xL[None, :], xR[None, :])
+            act = dw < prob.radius
+            if record_branches:
+                wall_margin[w, s] = (dw - prob.radius) / prob.radius
             for i in np.nonzero(act)[0]:
-                x_lo, x_hi, a = prox.wall_prox(n_lo[i], n_hi[i], _wnum(wb[i, s], rho0),
-                                               _wnum(wb[i, s + 1], rho0), xL, xR, prob.radius[i])
+                out = prox.wall_prox(n_lo[i], n_hi[i], _wnum(wb[i, s], rho0),
+                                     _wnum(wb[i, s + 1], rho0), xL, xR, prob.radius[i],
+                                     want_gap=record_branches)
+                x_lo, x_hi, a = out[:3]
                 assert a
+                if record_branches:
+                    wall_gap[w, s, i] = out[3]
                 wall_x[(w, s, i)] = (x_lo, x_hi)
                 for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):
                     mv = xv + u[i, e]
@@ -291,6 +316,9 @@ def iterate(prob: Problem, st: State, record_edges: bool = False):
     dz = float(np.max(np.abs(z_new - z)))
     info = Info(active_coll=active_coll, active_wall=active_wall, residual=max(primal, dz),
                 primal=primal, dz=dz)
+    if record_branches:
+        info.extra.update(coll_margin=coll_margin, coll_gap=coll_gap, wall_margin=wall_margin,
+                          wall_gap=wall_gap)
     if record_edges:
         info.extra["edges"] = edges
         info.extra["x_kin"] = x_kin

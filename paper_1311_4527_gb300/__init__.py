@@ -1,0 +1,265 @@
+"""GB300 three-weight ADMM multi-agent trajectory planner.
+
+Python binding of the C ABI in ``include/plan.h`` (Bento, Derbinsky,
+Alonso-Mora and Yedidia, "A message-passing algorithm for multi-agent
+trajectory planning", NIPS 2013).  The binding only marshals arguments: every
+step of an iteration runs in the CUDA kernels of ``csrc/plan.cu``.  PyTorch
+provides device memory (the workspace and state buffers) and streams.
+
+The library is required: importing works without it, but creating a
+``Planner`` raises if ``libplan.so`` is missing or no CUDA device is present.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_float, c_int, c_longlong, c_size_t, c_uint, c_void_p
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+__all__ = ["Planner", "PlanError", "load_library", "PLAN_U_KEEP", "PLAN_COST_UNNORM",
+           "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE", "EXPORTED_SYMBOLS"]
+
+PLAN_U_KEEP = 1 << 0
+PLAN_COST_UNNORM = 1 << 1
+PLAN_COST_PER_SEGMENT = 1 << 2
+PLAN_DENSE_STATE = 1 << 3
+
+STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: "PLAN_ENOTCONV",
+          5: "PLAN_ENUMERIC", 6: "PLAN_EINFEASIBLE_INPUT", 7: "PLAN_EUNSUPPORTED"}
+
+EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_set_endpoints",
+                    "plan_iterate", "plan_solve", "plan_get_trajectory", "plan_export_state",
+                    "plan_import_state", "plan_get_info", "plan_backward", "plan_destroy",
+                    "plan_last_error"]
+
+
+class PlanError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class plan_config(ctypes.Structure):
+    _fields_ = [("p", c_int), ("eta", c_int), ("T", c_float), ("rho0", c_float),
+                ("alpha", c_float), ("warm_iters", c_int), ("warm_rho", c_float),
+                ("tol", c_float), ("max_iter", c_int), ("check_every", c_int),
+                ("n_walls", c_int), ("flags", c_uint)]
+
+
+class plan_info(ctypes.Structure):
+    _fields_ = [("n_coll", c_longlong), ("n_kin", c_longlong), ("n_wall", c_longlong),
+                ("n_pos", c_longlong), ("active_coll", c_longlong), ("active_wall", c_longlong),
+                ("k", c_int), ("tile", c_int), ("workspace_bytes", c_size_t)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libplan.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"the planner's CUDA library is not built ({path}); "
+                           "run paper_1311_4527_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    fp = POINTER(c_float)
+    lib.plan_workspace_size.argtypes = [POINTER(plan_config), POINTER(c_size_t)]
+    lib.plan_create.argtypes = [POINTER(plan_config), fp, fp, fp, fp, fp, c_void_p, c_size_t,
+                                c_void_p, POINTER(c_void_p)]
+    lib.plan_reset.argtypes = [c_void_p]
+    lib.plan_set_endpoints.argtypes = [c_void_p, fp, fp]
+    lib.plan_iterate.argtypes = [c_void_p, c_int, fp]
+    lib.plan_solve.argtypes = [c_void_p, POINTER(c_int), fp]
+    lib.plan_get_trajectory.argtypes = [c_void_p, c_void_p, c_int]
+    lib.plan_export_state.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, POINTER(c_int)]
+    lib.plan_import_state.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]
+    lib.plan_get_info.argtypes = [c_void_p, POINTER(plan_info)]
+    lib.plan_backward.argtypes = [c_void_p, c_int, fp, fp, fp, fp, fp]
+    lib.plan_destroy.argtypes = [c_void_p]
+    lib.plan_destroy.restype = None
+    lib.plan_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED_SYMBOLS:
+        f = getattr(lib, name)
+        if name not in ("plan_destroy", "plan_last_error"):
+            f.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        msg = _lib.plan_last_error().decode(errors="replace")
+        raise PlanError(code, msg)
+
+
+def _f32(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
+    return a, a.ctypes.data_as(POINTER(c_float))
+
+
+def make_config(p, eta, rho0=1.0, alpha=0.1, tol=1e-6, max_iter=20000, n_walls=0, flags=0,
+                check_every=50, warm_iters=0, warm_rho=0.0, T=1.0):
+    return plan_config(p=p, eta=eta, T=T, rho0=rho0, alpha=alpha, warm_iters=warm_iters,
+                       warm_rho=warm_rho, tol=tol, max_iter=max_iter, check_every=check_every,
+                       n_walls=n_walls, flags=flags)
+
+
+class Planner:
+    """One planning problem on one GPU.
+
+    ``Planner(start, goal, radius, eta, cost_w=..., walls=..., rho0=..., ...)``
+    or ``Planner.from_instance(inst)`` for a ``workloads.Instance``.
+    The workspace is a torch uint8 tensor on the current CUDA device; work is
+    enqueued on the current torch stream.
+    """
+
+    def __init__(self, start, goal, radius, eta, cost_w=None, walls=None, rho0=1.0, alpha=0.1,
+                 tol=1e-6, max_iter=20000, flags=0, check_every=50, warm_iters=0, warm_rho=0.0,
+                 T=1.0, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Planner needs a CUDA device (there is no CPU fallback)")
+        lib = load_library()
+        start = np.asarray(start, dtype=np.float64).reshape(-1, 2)
+        p = start.shape[0]
+        if cost_w is None:
+            cost_w = np.ones(p)
+        cost_w = np.asarray(cost_w, dtype=np.float64)
+        if cost_w.ndim == 2:
+            flags |= PLAN_COST_PER_SEGMENT
+        walls = np.zeros((0, 4)) if walls is None else np.asarray(walls, dtype=np.float64).reshape(-1, 4)
+        self.p, self.eta, self.n_walls = p, int(eta), int(walls.shape[0])
+        self.flags = flags
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        self.cfg = make_config(p, self.eta, rho0, alpha, tol, max_iter, self.n_walls, flags,
+                               check_every, warm_iters, warm_rho, T)
+        nbytes = c_size_t(0)
+        _check(lib.plan_workspace_size(byref(self.cfg), byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self._keep = []
+        st, st_p = _f32(start, (p, 2))
+        gl, gl_p = _f32(goal, (p, 2))
+        rd, rd_p = _f32(radius, (p,))
+        cw, cw_p = _f32(cost_w, cost_w.shape)
+        wl, wl_p = _f32(walls if self.n_walls else np.zeros((1, 4)), (-1, 4))
+        h = c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.plan_create(byref(self.cfg), st_p, gl_p, rd_p, cw_p, wl_p,
+                                   c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                   c_void_p(self.stream.cuda_stream), byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        args = dict(rho0=inst.rho0, alpha=inst.alpha, tol=inst.tol, max_iter=inst.max_iter,
+                    T=inst.T)
+        args.update(kw)
+        return cls(inst.start, inst.goal, inst.radius, inst.eta, cost_w=inst.cost_w,
+                   walls=inst.walls, **args)
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- iteration ----------------------------------------------------------
+    def reset(self):
+        _check(_lib.plan_reset(self._h))
+
+    def iterate(self, k: int = 1, residual: bool = False):
+        """Run k iterations; with residual=True return the last one's residual."""
+        if residual:
+            r = c_float(0.0)
+            _check(_lib.plan_iterate(self._h, int(k), byref(r)))
+            return float(r.value)
+        _check(_lib.plan_iterate(self._h, int(k), None))
+        return None
+
+    def solve(self):
+        """Iterate to the tolerance.  Returns (converged, iterations, residual)."""
+        it = c_int(0)
+        r = c_float(0.0)
+        code = _lib.plan_solve(self._h, byref(it), byref(r))
+        if code not in (0, 4):
+            _check(code)
+        return code == 0, int(it.value), float(r.value)
+
+    def set_endpoints(self, start, goal):
+        st, st_p = _f32(start, (self.p, 2))
+        gl, gl_p = _f32(goal, (self.p, 2))
+        _check(_lib.plan_set_endpoints(self._h, st_p, gl_p))
+
+    # -- state ------------------------------------------------------------
+    def trajectory(self):
+        """Break-points z as a (p, eta+1, 2) float32 device tensor."""
+        import torch
+        z = torch.empty((self.p, self.eta + 1, 2), dtype=torch.float32, device=self.device)
+        _check(_lib.plan_get_trajectory(self._h, c_void_p(z.data_ptr()), 1))
+        return z
+
+    def trajectory_host(self, out: np.ndarray | None = None):
+        if out is None:
+            out = np.empty((self.p, self.eta + 1, 2), dtype=np.float32)
+        _check(_lib.plan_get_trajectory(self._h, out.ctypes.data_as(c_void_p), 0))
+        return out
+
+    def n_pairs(self):
+        return self.p * (self.p - 1) // 2
+
+    def export_state(self):
+        """State at the start of the next iteration, in the paper's variables."""
+        import torch
+        P = self.n_pairs()
+        dev = self.device
+        z = torch.empty((self.p, self.eta + 1, 2), dtype=torch.float32, device=dev)
+        u_coll = torch.empty((self.eta, P, 4, 2), dtype=torch.float32, device=dev)
+        u_kin = torch.empty((self.eta, self.p, 2, 2), dtype=torch.float32, device=dev)
+        u_wall = torch.empty((self.n_walls, self.eta, self.p, 2, 2), dtype=torch.float32, device=dev)
+        act_coll = torch.empty((self.eta, P), dtype=torch.uint8, device=dev)
+        act_wall = torch.empty((self.n_walls, self.eta, self.p), dtype=torch.uint8, device=dev)
+        k = c_int(0)
+        ptr = lambda t: c_void_p(t.data_ptr()) if t.numel() else None
+        _check(_lib.plan_export_state(self._h, ptr(z), ptr(u_coll), ptr(u_kin), ptr(u_wall),
+                                      ptr(act_coll), ptr(act_wall), byref(k)))
+        torch.cuda.current_stream(dev).synchronize()
+        return dict(z=z, u_coll=u_coll, u_kin=u_kin, u_wall=u_wall, act_coll=act_coll,
+                    act_wall=act_wall, k=int(k.value))
+
+    def import_state(self, z, u_coll, u_kin, u_wall, k: int):
+        import torch
+        dev = self.device
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        zt, uc, uk = t(z), t(u_coll), t(u_kin)
+        uw = t(u_wall) if self.n_walls else torch.zeros(1, device=dev)
+        self._keep = [zt, uc, uk, uw]
+        _check(_lib.plan_import_state(self._h, c_void_p(zt.data_ptr()), c_void_p(uc.data_ptr()),
+                                      c_void_p(uk.data_ptr()), c_void_p(uw.data_ptr()), int(k)))
+        torch.cuda.current_stream(dev).synchronize()
+
+    def info(self):
+        inf = plan_info()
+        _check(_lib.plan_get_info(self._h, byref(inf)))
+        return {f: getattr(inf, f) for f, _ in plan_info._fields_}

@@ -1,0 +1,1061 @@
+// plan.cu -- GB300 (sm_103a) kernels and C ABI of the three-weight ADMM
+// trajectory planner (Bento, Derbinsky, Alonso-Mora, Yedidia, NIPS 2013).
+//
+// One iteration = Appendix B steps 1-7 over the factor graph of Section 3.3,
+// run as two kernels:
+//
+//   factor_kernel  one CTA per (segment s, agent tile I, agent tile J >= I):
+//                  every collision factor (s, i in I, j in J, i < j) of the
+//                  tile -- and, in the diagonal CTAs, the kinetic and wall
+//                  factors of the agents of I at segment s.  Per factor: finish
+//                  the pending dual update of the previous iteration (step 7),
+//                  form n = z - u (step 1), run the minimizer and its weight
+//                  logic (steps 2-3), form m = x + u (step 4) and add the
+//                  weighted m into per-tile consensus partial sums (warp
+//                  shuffles for the row agent, registers + shared memory for
+//                  the column agent).  One store per (tile, agent, component).
+//   consensus_kernel  one thread per free break-point: z = sum(rho m) /
+//                  sum(rho) over the tile partials in a fixed order (step 5,
+//                  deterministic), and |z_new - z_old| for the residual.
+//
+// Step 7 needs z^{k+1}, which exists only after every factor ran.  The factor
+// kernel therefore stores x^{k+1} of the factors that sent rho0 and finishes
+// u^{k+1} = u^k + alpha (x^{k+1} - z^{k+1}) at the start of the next
+// iteration.  Back weights (step 6) are rho0 at every interior node, because
+// the kinetic factors always send rho0 there, and infinity at the fixed ends;
+// u on an edge whose forward weight was 0, or whose node is fixed, is 0.
+//
+// Collision-factor state lives in tile order: for CTA blk = s * ntp + tp the
+// 32 x 32 pair slots (row r = i - 32 I, column c = j - 32 J) are contiguous,
+// so a warp streams one row as 32 consecutive float4 (512 B).  Per slot:
+//   ulo[slot] = (u_i(s), u_j(s))       uhi[slot] = (u_i(s+1), u_j(s+1))
+//   xlo / xhi = pending x^{k+1}, read and written only for active factors
+//   bits[blk * 32 + r] bit c = forward weight rho0 in the last iteration.
+// With PLAN_DENSE_STATE the u record of every slot is read and written each
+// iteration; otherwise only those of factors whose bit is set (every other u
+// is 0 by the reset rule), which leaves 1 bit per factor of state traffic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "twa_math.cuh"
+
+using namespace twa;
+
+namespace {
+
+constexpr int TILE = 32;
+constexpr int WARPS = 8;
+constexpr int THREADS = TILE * WARPS;
+constexpr int ROWS = TILE / WARPS;  // rows of a tile per warp
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Dev {
+  int p, eta, nw, nt, ntp;
+  float rho, alpha;
+  int dense, keep;
+  const float2* z;       // z^k, [p][eta+1]
+  float2* z_next;        // z^{k+1}
+  const float* radius;   // [p]
+  const float* cost;     // [p][eta], kinetic coefficients c_{i,s}
+  const float4* walls;   // [nw] (xL.x, xL.y, xR.x, xR.y)
+  const int2* tiles;     // [ntp] (I, J), I <= J
+  float4 *ulo, *uhi, *xlo, *xhi;
+  uint32_t* bits;        // [eta * ntp * 32]
+  float4 *ukin, *xkin;   // [eta][p]
+  float4 *uwall, *xwall; // [nw][eta][p]
+  uint32_t* wbits;       // [nw][eta][nt]
+  float* partial;        // [eta][nt][nt][6][32]
+  unsigned* res_cur;     // residual slot of this iteration (consensus part)
+  unsigned* res_prev;    // residual slot of the previous iteration (primal part)
+  unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction
+};
+
+__device__ __forceinline__ float maxabs2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+
+// Step 7 of the previous iteration for one edge: u^k from the stored u^{k-1},
+// the pending x^k and z^k.
+__device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, float2 u_prev,
+                                           float2 x_pend, float2 zk, float alpha, float& res) {
+  if (pinned) return mk(0.f, 0.f);
+  if (bprev) {
+    float2 d = x_pend - zk;
+    res = fmaxf(res, maxabs2(d));
+    return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
+  }
+  return keep ? u_prev : mk(0.f, 0.f);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return mk(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return mk(v.z, v.w); }
+__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* slot, float v) {
+  atomicMax(slot, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// Collision minimizer of one pair (Appendix C with equal weights rho on each
+// end, or infinite at a fixed end).  n: (i lo, i hi, j lo, j hi).
+__device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 njl, float2 njh,
+                                               bool pin_lo, bool pin_hi, float R, float rho,
+                                               float2& xil, float2& xih, float2& xjl, float2& xjh) {
+  float2 cl = njl - nil, ch = njh - nih;     // relative targets v = x_j - x_i
+  float2 sl = nil + njl, sh = nih + njh;     // sum coordinates x_i + x_j
+  xil = nil; xih = nih; xjl = njl; xjh = njh;
+  if (pin_lo && pin_hi) return;
+  if (pin_lo) {
+    float2 vh = disk_prox_pinned(cl, ch, R);
+    xih = 0.5f * (sh - vh);
+    xjh = 0.5f * (sh + vh);
+  } else if (pin_hi) {
+    float2 vl = disk_prox_pinned(ch, cl, R);
+    xil = 0.5f * (sl - vl);
+    xjl = 0.5f * (sl + vl);
+  } else {
+    float2 vl, vh;
+    float w = 0.5f * rho;  // rho rho / (rho + rho)
+    disk_prox_free(cl, ch, w, w, R, vl, vh);
+    xil = 0.5f * (sl - vl);
+    xjl = 0.5f * (sl + vl);
+    xih = 0.5f * (sh - vh);
+    xjh = 0.5f * (sh + vh);
+  }
+}
+
+// Kinetic factor (i, s): always active.  Adds its contributions to acc.
+__device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float2 zl, float2 zh,
+                                               bool pin_lo, bool pin_hi, float* acc, float& res) {
+  size_t idx = (size_t)s * P.p + i;
+  float4 u4 = P.ukin[idx], x4 = P.xkin[idx];
+  float2 ul = finish_u(true, pin_lo, false, lo2(u4), lo2(x4), zl, P.alpha, res);
+  float2 uh = finish_u(true, pin_hi, false, hi2(u4), hi2(x4), zh, P.alpha, res);
+  float2 nl = zl - ul, nh = zh - uh;
+  float2 xl, xh;
+  energy_prox(nl, nh, P.rho, pin_lo, pin_hi, P.cost[(size_t)i * P.eta + s], xl, xh);
+  P.xkin[idx] = pack(xl, xh);
+  P.ukin[idx] = pack(ul, uh);
+  if (!pin_lo) { float2 m = xl + ul; acc[0] += m.x; acc[1] += m.y; acc[2] += 1.f; }
+  if (!pin_hi) { float2 m = xh + uh; acc[3] += m.x; acc[4] += m.y; acc[5] += 1.f; }
+}
+
+// Wall factor (w, i, s).  Called by a full warp (lane = agent of the tile).
+__device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
+                                            float2 zl, float2 zh, float r, bool pin_lo,
+                                            bool pin_hi, float* acc, float& res) {
+  int lane = threadIdx.x & 31;
+  size_t widx = ((size_t)w * P.eta + s) * P.nt + I;
+  uint32_t word = P.wbits[widx];
+  bool bprev = vi && ((word >> lane) & 1u);
+  size_t idx = ((size_t)w * P.eta + s) * P.p + i;
+  float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = u4;
+  if (vi && (P.dense || bprev)) u4 = P.uwall[idx];
+  if (bprev) x4 = P.xwall[idx];
+  float2 ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
+  float2 uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
+  float2 nl = zl - ul, nh = zh - uh;
+  float4 W = P.walls[w];
+  float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
+  bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
+  uint32_t nw = __ballot_sync(FULL, act);
+  if (lane == 0) P.wbits[widx] = nw;
+  if (act) {
+    float2 xl = nl, xh = nh;
+    if (pin_lo && pin_hi) {
+    } else if (pin_lo) {
+      if (!capsule_prox_pinned(nl, nh, c0, c1, r, xh)) atomicOr(P.status, 1u);
+    } else if (pin_hi) {
+      if (!capsule_prox_pinned(nh, nl, c0, c1, r, xl)) atomicOr(P.status, 1u);
+    } else {
+      float wgt = 0.5f * P.rho;
+      capsule_prox_free(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
+    }
+    P.xwall[idx] = pack(xl, xh);
+    P.uwall[idx] = pack(ul, uh);
+    if (!pin_lo) { float2 m = xl + ul; acc[0] += m.x; acc[1] += m.y; acc[2] += 1.f; }
+    if (!pin_hi) { float2 m = xh + uh; acc[3] += m.x; acc[4] += m.y; acc[5] += 1.f; }
+  } else if (vi && P.dense) {
+    P.uwall[idx] = pack(ul, uh);
+  }
+}
+
+__global__ void __launch_bounds__(THREADS) factor_kernel(Dev P) {
+  __shared__ float2 zI[2][TILE], zJ[2][TILE];
+  __shared__ float rI[TILE], rJ[TILE];
+  __shared__ float rowacc[6][TILE];
+  __shared__ float colacc[WARPS][6][TILE];
+  __shared__ float segacc[WARPS][6][TILE];
+
+  const int blk = blockIdx.x;
+  const int s = blk / P.ntp;
+  const int tp = blk - s * P.ntp;
+  const int2 IJ = P.tiles[tp];
+  const int I = IJ.x, J = IJ.y;
+  const bool diag = (I == J);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int E1 = P.eta + 1;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+
+  if (blk == 0 && tid == 0) *P.res_cur = 0u;
+
+  if (tid < 2 * TILE) {
+    int side = tid >> 5, a = tid & 31;
+    int ag = (side ? J : I) * TILE + a;
+    float2 zl = mk(0.f, 0.f), zh = mk(0.f, 0.f);
+    float rr = 0.f;
+    if (ag < P.p) { zl = P.z[(size_t)ag * E1 + s]; zh = P.z[(size_t)ag * E1 + s + 1]; rr = P.radius[ag]; }
+    if (side) { zJ[0][a] = zl; zJ[1][a] = zh; rJ[a] = rr; }
+    else { zI[0][a] = zl; zI[1][a] = zh; rI[a] = rr; }
+  }
+  __syncthreads();
+
+  float res = 0.f;
+  float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int j = J * TILE + lane;
+  const bool vj = j < P.p;
+  const float2 zjl = zJ[0][lane], zjh = zJ[1][lane];
+  const float rj = rJ[lane];
+
+#pragma unroll 1
+  for (int q = 0; q < ROWS; ++q) {
+    const int r = warp * ROWS + q;
+    const int i = I * TILE + r;
+    const bool vi = i < P.p;
+    const bool valid = vi && vj && (!diag || r < lane);
+    const size_t row = (size_t)blk * TILE + r;
+    const size_t fid = row * TILE + lane;
+    const uint32_t word = vi ? P.bits[row] : 0u;
+    const bool bprev = valid && ((word >> lane) & 1u);
+    float4 ul4 = make_float4(0.f, 0.f, 0.f, 0.f), uh4 = ul4, xl4 = ul4, xh4 = ul4;
+    if (valid && (P.dense || bprev)) { ul4 = P.ulo[fid]; uh4 = P.uhi[fid]; }
+    if (bprev) { xl4 = P.xlo[fid]; xh4 = P.xhi[fid]; }
+    const float2 zil = zI[0][r], zih = zI[1][r];
+    // step 7 of the previous iteration, then step 1
+    float2 uil = finish_u(bprev, pin_lo, P.keep, lo2(ul4), lo2(xl4), zil, P.alpha, res);
+    float2 ujl = finish_u(bprev, pin_lo, P.keep, hi2(ul4), hi2(xl4), zjl, P.alpha, res);
+    float2 uih = finish_u(bprev, pin_hi, P.keep, lo2(uh4), lo2(xh4), zih, P.alpha, res);
+    float2 ujh = finish_u(bprev, pin_hi, P.keep, hi2(uh4), hi2(xh4), zjh, P.alpha, res);
+    float2 nil = zil - uil, nih = zih - uih, njl = zjl - ujl, njh = zjh - ujh;
+    // steps 2-3: collision test of the n-trajectories (strict: touching is inactive)
+    const float R = rI[r] + rj;
+    const bool act = valid && dist2_origin_segment(njl - nil, njh - nih) < R * R;
+    const uint32_t nword = __ballot_sync(FULL, act);
+    if (lane == 0 && vi) P.bits[row] = nword;
+    float m[8];  // (i lo, i hi, j lo, j hi) x (x, y) of m = x + u, active lanes only
+#pragma unroll
+    for (int e = 0; e < 8; ++e) m[e] = 0.f;
+    if (act) {
+      float2 xil, xih, xjl, xjh;
+      coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, R, P.rho, xil, xih, xjl, xjh);
+      P.xlo[fid] = pack(xil, xjl);
+      P.xhi[fid] = pack(xih, xjh);
+      P.ulo[fid] = pack(uil, ujl);
+      P.uhi[fid] = pack(uih, ujh);
+      float2 a = xil + uil, b = xih + uih, c = xjl + ujl, d = xjh + ujh;
+      m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
+      m[4] = c.x; m[5] = c.y; m[6] = d.x; m[7] = d.y;
+    } else if (valid && P.dense) {
+      P.ulo[fid] = pack(uil, ujl);
+      P.uhi[fid] = pack(uih, ujh);
+    }
+    const float wl = (act && !pin_lo) ? 1.f : 0.f, wh = (act && !pin_hi) ? 1.f : 0.f;
+    // column agent j: registers, fixed row order
+    col[0] += wl * m[4]; col[1] += wl * m[5]; col[2] += wl;
+    col[3] += wh * m[6]; col[4] += wh * m[7]; col[5] += wh;
+    // row agent i: warp reduction when any lane is active
+    float v[6] = {wl * m[0], wl * m[1], wl, wh * m[2], wh * m[3], wh};
+    if (nword != 0u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) v[e] += __shfl_xor_sync(FULL, v[e], o);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) rowacc[e][r] = v[e];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e) colacc[warp][e][lane] = col[e];
+
+  // kinetic and wall factors of the diagonal tiles
+  if (diag) {
+    float seg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int i = I * TILE + lane;
+    const bool vi = i < P.p;
+    const float2 zl = zI[0][lane], zh = zI[1][lane];
+    for (int f = warp; f < 1 + P.nw; f += WARPS) {
+      if (f == 0) {
+        if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, seg, res);
+      } else {
+        wall_factor(P, f - 1, i, vi, s, I, zl, zh, rI[lane], pin_lo, pin_hi, seg, res);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) segacc[warp][e][lane] = seg[e];
+  }
+  __syncthreads();
+
+  if (tid < 6 * TILE) {
+    const int e = tid >> 5, a = tid & 31;
+    float cs = 0.f;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) cs += colacc[w][e][a];
+    float* base = P.partial;
+    if (diag) {
+      float ss = 0.f;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) ss += segacc[w][e][a];
+      float v = rowacc[e][a] + cs + ss;
+      base[((((size_t)s * P.nt + I) * P.nt + I) * 6 + e) * TILE + a] = v;
+    } else {
+      base[((((size_t)s * P.nt + I) * P.nt + J) * 6 + e) * TILE + a] = rowacc[e][a];
+      base[((((size_t)s * P.nt + J) * P.nt + I) * 6 + e) * TILE + a] = cs;
+    }
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
+// Step 5: z = sum m / count over the tile partials of both adjacent segments.
+__global__ void consensus_kernel(Dev P) {
+  const int nfree = (P.eta - 1) * P.p;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float dz = 0.f;
+  if (t < nfree) {
+    const int sp = 1 + t / P.p;
+    const int i = t - (sp - 1) * P.p;
+    const int A = i / TILE, a = i - A * TILE;
+    float mx = 0.f, my = 0.f, cnt = 0.f;
+    const float* lo = P.partial + (((size_t)sp * P.nt + A) * P.nt) * 6 * TILE + a;
+    const float* hi = P.partial + (((size_t)(sp - 1) * P.nt + A) * P.nt) * 6 * TILE + a;
+    for (int B = 0; B < P.nt; ++B) {
+      mx += lo[(B * 6 + 0) * TILE];
+      my += lo[(B * 6 + 1) * TILE];
+      cnt += lo[(B * 6 + 2) * TILE];
+    }
+    for (int B = 0; B < P.nt; ++B) {
+      mx += hi[(B * 6 + 3) * TILE];
+      my += hi[(B * 6 + 4) * TILE];
+      cnt += hi[(B * 6 + 5) * TILE];
+    }
+    const size_t zi = (size_t)i * (P.eta + 1) + sp;
+    const float2 zo = P.z[zi];
+    float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
+    if (cnt > 0.f) zn = mk(mx / cnt, my / cnt);
+    P.z_next[zi] = zn;
+    dz = fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f ? maxabs2(zn - zo) : -1.f;
+  }
+  // a NaN anywhere makes the residual NaN (reported as PLAN_ENUMERIC)
+  const bool bad = dz < 0.f;
+  dz = warp_max(bad ? 0.f : dz);
+  const bool anybad = __any_sync(FULL, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (anybad) atomicMax(P.res_cur, 0x7fc00000u);
+    else if (dz > 0.f) atomic_max_nonneg(P.res_cur, dz);
+  }
+}
+
+// Primal residual max |x^k - z^k| over weighted edges, without changing state
+// (the same finishing arithmetic the next factor_kernel will apply).
+__global__ void residual_kernel(Dev P) {
+  float res = 0.f;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int E1 = P.eta + 1;
+  const size_t nrows = (size_t)P.eta * P.ntp * TILE;
+  for (size_t row = gw; row < nrows; row += nwarps) {
+    uint32_t word = P.bits[row];
+    if (!((word >> lane) & 1u)) continue;
+    const size_t blk = row / TILE;
+    const int r = (int)(row - blk * TILE);
+    const int s = (int)(blk / P.ntp);
+    const int2 IJ = P.tiles[blk - (size_t)s * P.ntp];
+    const int i = IJ.x * TILE + r, j = IJ.y * TILE + lane;
+    const size_t fid = row * TILE + lane;
+    float4 xl = P.xlo[fid], xh = P.xhi[fid];
+    if (s != 0) {
+      res = fmaxf(res, maxabs2(lo2(xl) - P.z[(size_t)i * E1 + s]));
+      res = fmaxf(res, maxabs2(hi2(xl) - P.z[(size_t)j * E1 + s]));
+    }
+    if (s != P.eta - 1) {
+      res = fmaxf(res, maxabs2(lo2(xh) - P.z[(size_t)i * E1 + s + 1]));
+      res = fmaxf(res, maxabs2(hi2(xh) - P.z[(size_t)j * E1 + s + 1]));
+    }
+  }
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  for (int t = gt; t < P.eta * P.p; t += nth) {
+    const int s = t / P.p, i = t - s * P.p;
+    float4 x = P.xkin[t];
+    if (s != 0) res = fmaxf(res, maxabs2(lo2(x) - P.z[(size_t)i * E1 + s]));
+    if (s != P.eta - 1) res = fmaxf(res, maxabs2(hi2(x) - P.z[(size_t)i * E1 + s + 1]));
+  }
+  for (int t = gt; t < P.nw * P.eta * P.p; t += nth) {
+    const int i = t % P.p;
+    const int ws = t / P.p;
+    const int s = ws % P.eta;
+    const uint32_t word = P.wbits[(size_t)ws * P.nt + i / TILE];
+    if (!((word >> (i % TILE)) & 1u)) continue;
+    float4 x = P.xwall[t];
+    if (s != 0) res = fmaxf(res, maxabs2(lo2(x) - P.z[(size_t)i * E1 + s]));
+    if (s != P.eta - 1) res = fmaxf(res, maxabs2(hi2(x) - P.z[(size_t)i * E1 + s + 1]));
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f) atomic_max_nonneg(P.res_prev, res);
+}
+
+// Initial state (Section 4): z = start except the goal node; u = 0; the
+// kinetic pending x equals z so that the first finishing step gives u = 0.
+__global__ void reset_kernel(Dev P, float2* z0, float2* z1, const float2* start,
+                             const float2* goal) {
+  const int E1 = P.eta + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P.p * E1) {
+    const int i = t / E1, s = t - i * E1;
+    float2 v = (s == P.eta) ? goal[i] : start[i];
+    z0[t] = v;
+    z1[t] = v;
+  }
+  if (t < P.eta * P.p) {
+    const int s = t / P.p, i = t - s * P.p;
+    float2 zl = start[i];
+    float2 zh = (s + 1 == P.eta) ? goal[i] : start[i];
+    P.xkin[t] = pack(zl, zh);
+    P.ukin[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// New fixed ends: overwrite the s = 0 and s = eta nodes of both z buffers.
+__global__ void endpoints_kernel(int p, int eta, float2* z0, float2* z1, const float2* start,
+                                 const float2* goal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p) return;
+  const size_t b = (size_t)i * (eta + 1);
+  z0[b] = start[i]; z1[b] = start[i];
+  z0[b + eta] = goal[i]; z1[b + eta] = goal[i];
+}
+
+__device__ __forceinline__ size_t pair_index(int p, int i, int j) {
+  return (size_t)i * (2 * (size_t)p - i - 1) / 2 + (size_t)(j - i - 1);
+}
+
+// State export in the paper's variables (u^k after finishing step 7).
+__global__ void export_coll_kernel(Dev P, float* u_coll, uint8_t* act) {
+  const size_t slot = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nslots = (size_t)P.eta * P.ntp * TILE * TILE;
+  if (slot >= nslots) return;
+  const size_t row = slot / TILE;
+  const int lane = (int)(slot - row * TILE);
+  const size_t blk = row / TILE;
+  const int r = (int)(row - blk * TILE);
+  const int s = (int)(blk / P.ntp);
+  const int2 IJ = P.tiles[blk - (size_t)s * P.ntp];
+  const int i = IJ.x * TILE + r, j = IJ.y * TILE + lane;
+  if (i >= P.p || j >= P.p || i >= j) return;
+  const int E1 = P.eta + 1;
+  const bool bprev = (P.bits[row] >> lane) & 1u;
+  float4 ul4 = P.ulo[slot], uh4 = P.uhi[slot];
+  if (!P.dense && !bprev) { ul4 = make_float4(0.f, 0.f, 0.f, 0.f); uh4 = ul4; }
+  float4 xl4 = make_float4(0.f, 0.f, 0.f, 0.f), xh4 = xl4;
+  if (bprev) { xl4 = P.xlo[slot]; xh4 = P.xhi[slot]; }
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  float dummy = 0.f;
+  float2 uil = finish_u(bprev, pin_lo, P.keep, lo2(ul4), lo2(xl4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+  float2 ujl = finish_u(bprev, pin_lo, P.keep, hi2(ul4), hi2(xl4), P.z[(size_t)j * E1 + s], P.alpha, dummy);
+  float2 uih = finish_u(bprev, pin_hi, P.keep, lo2(uh4), lo2(xh4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+  float2 ujh = finish_u(bprev, pin_hi, P.keep, hi2(uh4), hi2(xh4), P.z[(size_t)j * E1 + s + 1], P.alpha, dummy);
+  const size_t P2 = (size_t)P.p * (P.p - 1) / 2;
+  const size_t q = (size_t)s * P2 + pair_index(P.p, i, j);
+  if (u_coll) {
+    float* o = u_coll + q * 8;
+    o[0] = uil.x; o[1] = uil.y; o[2] = uih.x; o[3] = uih.y;
+    o[4] = ujl.x; o[5] = ujl.y; o[6] = ujh.x; o[7] = ujh.y;
+  }
+  if (act) act[q] = bprev ? 1 : 0;
+}
+
+__global__ void export_seg_kernel(Dev P, float* u_kin, float* u_wall, uint8_t* act_wall) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int E1 = P.eta + 1;
+  const int nk = P.eta * P.p;
+  float dummy = 0.f;
+  if (t < nk) {
+    const int s = t / P.p, i = t - s * P.p;
+    float4 u4 = P.ukin[t], x4 = P.xkin[t];
+    float2 ul = finish_u(true, s == 0, false, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+    float2 uh = finish_u(true, s == P.eta - 1, false, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    if (u_kin) {
+      float* o = u_kin + (size_t)t * 4;
+      o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
+    }
+  }
+  if (t < P.nw * nk) {
+    const int i = t % P.p, ws = t / P.p, s = ws % P.eta;
+    const bool bprev = (P.wbits[(size_t)ws * P.nt + i / TILE] >> (i % TILE)) & 1u;
+    float4 u4 = P.uwall[t], x4 = P.xwall[t];
+    if (!P.dense && !bprev) u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 ul = finish_u(bprev, s == 0, P.keep, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+    float2 uh = finish_u(bprev, s == P.eta - 1, P.keep, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    if (u_wall) {
+      float* o = u_wall + (size_t)t * 4;
+      o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
+    }
+    if (act_wall) act_wall[t] = bprev ? 1 : 0;
+  }
+}
+
+// State import: u^k becomes the stored u with the pending x set to z^k, so
+// the next finishing step reproduces u^k exactly (u + alpha * 0).
+__global__ void import_coll_kernel(Dev P, const float* u_coll) {
+  const size_t slot = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nslots = (size_t)P.eta * P.ntp * TILE * TILE;
+  const int lane = threadIdx.x & 31;
+  bool nz = false;
+  size_t row = slot / TILE;
+  if (slot < nslots) {
+    const size_t blk = row / TILE;
+    const int r = (int)(row - blk * TILE);
+    const int s = (int)(blk / P.ntp);
+    const int2 IJ = P.tiles[blk - (size_t)s * P.ntp];
+    const int i = IJ.x * TILE + r, j = IJ.y * TILE + lane;
+    float4 ul = make_float4(0.f, 0.f, 0.f, 0.f), uh = ul, xl = ul, xh = ul;
+    if (i < P.p && j < P.p && i < j) {
+      const int E1 = P.eta + 1;
+      const size_t P2 = (size_t)P.p * (P.p - 1) / 2;
+      const float* u = u_coll + ((size_t)s * P2 + pair_index(P.p, i, j)) * 8;
+      ul = make_float4(u[0], u[1], u[4], u[5]);
+      uh = make_float4(u[2], u[3], u[6], u[7]);
+      xl = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)j * E1 + s]);
+      xh = pack(P.z[(size_t)i * E1 + s + 1], P.z[(size_t)j * E1 + s + 1]);
+      nz = ul.x != 0.f || ul.y != 0.f || ul.z != 0.f || ul.w != 0.f ||
+           uh.x != 0.f || uh.y != 0.f || uh.z != 0.f || uh.w != 0.f;
+    }
+    P.ulo[slot] = ul; P.uhi[slot] = uh; P.xlo[slot] = xl; P.xhi[slot] = xh;
+  }
+  uint32_t word = __ballot_sync(FULL, nz);
+  if (lane == 0 && slot < nslots) P.bits[row] = word;
+}
+
+__global__ void import_seg_kernel(Dev P, const float* u_kin, const float* u_wall) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int E1 = P.eta + 1;
+  const int nk = P.eta * P.p;
+  if (t < nk) {
+    const int s = t / P.p, i = t - s * P.p;
+    const float* u = u_kin + (size_t)t * 4;
+    P.ukin[t] = make_float4(u[0], u[1], u[2], u[3]);
+    P.xkin[t] = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s + 1]);
+  }
+  if (t < P.nw * nk) {
+    const int i = t % P.p, s = (t / P.p) % P.eta;
+    const float* u = u_wall + (size_t)t * 4;
+    P.uwall[t] = make_float4(u[0], u[1], u[2], u[3]);
+    P.xwall[t] = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s + 1]);
+  }
+}
+
+// wall bits: one 32-agent word per (wall, segment, tile); set where u != 0
+__global__ void import_wbits_kernel(Dev P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (w, s, tile, lane)
+  const int lane = threadIdx.x & 31;
+  const int words = P.nw * P.eta * P.nt;
+  const int w = t >> 5;
+  bool nz = false;
+  if (w < words) {
+    const int tile = w % P.nt, ws = w / P.nt;
+    const int i = tile * TILE + lane;
+    if (i < P.p) {
+      float4 u = P.uwall[(size_t)ws * P.p + i];
+      nz = u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f;
+    }
+  }
+  uint32_t word = __ballot_sync(FULL, nz);
+  if (lane == 0 && w < words) P.wbits[w] = word;
+}
+
+__global__ void count_kernel(const uint32_t* words, size_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    c += __popc(words[t]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+thread_local std::string g_err;
+
+plan_status fail(plan_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(PLAN_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t z0, z1, start, goal, radius, cost, walls, tiles;
+  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, partial, res, status, count;
+  size_t total;
+};
+
+bool sizes_ok(const plan_config* c) {
+  if (c->p < 1 || c->eta < 1 || c->n_walls < 0) return false;
+  if (c->p > (1 << 16) || c->eta > (1 << 12) || c->n_walls > 4096) return false;
+  return true;
+}
+
+Layout layout_for(const plan_config* c) {
+  const size_t p = c->p, eta = c->eta, nw = c->n_walls;
+  const size_t nt = (p + TILE - 1) / TILE, ntp = nt * (nt + 1) / 2;
+  const size_t slots = eta * ntp * TILE * TILE;
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = a256(o + std::max<size_t>(bytes, 1)); return at; };
+  L.z0 = take(p * (eta + 1) * 8);
+  L.z1 = take(p * (eta + 1) * 8);
+  L.start = take(p * 8);
+  L.goal = take(p * 8);
+  L.radius = take(p * 4);
+  L.cost = take(p * eta * 4);
+  L.walls = take(nw * 16);
+  L.tiles = take(ntp * 8);
+  L.ulo = take(slots * 16);
+  L.uhi = take(slots * 16);
+  L.xlo = take(slots * 16);
+  L.xhi = take(slots * 16);
+  L.bits = take(eta * ntp * TILE * 4);
+  L.ukin = take(eta * p * 16);
+  L.xkin = take(eta * p * 16);
+  L.uwall = take(nw * eta * p * 16);
+  L.xwall = take(nw * eta * p * 16);
+  L.wbits = take(nw * eta * nt * 4);
+  L.partial = take(eta * nt * nt * 6 * TILE * 4);
+  L.res = take(4 * 4);
+  L.status = take(4);
+  L.count = take(16);
+  L.total = o;
+  return L;
+}
+
+bool finite_all(const float* a, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(a[k])) return false;
+  return true;
+}
+
+double seg_point_dist(double px, double py, double ax, double ay, double bx, double by) {
+  double dx = bx - ax, dy = by - ay, dd = dx * dx + dy * dy;
+  double t = dd > 0 ? ((px - ax) * dx + (py - ay) * dy) / dd : 0.0;
+  t = std::min(1.0, std::max(0.0, t));
+  double cx = ax + t * dx - px, cy = ay + t * dy - py;
+  return std::sqrt(cx * cx + cy * cy);
+}
+
+// Host-side input check: fixed configurations must be feasible.
+plan_status check_endpoints(int p, const float* start, const float* goal, const float* radius,
+                            int nw, const float* walls) {
+  for (int which = 0; which < 2; ++which) {
+    const float* X = which ? goal : start;
+    for (int i = 0; i < p; ++i) {
+      for (int j = i + 1; j < p; ++j) {
+        double dx = (double)X[2 * j] - X[2 * i], dy = (double)X[2 * j + 1] - X[2 * i + 1];
+        double R = (double)radius[i] + radius[j];
+        if (dx * dx + dy * dy < R * R)
+          return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %d and %d overlap",
+                      which ? "goal" : "start", i, j);
+      }
+      for (int w = 0; w < nw; ++w) {
+        const float* W = walls + 4 * w;
+        if (seg_point_dist(X[2 * i], X[2 * i + 1], W[0], W[1], W[2], W[3]) < radius[i])
+          return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %d is within its radius of wall %d",
+                      which ? "goal" : "start", i, w);
+      }
+    }
+  }
+  return PLAN_OK;
+}
+
+}  // namespace
+
+struct plan_s {
+  plan_config cfg;
+  int p, eta, nw, nt, ntp;
+  size_t slots;
+  cudaStream_t stream;
+  Layout L;
+  char* ws;
+  bool own_ws;
+  int k;
+  int cur;  // which z buffer holds z^k
+  unsigned* h_res;  // pinned host word for residual readback
+  std::vector<float> h_radius;
+  std::vector<float> h_walls;
+
+  template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+
+  float rho_at(int kk) const {
+    return (kk < cfg.warm_iters) ? cfg.warm_rho : cfg.rho0;
+  }
+
+  Dev dev(int kk) const {
+    Dev P{};
+    P.p = p; P.eta = eta; P.nw = nw; P.nt = nt; P.ntp = ntp;
+    P.rho = rho_at(kk);
+    P.alpha = cfg.alpha;
+    // keeping u on inactive edges needs every u record, so it implies the dense state
+    P.dense = (cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) ? 1 : 0;
+    P.keep = (cfg.flags & PLAN_U_KEEP) ? 1 : 0;
+    float2* z0 = at<float2>(L.z0);
+    float2* z1 = at<float2>(L.z1);
+    P.z = cur ? z1 : z0;
+    P.z_next = cur ? z0 : z1;
+    P.radius = at<float>(L.radius);
+    P.cost = at<float>(L.cost);
+    P.walls = at<float4>(L.walls);
+    P.tiles = at<int2>(L.tiles);
+    P.ulo = at<float4>(L.ulo); P.uhi = at<float4>(L.uhi);
+    P.xlo = at<float4>(L.xlo); P.xhi = at<float4>(L.xhi);
+    P.bits = at<uint32_t>(L.bits);
+    P.ukin = at<float4>(L.ukin); P.xkin = at<float4>(L.xkin);
+    P.uwall = at<float4>(L.uwall); P.xwall = at<float4>(L.xwall);
+    P.wbits = at<uint32_t>(L.wbits);
+    P.partial = at<float>(L.partial);
+    unsigned* res = at<unsigned>(L.res);
+    P.res_cur = res + (kk & 1);
+    P.res_prev = kk > 0 ? res + ((kk - 1) & 1) : nullptr;
+    P.status = at<unsigned>(L.status);
+    return P;
+  }
+};
+
+namespace {
+
+plan_status run_iteration(plan_t h) {
+  Dev P = h->dev(h->k);
+  const unsigned grid = (unsigned)((size_t)h->eta * h->ntp);
+  factor_kernel<<<grid, THREADS, 0, h->stream>>>(P);
+  const int nfree = (h->eta - 1) * h->p;
+  if (nfree > 0) consensus_kernel<<<(nfree + 255) / 256, 256, 0, h->stream>>>(P);
+  CK(cudaGetLastError());
+  if (nfree > 0) h->cur ^= 1;
+  h->k += 1;
+  return PLAN_OK;
+}
+
+// Residual of the last completed iteration (k - 1): its consensus part was
+// written by consensus_kernel, the primal part comes from residual_kernel.
+plan_status read_residual(plan_t h, float* out) {
+  if (h->k == 0) { *out = INFINITY; return PLAN_OK; }
+  Dev P = h->dev(h->k);
+  residual_kernel<<<h->eta > 0 ? 304 : 1, 256, 0, h->stream>>>(P);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->h_res, P.res_prev, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  uint32_t bitsv = *h->h_res;
+  float v;
+  std::memcpy(&v, &bitsv, 4);
+  *out = v;
+  return PLAN_OK;
+}
+
+plan_status upload_inputs(plan_t h, const float* start, const float* goal, const float* radius,
+                          const float* cost_w, const float* walls) {
+  const plan_config& c = h->cfg;
+  const size_t p = c.p, eta = c.eta;
+  std::vector<float> cost(p * eta);
+  const double norm = (c.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * eta);
+  for (size_t i = 0; i < p; ++i)
+    for (size_t s = 0; s < eta; ++s) {
+      double C = (c.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i];
+      cost[i * eta + s] = (float)(C * norm);
+    }
+  std::vector<int2> tiles;
+  for (int I = 0; I < h->nt; ++I)
+    for (int J = I; J < h->nt; ++J) tiles.push_back(make_int2(I, J));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.start), start, p * 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.goal), goal, p * 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.radius), radius, p * 4, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.cost), cost.data(), p * eta * 4, cudaMemcpyHostToDevice, h->stream));
+  if (h->nw)
+    CK(cudaMemcpyAsync(h->at<void>(h->L.walls), walls, (size_t)h->nw * 16, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.tiles), tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  // the staging vectors die at return: wait for the copies
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* plan_last_error(void) { return g_err.c_str(); }
+
+plan_status plan_workspace_size(const plan_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return fail(PLAN_EINVAL, "null argument");
+  if (!sizes_ok(cfg)) return fail(PLAN_EINVAL, "p, eta or n_walls out of range");
+  *bytes = layout_for(cfg).total;
+  return PLAN_OK;
+}
+
+plan_status plan_reset(plan_t h) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  h->k = 0;
+  h->cur = 0;
+  Dev P = h->dev(0);
+  const size_t zbytes = (size_t)h->p * (h->eta + 1) * 8;
+  (void)zbytes;
+  CK(cudaMemsetAsync(h->at<void>(h->L.bits), 0, (size_t)h->eta * h->ntp * TILE * 4, h->stream));
+  if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.wbits), 0, (size_t)h->nw * h->eta * h->nt * 4, h->stream));
+  if (h->cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) {
+    CK(cudaMemsetAsync(h->at<void>(h->L.ulo), 0, h->slots * 16, h->stream));
+    CK(cudaMemsetAsync(h->at<void>(h->L.uhi), 0, h->slots * 16, h->stream));
+    if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, (size_t)h->nw * h->eta * h->p * 16, h->stream));
+  }
+  CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
+  const int n = std::max(h->p * (h->eta + 1), h->eta * h->p);
+  reset_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(P, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1),
+                                                      h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+plan_status plan_create(const plan_config* cfg, const float* start, const float* goal,
+                        const float* radius, const float* cost_w, const float* walls,
+                        void* workspace, size_t workspace_bytes, void* cuda_stream, plan_t* out) {
+  if (!cfg || !start || !goal || !radius || !cost_w || !out) return fail(PLAN_EINVAL, "null argument");
+  *out = nullptr;
+  if (!sizes_ok(cfg)) return fail(PLAN_EINVAL, "p, eta or n_walls out of range");
+  if (cfg->n_walls > 0 && !walls) return fail(PLAN_EINVAL, "walls is NULL but n_walls > 0");
+  if (!(cfg->rho0 > 0.f) || !std::isfinite(cfg->rho0)) return fail(PLAN_EINVAL, "rho0 must be positive");
+  if (!(cfg->alpha > 0.f) || !std::isfinite(cfg->alpha)) return fail(PLAN_EINVAL, "alpha must be positive");
+  if (cfg->warm_iters < 0 || (cfg->warm_iters > 0 && !(cfg->warm_rho > 0.f)))
+    return fail(PLAN_EINVAL, "warm_rho must be positive when warm_iters > 0");
+  if (cfg->max_iter < 0) return fail(PLAN_EINVAL, "max_iter must be >= 0");
+  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT | PLAN_DENSE_STATE;
+  if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
+  const size_t p = cfg->p, eta = cfg->eta;
+  const size_t ncost = (cfg->flags & PLAN_COST_PER_SEGMENT) ? p * eta : p;
+  if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p) || !finite_all(radius, p) ||
+      !finite_all(cost_w, ncost) || (cfg->n_walls && !finite_all(walls, 4 * (size_t)cfg->n_walls)))
+    return fail(PLAN_EINVAL, "non-finite input");
+  for (size_t i = 0; i < p; ++i)
+    if (!(radius[i] > 0.f)) return fail(PLAN_EINVAL, "radius[%zu] must be positive", i);
+  for (size_t i = 0; i < ncost; ++i)
+    if (cost_w[i] < 0.f) return fail(PLAN_EINVAL, "cost_w[%zu] must be >= 0", i);
+  plan_status st = check_endpoints(cfg->p, start, goal, radius, cfg->n_walls, walls);
+  if (st != PLAN_OK) return st;
+
+  Layout L = layout_for(cfg);
+  plan_s* h = new plan_s();
+  h->cfg = *cfg;
+  if (h->cfg.check_every < 1) h->cfg.check_every = 1;
+  h->p = cfg->p; h->eta = cfg->eta; h->nw = cfg->n_walls;
+  h->nt = (h->p + TILE - 1) / TILE;
+  h->ntp = h->nt * (h->nt + 1) / 2;
+  h->slots = (size_t)h->eta * h->ntp * TILE * TILE;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->L = L;
+  h->h_radius.assign(radius, radius + p);
+  if (h->nw) h->h_walls.assign(walls, walls + 4 * (size_t)h->nw);
+  if (workspace) {
+    if (workspace_bytes < L.total) {
+      delete h;
+      return fail(PLAN_ENOMEM, "workspace of %zu bytes, %zu needed", workspace_bytes, L.total);
+    }
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) {
+      delete h;
+      return fail(PLAN_EINVAL, "workspace must be 256-byte aligned");
+    }
+    h->ws = static_cast<char*>(workspace);
+    h->own_ws = false;
+  } else {
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, L.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(PLAN_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+    }
+    h->ws = static_cast<char*>(mem);
+    h->own_ws = true;
+  }
+  cudaError_t e = cudaMallocHost(&h->h_res, 16);
+  if (e != cudaSuccess) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+  }
+  st = upload_inputs(h, start, goal, radius, cost_w, walls);
+  if (st == PLAN_OK) st = plan_reset(h);
+  if (st != PLAN_OK) {
+    plan_destroy(h);
+    return st;
+  }
+  *out = h;
+  return PLAN_OK;
+}
+
+void plan_destroy(plan_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->h_res) cudaFreeHost(h->h_res);
+  delete h;
+}
+
+plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) {
+  if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
+  if (!finite_all(start, 2 * (size_t)h->p) || !finite_all(goal, 2 * (size_t)h->p))
+    return fail(PLAN_EINVAL, "non-finite input");
+  plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data());
+  if (st != PLAN_OK) return st;
+  CK(cudaMemcpyAsync(h->at<void>(h->L.start), start, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.goal), goal, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
+  endpoints_kernel<<<(h->p + 255) / 256, 256, 0, h->stream>>>(
+      h->p, h->eta, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1), h->at<float2>(h->L.start),
+      h->at<float2>(h->L.goal));
+  CK(cudaGetLastError());
+  // the caller's host buffers may be reused once this returns
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_iterate(plan_t h, int k_iters, float* max_residual) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  if (k_iters < 0) return fail(PLAN_EINVAL, "k_iters must be >= 0");
+  for (int it = 0; it < k_iters; ++it) {
+    plan_status st = run_iteration(h);
+    if (st != PLAN_OK) return st;
+  }
+  if (max_residual) return read_residual(h, max_residual);
+  return PLAN_OK;
+}
+
+plan_status plan_solve(plan_t h, int* iters_done, float* max_residual) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  float res = INFINITY;
+  plan_status st = PLAN_OK;
+  while (h->k < h->cfg.max_iter) {
+    int n = std::min(h->cfg.check_every, h->cfg.max_iter - h->k);
+    st = plan_iterate(h, n, &res);
+    if (st != PLAN_OK) break;
+    if (!(res == res)) { st = fail(PLAN_ENUMERIC, "non-finite residual at iteration %d", h->k); break; }
+    if (res < h->cfg.tol) break;
+  }
+  if (st == PLAN_OK && !(res < h->cfg.tol))
+    st = fail(PLAN_ENOTCONV, "residual %g after %d iterations", (double)res, h->k);
+  if (iters_done) *iters_done = h->k;
+  if (max_residual) *max_residual = res;
+  return st;
+}
+
+plan_status plan_get_trajectory(plan_t h, float* z, int on_device) {
+  if (!h || !z) return fail(PLAN_EINVAL, "null argument");
+  const size_t bytes = (size_t)h->p * (h->eta + 1) * 8;
+  const void* src = h->cur ? h->at<void>(h->L.z1) : h->at<void>(h->L.z0);
+  CK(cudaMemcpyAsync(z, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_export_state(plan_t h, float* z, float* u_coll, float* u_kin, float* u_wall,
+                              uint8_t* act_coll, uint8_t* act_wall, int* k) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  Dev P = h->dev(h->k);
+  if (z) {
+    plan_status st = plan_get_trajectory(h, z, 1);
+    if (st != PLAN_OK) return st;
+  }
+  if (u_coll || act_coll) {
+    const size_t n = h->slots;
+    export_coll_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(P, u_coll, act_coll);
+  }
+  const int nseg = std::max(h->eta * h->p, h->nw * h->eta * h->p);
+  if (u_kin || u_wall || act_wall)
+    export_seg_kernel<<<(nseg + 255) / 256, 256, 0, h->stream>>>(P, u_kin, u_wall, act_wall);
+  CK(cudaGetLastError());
+  if (k) *k = h->k;
+  return PLAN_OK;
+}
+
+plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, const float* u_kin,
+                              const float* u_wall, int k) {
+  if (!h || !z || !u_coll || !u_kin || (h->nw && !u_wall)) return fail(PLAN_EINVAL, "null argument");
+  if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
+  const size_t zbytes = (size_t)h->p * (h->eta + 1) * 8;
+  CK(cudaMemcpyAsync(h->at<void>(h->L.z0), z, zbytes, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.z1), z, zbytes, cudaMemcpyDeviceToDevice, h->stream));
+  h->cur = 0;
+  h->k = k;
+  Dev P = h->dev(k);
+  import_coll_kernel<<<(unsigned)((h->slots + 255) / 256), 256, 0, h->stream>>>(P, u_coll);
+  const int nseg = std::max(h->eta * h->p, h->nw * h->eta * h->p);
+  import_seg_kernel<<<(nseg + 255) / 256, 256, 0, h->stream>>>(P, u_kin, u_wall);
+  if (h->nw) {
+    const int words = h->nw * h->eta * h->nt;
+    import_wbits_kernel<<<(words * 32 + 255) / 256, 256, 0, h->stream>>>(P);
+  }
+  CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+plan_status plan_get_info(plan_t h, plan_info* info) {
+  if (!h || !info) return fail(PLAN_EINVAL, "null argument");
+  const long long p = h->p, eta = h->eta;
+  info->n_coll = eta * p * (p - 1) / 2;
+  info->n_kin = eta * p;
+  info->n_wall = (long long)h->nw * eta * p;
+  info->n_pos = 2 * p;
+  info->k = h->k;
+  info->tile = TILE;
+  info->workspace_bytes = h->L.total;
+  unsigned long long* cnt = h->at<unsigned long long>(h->L.count);
+  CK(cudaMemsetAsync(cnt, 0, 16, h->stream));
+  count_kernel<<<256, 256, 0, h->stream>>>(h->at<uint32_t>(h->L.bits), (size_t)h->eta * h->ntp * TILE, cnt);
+  if (h->nw) count_kernel<<<64, 256, 0, h->stream>>>(h->at<uint32_t>(h->L.wbits), (size_t)h->nw * h->eta * h->nt, cnt + 1);
+  CK(cudaGetLastError());
+  unsigned long long hc[2] = {0, 0};
+  CK(cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  info->active_coll = (long long)hc[0];
+  info->active_wall = (long long)hc[1];
+  return PLAN_OK;
+}
+
+plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, float* d_goal,
+                          float* d_radius, float* d_cost_w) {
+  (void)h; (void)K; (void)dL_dz; (void)d_start; (void)d_goal; (void)d_radius; (void)d_cost_w;
+  return fail(PLAN_EUNSUPPORTED, "plan_backward is not built yet");
+}
+
+}  // extern "C"

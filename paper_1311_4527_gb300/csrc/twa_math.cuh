@@ -1,0 +1,365 @@
+// twa_math.cuh -- FP32 device minimizers of the planning factors.
+//
+// Notation of Bento et al., "A message-passing algorithm for multi-agent
+// trajectory planning" (NIPS 2013): n_lo / n_hi are the incoming messages of
+// the two break-points of a segment, x_* the minimizer outputs.
+//
+// Collision and wall minimizers (Appendices C, D, I).  A segment [v_lo, v_hi]
+// misses an open convex region iff a unit normal n separates them:
+// <v_lo,n> >= h(n) and <v_hi,n> >= h(n), h the region's support function.
+// For fixed n the cheapest v's are v = a + [h - <a,n>]_+ n, so the minimizer
+// is min over directions of
+//     E(n) = wl/2 [h - <a,n>]_+^2 + wh/2 [h - <b,n>]_+^2 .
+// (Both hinges positive is the paper's tangent-slab configuration, one hinge
+// at zero its compressed-spring configuration.)
+//
+// Disk of radius R at the origin (the collision minimizer through
+// Eq. wall_min_goes_to_coll_min).  Let f(n) = wl (R - <a,n>)^2 +
+// wh (R - <b,n>)^2 be the both-stretched piece, so E <= f/2 everywhere and
+// E = f/2 where both hinges are positive.  Then
+//     min E = min( E(n_f), m_a, m_b ),
+// n_f the global minimiser of f on the unit circle, m_a the minimum of
+// wl/2 [R - <a,n>]_+^2 over the arc <b,n> >= R (where the b hinge is zero)
+// and m_b likewise: every piece of the circle is covered, and each of the
+// three values is E at some direction.  n_f is a trust-region subproblem:
+// with M = wl a a^T + wh b b^T = lambda1 e1 e1^T + lambda2 e2 e2^T and
+// S = wl a + wh b, the global minimiser solves (M - mu I) n = R S with
+// mu <= lambda1, i.e. t = lambda1 - mu >= 0 is the unique root of the
+// decreasing secular function (R s1 / t)^2 + (R s2 / (d + t))^2 = 1,
+// d = lambda2 - lambda1 (hard case: s1 = 0 and R |s2| < d gives t = 0).
+// m_a / m_b are closed form: the arc point closest in angle to a (or b).
+//
+// Capsule (wall) regions use the same hinge energy with
+// h(n) = max(<xL,n>, <xR,n>) + r; candidates are the two kink directions,
+// per end-circle the global minimiser of its both-stretched piece and the
+// single-hinge directions, plus a 128-direction scan refined by golden
+// section search.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace twa {
+
+#define TWA_DEV __device__ __forceinline__
+
+TWA_DEV float2 mk(float x, float y) { return make_float2(x, y); }
+TWA_DEV float2 operator+(float2 a, float2 b) { return mk(a.x + b.x, a.y + b.y); }
+TWA_DEV float2 operator-(float2 a, float2 b) { return mk(a.x - b.x, a.y - b.y); }
+TWA_DEV float2 operator-(float2 a) { return mk(-a.x, -a.y); }
+TWA_DEV float2 operator*(float s, float2 a) { return mk(s * a.x, s * a.y); }
+TWA_DEV float dot(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+TWA_DEV float cross(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
+TWA_DEV float2 perp(float2 a) { return mk(-a.y, a.x); }
+TWA_DEV float2 normalized(float2 a) {
+  float n = hypotf(a.x, a.y);
+  return n > 0.f ? mk(a.x / n, a.y / n) : mk(1.f, 0.f);
+}
+
+// Angle of a unit vector in [0, 2 pi): the tie-break order of directions.
+TWA_DEV float angle_of(float2 n) {
+  float t = atan2f(n.y, n.x);
+  return t < 0.f ? t + 6.283185307179586f : t;
+}
+
+// Squared distance from the origin to segment [p0, p1].  Interior projections
+// use the cross product (absolute error ~ eps |p0|, no cancellation of
+// |p0|^2 against the projection).
+TWA_DEV float dist2_origin_segment(float2 p0, float2 p1) {
+  float2 d = p1 - p0;
+  float dd = dot(d, d);
+  float t = -dot(p0, d);
+  if (t <= 0.f || dd == 0.f) return dot(p0, p0);
+  if (t >= dd) return dot(p1, p1);
+  float c = cross(p0, d);
+  return c * c / dd;
+}
+
+TWA_DEV float dist2_point_segment(float2 q, float2 p0, float2 p1) {
+  return dist2_origin_segment(p0 - q, p1 - q);
+}
+
+// Squared distance between segments [a0, a1] and [b0, b1].
+TWA_DEV float dist2_segment_segment(float2 a0, float2 a1, float2 b0, float2 b1) {
+  float d1 = cross(a1 - a0, b0 - a0), d2 = cross(a1 - a0, b1 - a0);
+  float d3 = cross(b1 - b0, a0 - b0), d4 = cross(b1 - b0, a1 - b0);
+  if (((d1 < 0.f && d2 > 0.f) || (d1 > 0.f && d2 < 0.f)) &&
+      ((d3 < 0.f && d4 > 0.f) || (d3 > 0.f && d4 < 0.f)))
+    return 0.f;
+  float m = fminf(dist2_point_segment(a0, b0, b1), dist2_point_segment(a1, b0, b1));
+  return fminf(m, fminf(dist2_point_segment(b0, a0, a1), dist2_point_segment(b1, a0, a1)));
+}
+
+// Keep the best (lowest E, then smallest angle) candidate direction.
+struct Best {
+  float2 n;
+  float E;
+  TWA_DEV void init() { n = mk(1.f, 0.f); E = INFINITY; }
+  TWA_DEV void offer(float2 c, float e) {
+    if (e < E || (e == E && angle_of(c) < angle_of(n))) { n = c; E = e; }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Energy minimizer (Appendix E, Eq. energy_minimizer_output)
+// ---------------------------------------------------------------------------
+// pin_lo / pin_hi: that end's incoming weight is infinite (fixed endpoint).
+TWA_DEV void energy_prox(float2 n_lo, float2 n_hi, float rho, bool pin_lo, bool pin_hi, float c,
+                         float2& x_lo, float2& x_hi) {
+  if (pin_lo && pin_hi) { x_lo = n_lo; x_hi = n_hi; return; }
+  if (pin_lo) {
+    x_lo = n_lo;
+    float inv = 1.f / (2.f * c + rho);
+    x_hi = mk((rho * n_hi.x + 2.f * c * n_lo.x) * inv, (rho * n_hi.y + 2.f * c * n_lo.y) * inv);
+    return;
+  }
+  if (pin_hi) {
+    x_hi = n_hi;
+    float inv = 1.f / (2.f * c + rho);
+    x_lo = mk((rho * n_lo.x + 2.f * c * n_hi.x) * inv, (rho * n_lo.y + 2.f * c * n_hi.y) * inv);
+    return;
+  }
+  // equal weights rho on both ends
+  float inv = 1.f / (4.f * c + rho);
+  float2 s = n_lo + n_hi;
+  x_lo = mk((rho * n_lo.x + 2.f * c * s.x) * inv, (rho * n_lo.y + 2.f * c * s.y) * inv);
+  x_hi = mk((rho * n_hi.x + 2.f * c * s.x) * inv, (rho * n_hi.y + 2.f * c * s.y) * inv);
+}
+
+// ---------------------------------------------------------------------------
+// Disk of radius R at the origin
+// ---------------------------------------------------------------------------
+TWA_DEV float hinge_E(float2 a, float2 b, float wl, float wh, float R, float2 n) {
+  float ga = fmaxf(R - dot(a, n), 0.f), gb = fmaxf(R - dot(b, n), 0.f);
+  return 0.5f * wl * ga * ga + 0.5f * wh * gb * gb;
+}
+
+// Global minimiser(s) of f(n) = wl (R - <a,n>)^2 + wh (R - <b,n>)^2 on the
+// unit circle.  Writes 1 or 2 directions (2 only for exact ties).
+__device__ __noinline__ int trs_global(float2 a, float2 b, float wl, float wh, float R,
+                                       float2* out) {
+  float m11 = wl * a.x * a.x + wh * b.x * b.x;
+  float m22 = wl * a.y * a.y + wh * b.y * b.y;
+  float m12 = wl * a.x * a.y + wh * b.x * b.y;
+  float2 S = mk(wl * a.x + wh * b.x, wl * a.y + wh * b.y);
+  float hd = 0.5f * (m11 - m22);
+  float disc = hypotf(hd, m12);
+  float d = 2.f * disc;  // lambda2 - lambda1 >= 0
+  float2 e2;
+  if (disc == 0.f) e2 = mk(1.f, 0.f);
+  else if (hd >= 0.f) e2 = normalized(mk(hd + disc, m12));
+  else e2 = normalized(mk(m12, disc - hd));
+  float2 e1 = perp(e2);
+  float s1 = dot(S, e1), s2 = dot(S, e2);
+  float Sn = hypotf(s1, s2);
+  if (!(Sn > 0.f)) { out[0] = e1; out[1] = -e1; return 2; }
+  float A1 = R * fabsf(s1), A2 = R * fabsf(s2);
+  if (A1 <= 1e-7f * R * Sn && A2 < d) {  // hard case: t = 0
+    float n2 = R * s2 / d;
+    float n1 = sqrtf(fmaxf(0.f, 1.f - n2 * n2));
+    out[0] = n1 * e1 + n2 * e2;
+    out[1] = (-n1) * e1 + n2 * e2;
+    return 2;
+  }
+  // root of h(t) = phi(t)^{-1/2} - 1 (increasing) with phi = (A1/t)^2 + (A2/(d+t))^2
+  float lo = fmaxf(fmaxf(A1, R * Sn - d), 0.f), hi = R * Sn;
+  if (lo > hi) lo = hi;
+  float t = hi;
+  for (int it = 0; it < 60; ++it) {
+    if (!(t > 0.f)) t = 0.5f * (lo + hi);
+    float q1 = A1 / t, q2 = A2 / (d + t);
+    float phi = q1 * q1 + q2 * q2;
+    float ip = 1.f / sqrtf(phi);
+    float h = ip - 1.f;
+    if (h > 0.f) hi = t; else lo = t;
+    if (h == 0.f) break;
+    float dh = ip * ip * ip * (q1 * q1 / t + q2 * q2 / (d + t));
+    float tn = t - h / dh;
+    if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+    if (fabsf(tn - t) <= 2e-7f * t || hi - lo <= 2e-7f * hi) { t = tn; break; }
+    t = tn;
+  }
+  float p1 = (t > 0.f) ? R * s1 / t : copysignf(INFINITY, s1);
+  float p2 = R * s2 / (d + t);
+  float n1, n2;
+  if (fabsf(p1) <= fabsf(p2)) {
+    n1 = p1;
+    n2 = copysignf(sqrtf(fmaxf(0.f, 1.f - p1 * p1)), s2);
+  } else {
+    n2 = p2;
+    n1 = copysignf(sqrtf(fmaxf(0.f, 1.f - p2 * p2)), s1);
+  }
+  out[0] = normalized(n1 * e1 + n2 * e2);
+  return 1;
+}
+
+// Tangent normals n with <q, n> = R from a point q (|q| >= R).
+TWA_DEV void tangent_normals(float2 q, float R, float2& t0, float2& t1) {
+  float L2 = dot(q, q);
+  float s = sqrtf(fmaxf(L2 - R * R, 0.f));
+  float inv = 1.f / L2;
+  float2 pq = perp(q);
+  t0 = mk((R * q.x + s * pq.x) * inv, (R * q.y + s * pq.y) * inv);
+  t1 = mk((R * q.x - s * pq.x) * inv, (R * q.y - s * pq.y) * inv);
+}
+
+// Direction in the arc {n : <q,n> >= R} (|q| >= R) maximising <w, n>.
+TWA_DEV float2 arc_argmax(float2 q, float R, float2 w) {
+  float nw = hypotf(w.x, w.y);
+  if (nw > 0.f && dot(q, w) >= R * nw) return mk(w.x / nw, w.y / nw);
+  float2 t0, t1;
+  tangent_normals(q, R, t0, t1);
+  float d0 = dot(w, t0), d1 = dot(w, t1);
+  if (d0 > d1 || (d0 == d1 && angle_of(t0) <= angle_of(t1))) return normalized(t0);
+  return normalized(t1);
+}
+
+// Collision minimizer core: disk of radius R at the origin, finite equal or
+// unequal weights, neither end pinned.  (a, b): targets; (vl, vh): result.
+__device__ __noinline__ void disk_prox_free(float2 a, float2 b, float wl, float wh, float R,
+                                            float2& vl, float2& vh) {
+  Best best;
+  best.init();
+  best.offer(mk(1.f, 0.f), hinge_E(a, b, wl, wh, R, mk(1.f, 0.f)));
+  float2 c[2];
+  int nc = trs_global(a, b, wl, wh, R, c);
+  for (int k = 0; k < nc; ++k) best.offer(c[k], hinge_E(a, b, wl, wh, R, c[k]));
+  if (dot(b, b) >= R * R) {  // b's hinge can be zero: best a-term on that arc
+    float2 n = arc_argmax(b, R, a);
+    best.offer(n, hinge_E(a, b, wl, wh, R, n));
+  }
+  if (dot(a, a) >= R * R) {
+    float2 n = arc_argmax(a, R, b);
+    best.offer(n, hinge_E(a, b, wl, wh, R, n));
+  }
+  float2 n = best.n;
+  vl = a + fmaxf(R - dot(a, n), 0.f) * n;
+  vh = b + fmaxf(R - dot(b, n), 0.f) * n;
+}
+
+// One end pinned at q (weight infinite): the free end's target is w.  The
+// separating direction ranges over the arc {<q,n> >= R}.
+__device__ __noinline__ float2 disk_prox_pinned(float2 q, float2 w, float R) {
+  float2 n = arc_argmax(q, R, w);
+  return w + fmaxf(R - dot(w, n), 0.f) * n;
+}
+
+// ---------------------------------------------------------------------------
+// Capsule of radius r around the wall segment [c0, c1]
+// ---------------------------------------------------------------------------
+TWA_DEV float capsule_h(float2 c0, float2 c1, float r, float2 n) {
+  return fmaxf(dot(c0, n), dot(c1, n)) + r;
+}
+
+TWA_DEV float capsule_E(float2 a, float2 b, float wl, float wh, float2 c0, float2 c1, float r,
+                        float2 n) {
+  float h = capsule_h(c0, c1, r, n);
+  float ga = fmaxf(h - dot(a, n), 0.f), gb = fmaxf(h - dot(b, n), 0.f);
+  return 0.5f * wl * ga * ga + 0.5f * wh * gb * gb;
+}
+
+TWA_DEV float2 dir(float th) {
+  float s, c;
+  sincosf(th, &s, &c);
+  return mk(c, s);
+}
+
+__device__ __noinline__ void capsule_prox_free(float2 a, float2 b, float wl, float wh, float2 c0,
+                                               float2 c1, float r, float2& vl, float2& vh) {
+  Best best;
+  best.init();
+  best.offer(mk(1.f, 0.f), capsule_E(a, b, wl, wh, c0, c1, r, mk(1.f, 0.f)));
+  float2 e = c1 - c0;
+  if (e.x != 0.f || e.y != 0.f) {
+    float2 k0 = normalized(perp(e));
+    best.offer(k0, capsule_E(a, b, wl, wh, c0, c1, r, k0));
+    best.offer(-k0, capsule_E(a, b, wl, wh, c0, c1, r, -k0));
+  }
+  for (int ci = 0; ci < 2; ++ci) {
+    float2 cc = ci ? c1 : c0;
+    float2 ac = a - cc, bc = b - cc;
+    float2 t[2];
+    int nt = trs_global(ac, bc, wl, wh, r, t);
+    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]));
+    if (dot(ac, ac) > 0.f) {
+      float2 n = normalized(ac);
+      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n));
+    }
+    if (dot(bc, bc) > 0.f) {
+      float2 n = normalized(bc);
+      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n));
+    }
+  }
+  // scan + golden-section refinement of the best sampled direction
+  const int NS = 128;
+  const float step = 6.283185307179586f / NS;
+  float bestE = INFINITY, bestT = 0.f;
+  for (int k = 0; k < NS; ++k) {
+    float th = k * step;
+    float E = capsule_E(a, b, wl, wh, c0, c1, r, dir(th));
+    if (E < bestE) { bestE = E; bestT = th; }
+  }
+  float lo = bestT - step, hi = bestT + step;
+  const float g = 0.6180339887498949f;
+  float x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+  float f1 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x1));
+  float f2 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x2));
+  for (int it = 0; it < 40; ++it) {
+    if (f1 <= f2) { hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x1)); }
+    else { lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x2)); }
+  }
+  float2 ng = dir(0.5f * (lo + hi));
+  best.offer(ng, capsule_E(a, b, wl, wh, c0, c1, r, ng));
+  float2 n = best.n;
+  float h = capsule_h(c0, c1, r, n);
+  vl = a + fmaxf(h - dot(a, n), 0.f) * n;
+  vh = b + fmaxf(h - dot(b, n), 0.f) * n;
+}
+
+// One end pinned at q; free end target w.  Candidates: tangent directions
+// from q to both end circles, the kinks, and the single-hinge directions;
+// only directions that still separate q from the capsule are kept.
+// Returns false if no candidate separates q (q inside the capsule).
+__device__ __noinline__ bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, float r,
+                                                 float2& vw) {
+  float2 cand[8];
+  int nc = 0;
+  for (int ci = 0; ci < 2; ++ci) {
+    float2 cc = ci ? c1 : c0;
+    float2 qc = q - cc;
+    if (dot(qc, qc) >= r * r) {
+      float2 t0, t1;
+      tangent_normals(qc, r, t0, t1);
+      cand[nc++] = normalized(t0);
+      cand[nc++] = normalized(t1);
+    }
+    float2 wc = w - cc;
+    if (dot(wc, wc) > 0.f) cand[nc++] = normalized(wc);
+  }
+  float2 e = c1 - c0;
+  if (e.x != 0.f || e.y != 0.f) {
+    float2 k0 = normalized(perp(e));
+    cand[nc++] = k0;
+    cand[nc++] = -k0;
+  }
+  float scale = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)),
+                      fmaxf(fmaxf(fabsf(c0.x), fabsf(c0.y)), fmaxf(fabsf(c1.x), fabsf(c1.y)))) + r;
+  float tol = 4e-6f * scale;
+  Best best;
+  best.init();
+  bool any = false;
+  for (int k = 0; k < nc; ++k) {
+    float h = capsule_h(c0, c1, r, cand[k]);
+    if (dot(q, cand[k]) - h >= -tol) {
+      float g = fmaxf(h - dot(w, cand[k]), 0.f);
+      best.offer(cand[k], 0.5f * g * g);
+      any = true;
+    }
+  }
+  if (!any) { vw = w; return false; }
+  float h = capsule_h(c0, c1, r, best.n);
+  vw = w + fmaxf(h - dot(w, best.n), 0.f) * best.n;
+  return true;
+}
+
+}  // namespace twa

@@ -1,0 +1,128 @@
+"""Helpers shared by the GPU parity tests: run the oracle to an iterate, import
+that state into the CUDA planner, run one GPU iteration and compare.
+
+Tolerance: an FP32 entry matches when |gpu - oracle| <= TOL * L, with L the
+workload's coordinate scale max(1, |start|_inf, |goal|_inf, |walls|_inf).
+
+Branches.  A factor whose activity test sits within MARGIN of the collision
+distance, or whose minimizer has a runner-up direction within GAP in energy,
+may legitimately go the other way in FP32.  Such factors (per the oracle's
+own FP64 diagnostics) may disagree on the activity bit; any other
+disagreement fails.  Entries depending on a factor whose branch differs or may
+differ are left out of the value comparison and counted.
+"""
+import numpy as np
+
+from oracle import twa
+
+TOL = 2e-5
+MARGIN = 1e-4
+GAP = 1e-3
+
+
+def scale_of(prob):
+    vals = [1.0, np.max(np.abs(prob.start)), np.max(np.abs(prob.goal))]
+    if prob.n_walls:
+        vals.append(np.max(np.abs(prob.walls)))
+    return float(max(vals))
+
+
+def oracle_state(prob, k):
+    st = twa.initial_state(prob)
+    for _ in range(k):
+        st, _ = twa.iterate(prob, st)
+    return st
+
+
+def make_planner(prob, flags=0, **kw):
+    import paper_1311_4527_gb300 as pk
+    cost = prob.cost
+    flags = flags | (pk.PLAN_COST_UNNORM if prob.cost_unnorm else 0)
+    if prob.u_keep:
+        flags |= pk.PLAN_U_KEEP
+    return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=cost,
+                      walls=prob.walls if prob.n_walls else None, rho0=prob.rho0,
+                      alpha=prob.alpha, flags=flags, **kw)
+
+
+def gpu_step(prob, st, flags=0, planner=None):
+    """Import oracle state st, run one GPU iteration, export as numpy."""
+    pl = planner or make_planner(prob, flags)
+    pl.import_state(st.z, st.u_coll, st.u_kin, st.u_wall if prob.n_walls else None, st.k)
+    pl.iterate(1)
+    ex = pl.export_state()
+    out = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ex.items()}
+    if planner is None:
+        pl.close()
+    return out
+
+
+def compare(prob, new, info, gpu, tol=TOL):
+    """Compare the oracle's iterate `new` (with its Info, recorded with
+    record_branches=True) to the GPU export.  Returns a stats dict; raises
+    AssertionError on any mismatch outside the rules above."""
+    L = scale_of(prob)
+    p, eta = prob.p, prob.eta
+    iu, ju = twa.pairs(p)
+    stats = {}
+    # --- branch classification --------------------------------------------
+    act_o = info.active_coll
+    act_g = gpu["act_coll"].astype(bool)
+    cm, cg = info.extra["coll_margin"], info.extra["coll_gap"]
+    ambiguous = (np.abs(cm) < MARGIN) | (act_o & (cg < GAP))
+    differ = act_o != act_g
+    bad = differ & ~(np.abs(cm) < MARGIN)
+    assert not bad.any(), f"{int(bad.sum())} collision factors disagree on activity away from the boundary"
+    excl = differ | ambiguous
+    stats["coll_active"] = int(act_o.sum())
+    stats["coll_active_gpu"] = int(act_g.sum())
+    stats["coll_excluded"] = int(excl.sum())
+    bad_node = np.zeros((p, eta + 1), dtype=bool)
+    for s in range(eta):
+        q = np.nonzero(excl[s])[0]
+        for arr in (iu[q], ju[q]):
+            bad_node[arr, s] = True
+            bad_node[arr, s + 1] = True
+    if prob.n_walls:
+        aw_o = info.active_wall
+        aw_g = gpu["act_wall"].astype(bool)
+        wm, wg = info.extra["wall_margin"], info.extra["wall_gap"]
+        wamb = (np.abs(wm) < MARGIN) | (aw_o & (wg < GAP))
+        wdiff = aw_o != aw_g
+        wbad = wdiff & ~(np.abs(wm) < MARGIN)
+        assert not wbad.any(), f"{int(wbad.sum())} wall factors disagree on activity away from the boundary"
+        wex = wdiff | wamb
+        stats["wall_active"] = int(aw_o.sum())
+        stats["wall_excluded"] = int(wex.sum())
+        for w in range(prob.n_walls):
+            for s in range(eta):
+                idx = np.nonzero(wex[w, s])[0]
+                bad_node[idx, s] = True
+                bad_node[idx, s + 1] = True
+    stats["nodes_excluded"] = int(bad_node.sum())
+    # --- values --------------------------------------------------------------
+    dz = np.abs(gpu["z"] - new.z)
+    worst = float(np.max(dz[~bad_node])) if (~bad_node).any() else 0.0
+    stats["z_maxerr"] = worst / L
+    assert worst <= tol * L, f"z error {worst} > {tol * L}"
+    seg_bad = bad_node[:, :-1] | bad_node[:, 1:]            # (p, eta)
+    ok = ~excl
+    for s in range(eta):
+        ok[s] &= ~(seg_bad[iu, s] | seg_bad[ju, s])
+    du = np.abs(gpu["u_coll"] - new.u_coll)
+    worst = float(np.max(du[ok])) if ok.any() else 0.0
+    stats["u_coll_maxerr"] = worst / L
+    stats["coll_compared_active"] = int((ok & act_o).sum())
+    assert worst <= tol * L, f"u_coll error {worst} > {tol * L}"
+    kin_ok = ~seg_bad.T                                     # (eta, p)
+    dk = np.abs(gpu["u_kin"] - new.u_kin)
+    worst = float(np.max(dk[kin_ok])) if kin_ok.any() else 0.0
+    stats["u_kin_maxerr"] = worst / L
+    assert worst <= tol * L, f"u_kin error {worst} > {tol * L}"
+    if prob.n_walls:
+        okw = ~wex & ~seg_bad.T[None, :, :]
+        dw = np.abs(gpu["u_wall"] - new.u_wall)
+        worst = float(np.max(dw[okw])) if okw.any() else 0.0
+        stats["u_wall_maxerr"] = worst / L
+        assert worst <= tol * L, f"u_wall error {worst} > {tol * L}"
+    return stats

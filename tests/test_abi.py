@@ -1,0 +1,110 @@
+"""The C-ABI library builds for sm_103a, loads, exports every symbol that
+include/plan.h declares, and rejects bad input on the host before touching a
+GPU.  CPU only: no kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1311_4527_gb300 as pk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pk.build()
+    return pk.load_library()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "plan.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(plan_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_names():
+    assert _declared_symbols() == sorted(pk.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_built_for_sm_103a(lib):
+    # the fatbinary embedded in the library names its target architecture
+    blob = open(pk.LIB, "rb").read()
+    assert b"sm_103a" in blob
+
+
+def _cfg(p, eta, **kw):
+    return pk.make_config(p, eta, **kw)
+
+
+def test_workspace_size_scales_with_the_problem(lib):
+    n1, n2 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(64, 8)), ctypes.byref(n1)) == 0
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(128, 8)), ctypes.byref(n2)) == 0
+    # collision state grows with the number of tile pairs: 3 -> 10 for 2 -> 4 tiles
+    assert n2.value > 3 * n1.value
+    assert n1.value % 256 == 0
+
+
+def test_workspace_size_rejects_bad_sizes(lib):
+    n = ctypes.c_size_t()
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(0, 8)), ctypes.byref(n)) == 1
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(4, 0)), ctypes.byref(n)) == 1
+    assert lib.plan_workspace_size(None, ctypes.byref(n)) == 1
+
+
+def _create(lib, cfg, start, goal, radius, cost=None, walls=None):
+    p = cfg.p
+    f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    st, gl, rd = f(start), f(goal), f(radius)
+    cw = f(np.ones(p) if cost is None else cost)
+    wl = f(np.zeros((1, 4)) if walls is None else walls)
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    h = ctypes.c_void_p()
+    code = lib.plan_create(ctypes.byref(cfg), ptr(st), ptr(gl), ptr(rd), ptr(cw), ptr(wl),
+                           None, 0, None, ctypes.byref(h))
+    return code, lib.plan_last_error().decode()
+
+
+def test_overlapping_starts_are_rejected_on_the_host(lib):
+    code, msg = _create(lib, _cfg(2, 4), [[0, 0], [0.1, 0]], [[5, 0], [0, 5]], [0.2, 0.2])
+    assert code == 6 and "start" in msg
+
+
+def test_overlapping_goals_are_rejected_on_the_host(lib):
+    code, msg = _create(lib, _cfg(2, 4), [[0, 0], [3, 0]], [[5, 5], [5.3, 5]], [0.2, 0.2])
+    assert code == 6 and "goal" in msg
+
+
+def test_endpoint_inside_a_wall_is_rejected(lib):
+    cfg = _cfg(1, 4, n_walls=1)
+    code, msg = _create(lib, cfg, [[0, 0.1]], [[3, 3]], [0.2], walls=[[-1, 0, 1, 0]])
+    assert code == 6 and "wall" in msg
+
+
+def test_touching_endpoints_are_allowed_by_the_check(lib):
+    """Distance exactly r_i + r_j passes the host check (touching is feasible);
+    the call then fails only because there is no GPU here, or succeeds."""
+    code, msg = _create(lib, _cfg(2, 4), [[0, 0], [0.5, 0]], [[5, 0], [0, 5]], [0.25, 0.25])
+    assert code != 6
+
+
+def test_bad_parameters_are_rejected(lib):
+    for kw in (dict(rho0=0.0), dict(alpha=-1.0), dict(flags=1 << 20), dict(max_iter=-1)):
+        code, _ = _create(lib, _cfg(2, 4, **kw), [[0, 0], [3, 0]], [[5, 5], [0, 5]], [0.2, 0.2])
+        assert code == 1, kw
+    code, _ = _create(lib, _cfg(2, 4), [[0, 0], [3, 0]], [[5, 5], [0, 5]], [0.2, -0.2])
+    assert code == 1
+    code, _ = _create(lib, _cfg(2, 4), [[0, np.nan], [3, 0]], [[5, 5], [0, 5]], [0.2, 0.2])
+    assert code == 1
+
+
+def test_backward_reports_unsupported(lib):
+    assert lib.plan_backward(None, 1, None, None, None, None, None) == 7

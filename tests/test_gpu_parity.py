@@ -1,0 +1,101 @@
+"""GPU parity: one FP32 CUDA iteration from an oracle iterate against the FP64
+oracle's next iterate, entry by entry (see tests/_parity.py for the rules).
+Cases span one tile and several tiles with ragged tails, walls, fixed ends,
+the U_KEEP reading, and the dense-state streaming mode."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import twa
+
+import _parity as par
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(prob, ks, flags=0):
+    """Parity at each iterate k in ks; returns the stats of every step."""
+    out = []
+    st = twa.initial_state(prob)
+    done = 0
+    for k in sorted(ks):
+        while done < k:
+            st, _ = twa.iterate(prob, st)
+            done += 1
+        new, info = twa.iterate(prob, st, record_branches=True)
+        gpu = par.gpu_step(prob, st, flags=flags)
+        stats = par.compare(prob, new, info, gpu)
+        stats["k"] = k
+        out.append(stats)
+    return out
+
+
+def _prob(inst, **kw):
+    return twa.Problem.from_instance(inst, **kw)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_circle4_parity_along_the_solve(dense):
+    import paper_1311_4527_gb300 as pk
+    prob = _prob(workloads.circle4())
+    stats = _run(prob, [0, 1, 5, 40, 200], flags=pk.PLAN_DENSE_STATE if dense else 0)
+    assert sum(s["coll_active"] for s in stats) > 0
+    assert all(s["coll_excluded"] <= 2 for s in stats), stats
+
+
+def test_circle100_parity():
+    prob = _prob(workloads.circle100())
+    stats = _run(prob, [0, 12])
+    for s in stats:
+        assert s["coll_compared_active"] > 0.8 * s["coll_active"], s
+
+
+def test_square_with_walls_ragged_tiles_parity():
+    # p = 72: three 32-agent tiles, the last one ragged; walls on all sides
+    inst = workloads.small_square(72, 6, seed=11)
+    prob = _prob(inst, cost_unnorm=True)
+    stats = _run(prob, [0, 3, 25])
+    assert sum(s["coll_active"] for s in stats) > 0
+
+
+def test_ragged_single_extra_agent_parity():
+    # p = 33: a second tile holding one agent
+    inst = workloads.circle_swap(33, 3, None, 0.004, 321, radius_range=(0.02, 0.05))
+    prob = _prob(inst)
+    _run(prob, [0, 7])
+
+
+def test_single_agent_and_single_segment():
+    prob = _prob(workloads.circle_swap(1, 5, 0.1, 0.0, 5))
+    _run(prob, [0, 3])
+    inst = workloads.circle_swap(6, 1, 0.1, 0.01, 6)
+    prob = _prob(inst)
+    st = twa.initial_state(prob)
+    new, info = twa.iterate(prob, st, record_branches=True)
+    gpu = par.gpu_step(prob, st)
+    par.compare(prob, new, info, gpu)
+    assert np.array_equal(gpu["z"], st.z.astype(np.float32))
+
+
+def test_u_keep_reading_parity():
+    prob = _prob(workloads.circle4(), u_keep=True)
+    _run(prob, [0, 6, 30])
+
+
+def test_per_segment_costs_and_unnormalised_cost_parity():
+    inst = workloads.circle_swap(5, 6, 0.2, 0.01, 55)
+    rng = np.random.default_rng(0)
+    prob = _prob(inst, cost_unnorm=True)
+    prob.cost = rng.uniform(0.5, 2.0, size=(5, 6))
+    _run(prob, [0, 10])
+
+
+def test_full_size_square1024_one_iteration():
+    """p=1024, eta=16, 4 walls (8.4M collision factors) in the launch
+    configuration the benchmark times: the first iteration and one from the
+    oracle's second iterate, compared entry by entry."""
+    prob = _prob(workloads.square1024())
+    stats = _run(prob, [0, 2])
+    for s in stats:
+        assert s["coll_active"] > 10000
+        assert s["coll_excluded"] < 0.01 * s["coll_active"], s

@@ -1,0 +1,138 @@
+"""GPU solver behaviour over many iterations: convergence on the p=4 circle
+swap to the oracle's cost, feasibility of converged plans, determinism, the
+dense-state and bit-gated modes agreeing bit for bit, warm-start re-planning
+and the non-finite detector."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import twa
+
+import _parity as par
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _solve(inst, **kw):
+    import paper_1311_4527_gb300 as pk
+    pl = pk.Planner.from_instance(inst, check_every=kw.pop("check_every", 1), **kw)
+    conv, it, res = pl.solve()
+    z = pl.trajectory().cpu().numpy().astype(np.float64)
+    pl.close()
+    return conv, it, res, z
+
+
+def test_circle4_converged_cost_matches_the_oracle():
+    inst = workloads.circle4()
+    prob = twa.Problem.from_instance(inst)
+    g = json.load(open(os.path.join(HERE, "golden", "circle4_eta4.json")))
+    conv, it, res, z = _solve(inst)
+    assert conv, (it, res)
+    cost = twa.total_cost(prob, z)
+    assert abs(cost - g["total_cost"]) <= 1e-3 * g["total_cost"], (cost, g["total_cost"])
+    coll, _ = twa.min_clearance(prob, z)
+    assert coll >= 1.0 - 1e-4
+    assert np.abs(z[:, 0] - inst.start).max() <= 1e-6 * par.scale_of(prob) + 1e-7
+    assert np.abs(z[:, -1] - inst.goal).max() <= 1e-6 * par.scale_of(prob) + 1e-7
+    # the converged plan is close to the oracle's, not just equally cheap
+    assert np.abs(z - np.array(g["z"])).max() <= 1e-3
+
+
+def test_circle100_solve_is_feasible_when_converged():
+    inst = workloads.circle100()
+    prob = twa.Problem.from_instance(inst)
+    conv, it, res, z = _solve(inst, check_every=50)
+    if conv:
+        coll, _ = twa.min_clearance(prob, z)
+        assert coll >= 1.0 - 1e-4
+    assert np.all(np.isfinite(z))
+    assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
+
+
+def test_dense_and_gated_state_are_bitwise_identical():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.circle100()
+    zs = []
+    for flags in (0, pk.PLAN_DENSE_STATE):
+        pl = pk.Planner.from_instance(inst, flags=flags)
+        pl.iterate(150)
+        zs.append(pl.trajectory().cpu().numpy())
+        pl.close()
+    assert np.array_equal(zs[0], zs[1])
+
+
+def test_runs_are_deterministic():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(100, 8, seed=3)
+    outs = []
+    for _ in range(2):
+        pl = pk.Planner.from_instance(inst)
+        r = pl.iterate(60, residual=True)
+        outs.append((pl.trajectory().cpu().numpy(), r, pl.info()["active_coll"]))
+        pl.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+
+
+def test_residual_matches_the_oracle_definition():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.circle4()
+    prob = twa.Problem.from_instance(inst)
+    st = twa.initial_state(prob)
+    pl = pk.Planner.from_instance(inst)
+    for k in range(12):
+        st, info = twa.iterate(prob, st)
+        r = pl.iterate(1, residual=True)
+        assert abs(r - info.residual) <= 2e-5 * max(1.0, info.residual), (k, r, info.residual)
+    pl.close()
+
+
+def test_warm_start_replanning_moves_the_goals():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.circle4()
+    pl = pk.Planner.from_instance(inst, check_every=1)
+    conv, it, _ = pl.solve()
+    assert conv
+    goal = inst.goal * 1.2
+    pl.set_endpoints(inst.start, goal)
+    z = pl.trajectory().cpu().numpy()
+    assert np.allclose(z[:, -1], goal.astype(np.float32))
+    r = pl.iterate(2000, residual=True)
+    z = pl.trajectory().cpu().numpy()
+    prob = twa.Problem.from_instance(inst)
+    prob.goal = goal
+    coll, _ = twa.min_clearance(prob, z.astype(np.float64))
+    assert r < 1e-3 and coll >= 1.0 - 1e-3
+    pl.close()
+
+
+def test_non_finite_state_is_reported():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.circle4()
+    prob = twa.Problem.from_instance(inst)
+    st = twa.initial_state(prob)
+    st.z[1, 2] = np.nan  # injected on the host into the imported state
+    pl = pk.Planner.from_instance(inst, check_every=1, max_iter=5)
+    pl.import_state(st.z, st.u_coll, st.u_kin, None, 0)
+    with pytest.raises(pk.PlanError) as e:
+        pl.solve()
+    assert e.value.status == "PLAN_ENUMERIC"
+    pl.close()
+
+
+def test_info_counts():
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(72, 6, seed=11)
+    pl = pk.Planner.from_instance(inst)
+    pl.iterate(3)
+    inf = pl.info()
+    assert inf["n_coll"] == 6 * 72 * 71 // 2 and inf["n_kin"] == 6 * 72
+    assert inf["n_wall"] == 4 * 6 * 72 and inf["k"] == 3
+    ex = pl.export_state()
+    assert inf["active_coll"] == int(ex["act_coll"].sum().item())
+    pl.close()
