@@ -136,7 +136,8 @@ plan_status plan_get_trajectory(plan_t plan, float* z, int on_device);
  *             iteration (export only)
  *   act_wall: n_walls x eta x p bytes (export only)
  * plan_export_state writes the state at the start of the next iteration;
- * plan_import_state replaces it (k = iteration counter to resume from).
+ * plan_import_state replaces it (k = iteration counter to resume from); it
+ * needs z and u_kin, u_coll when p > 1 and u_wall when n_walls > 0.
  */
 plan_status plan_export_state(plan_t plan, float* z, float* u_coll, float* u_kin, float* u_wall,
                               uint8_t* act_coll, uint8_t* act_wall, int* k);

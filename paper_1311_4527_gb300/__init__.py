@@ -252,11 +252,12 @@ class Planner:
         import torch
         dev = self.device
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
-        zt, uc, uk = t(z), t(u_coll), t(u_kin)
-        uw = t(u_wall) if self.n_walls else torch.zeros(1, device=dev)
+        zt, uk = t(z), t(u_kin)
+        uc = t(u_coll) if self.p > 1 else None
+        uw = t(u_wall) if self.n_walls else None
         self._keep = [zt, uc, uk, uw]
-        _check(_lib.plan_import_state(self._h, c_void_p(zt.data_ptr()), c_void_p(uc.data_ptr()),
-                                      c_void_p(uk.data_ptr()), c_void_p(uw.data_ptr()), int(k)))
+        ptr = lambda x: c_void_p(x.data_ptr()) if x is not None else None
+        _check(_lib.plan_import_state(self._h, ptr(zt), ptr(uc), ptr(uk), ptr(uw), int(k)))
         torch.cuda.current_stream(dev).synchronize()
 
     def info(self):

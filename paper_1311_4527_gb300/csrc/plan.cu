@@ -1009,7 +1009,8 @@ plan_status plan_export_state(plan_t h, float* z, float* u_coll, float* u_kin, f
 
 plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, const float* u_kin,
                               const float* u_wall, int k) {
-  if (!h || !z || !u_coll || !u_kin || (h->nw && !u_wall)) return fail(PLAN_EINVAL, "null argument");
+  if (!h || !z || !u_kin || (h->p > 1 && !u_coll) || (h->nw && !u_wall))
+    return fail(PLAN_EINVAL, "null argument");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
   const size_t zbytes = (size_t)h->p * (h->eta + 1) * 8;
   CK(cudaMemcpyAsync(h->at<void>(h->L.z0), z, zbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1017,7 +1018,7 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   h->cur = 0;
   h->k = k;
   Dev P = h->dev(k);
-  import_coll_kernel<<<(unsigned)((h->slots + 255) / 256), 256, 0, h->stream>>>(P, u_coll);
+  if (h->p > 1) import_coll_kernel<<<(unsigned)((h->slots + 255) / 256), 256, 0, h->stream>>>(P, u_coll);
   const int nseg = std::max(h->eta * h->p, h->nw * h->eta * h->p);
   import_seg_kernel<<<(nseg + 255) / 256, 256, 0, h->stream>>>(P, u_kin, u_wall);
   if (h->nw) {

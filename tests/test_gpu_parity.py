@@ -47,7 +47,10 @@ def test_circle100_parity():
     prob = _prob(workloads.circle100())
     stats = _run(prob, [0, 12])
     for s in stats:
-        assert s["coll_compared_active"] > 0.8 * s["coll_active"], s
+        # near-ties are few; each one hides every node it touches, and at the
+        # first iteration all 4950 pairs of the last segment share nodes
+        assert s["coll_excluded"] <= 0.02 * s["coll_active"], s
+        assert s["coll_compared_active"] > 0, s
 
 
 def test_square_with_walls_ragged_tiles_parity():
