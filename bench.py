@@ -168,12 +168,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="gated", choices=["gated", "dense"])
-    ap.add_argument("--workload", default="square1024_eta16")
+    ap.add_argument("--workload", default="square1024_eta16",
+                    help="a named workload, or 'square' for a random square of --p agents")
+    ap.add_argument("--p", type=int, default=768)
+    ap.add_argument("--eta", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--start-iter", type=int, default=20,
                     help="untimed iterations before warm-up (a mid-solve iterate)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    inst = workloads.by_name(args.workload)
+    if args.workload == "square":
+        inst = workloads.small_square(args.p, args.eta, seed=args.seed)
+    else:
+        inst = workloads.by_name(args.workload)
 
     if args.impl == "reference":
         return run_reference(args, inst)
