@@ -164,6 +164,41 @@ plan_status plan_get_info(plan_t plan, plan_info* info);
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,
                           float* d_radius, float* d_cost_w);
 
+/*
+ * One iteration without any allocation, for callers that cannot allocate GPU
+ * memory: code whose device memory is owned by a host framework or a memory
+ * pool it may not bypass, real-time control loops where cudaMalloc is banned
+ * because it can synchronise the device and take unbounded time, and plugins
+ * loaded into processes whose allocator belongs to someone else.  The paper
+ * has no counterpart; this is a packaging of plan_iterate for those callers.
+ *
+ * It runs the same kernels as plan_iterate on one iteration of the paper's
+ * variables: (z_in, u_*_in) at iteration k -> (z_out, u_*_out) at k + 1,
+ * with the layouts of plan_export_state.  Every pointer is DEVICE memory on
+ * the current device: the problem arrays (start, goal, radius, cost_w,
+ * walls, laid out as for plan_create; walls may be NULL when n_walls == 0,
+ * u_coll_* when p == 1, u_wall_* when n_walls == 0, act_* may be NULL) and
+ * the state in and out (in and out must not overlap).  The endpoints are not
+ * checked for overlap: that check needs host copies.
+ *
+ * All temporaries live in one file-scope device array of
+ * PLAN_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits.  Problems whose workspace
+ * (plan_workspace_size) exceeds it are rejected with PLAN_ENOMEM.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call reuses the same array, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Work is enqueued on cuda_stream; the call does not synchronise.
+ */
+#define PLAN_STATIC_SCRATCH_BYTES (16u << 20)
+plan_status plan_iterate_static(const plan_config* cfg, const float* start, const float* goal,
+                                const float* radius, const float* cost_w, const float* walls,
+                                const float* z_in, const float* u_coll_in, const float* u_kin_in,
+                                const float* u_wall_in, float* z_out, float* u_coll_out,
+                                float* u_kin_out, float* u_wall_out, uint8_t* act_coll_out,
+                                uint8_t* act_wall_out, int k, void* cuda_stream);
+
 void plan_destroy(plan_t plan);
 const char* plan_last_error(void);
 

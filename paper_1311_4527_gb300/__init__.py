@@ -34,7 +34,7 @@ STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: 
 EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_set_endpoints",
                     "plan_iterate", "plan_solve", "plan_get_trajectory", "plan_export_state",
                     "plan_import_state", "plan_get_info", "plan_backward", "plan_destroy",
-                    "plan_last_error"]
+                    "plan_last_error", "plan_iterate_static"]
 
 
 class PlanError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library(path: str | None = None):
     lib.plan_import_state.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]
     lib.plan_get_info.argtypes = [c_void_p, POINTER(plan_info)]
     lib.plan_backward.argtypes = [c_void_p, c_int, fp, fp, fp, fp, fp]
+    lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_destroy.argtypes = [c_void_p]
     lib.plan_destroy.restype = None
     lib.plan_last_error.restype = ctypes.c_char_p

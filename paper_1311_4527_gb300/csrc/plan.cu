@@ -41,6 +41,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1057,6 +1058,122 @@ plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, f
                           float* d_radius, float* d_cost_w) {
   (void)h; (void)K; (void)dL_dz; (void)d_start; (void)d_goal; (void)d_radius; (void)d_cost_w;
   return fail(PLAN_EUNSUPPORTED, "plan_backward is not built yet");
+}
+
+
+// ---------------------------------------------------------------------------
+// plan_iterate_static: one iteration with every temporary in a static array
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// Temporaries of plan_iterate_static, laid out like a plan_create workspace.
+// Host code must not use this name as an address: it is looked up per device
+// with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[PLAN_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Kinetic coefficients c_{i,s} and the tile-pair table, computed on the
+// device from the caller's device arrays (same arithmetic as upload_inputs).
+__global__ void static_prep_kernel(int p, int eta, int nt, int ntp, unsigned flags,
+                                   const float* cost_w, float* cost, int2* tiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p * eta) {
+    const int i = t / eta, s = t - i * eta;
+    const double norm = (flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * eta);
+    const double C = (flags & PLAN_COST_PER_SEGMENT) ? cost_w[(size_t)i * eta + s] : cost_w[i];
+    cost[t] = (float)(C * norm);
+  }
+  if (t < ntp) {
+    int I = 0, off = 0;
+    while (off + (nt - I) <= t) { off += nt - I; ++I; }
+    tiles[t] = make_int2(I, I + (t - off));
+  }
+}
+
+plan_status static_scratch_for_current_device(void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(PLAN_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_static_scratch));
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plan_status plan_iterate_static(const plan_config* cfg, const float* start, const float* goal,
+                                const float* radius, const float* cost_w, const float* walls,
+                                const float* z_in, const float* u_coll_in, const float* u_kin_in,
+                                const float* u_wall_in, float* z_out, float* u_coll_out,
+                                float* u_kin_out, float* u_wall_out, uint8_t* act_coll_out,
+                                uint8_t* act_wall_out, int k, void* cuda_stream) {
+  if (!cfg || !start || !goal || !radius || !cost_w || !z_in || !u_kin_in || !z_out || !u_kin_out)
+    return fail(PLAN_EINVAL, "null argument");
+  if (!sizes_ok(cfg)) return fail(PLAN_EINVAL, "p, eta or n_walls out of range");
+  if (cfg->p > 1 && (!u_coll_in || !u_coll_out)) return fail(PLAN_EINVAL, "null u_coll");
+  if (cfg->n_walls > 0 && (!walls || !u_wall_in || !u_wall_out)) return fail(PLAN_EINVAL, "null wall array");
+  if (!(cfg->rho0 > 0.f) || !(cfg->alpha > 0.f)) return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
+  if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
+  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT | PLAN_DENSE_STATE;
+  if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
+  const Layout L = layout_for(cfg);
+  if (L.total > PLAN_STATIC_SCRATCH_BYTES)
+    return fail(PLAN_ENOMEM, "problem needs %zu bytes of scratch; the static array holds %u "
+                "(p = %d, eta = %d, n_walls = %d)", L.total, PLAN_STATIC_SCRATCH_BYTES, cfg->p,
+                cfg->eta, cfg->n_walls);
+  void* scratch = nullptr;
+  plan_status st = static_scratch_for_current_device(&scratch);
+  if (st != PLAN_OK) return st;
+
+  plan_s h;  // a plan over the static array; nothing here allocates
+  h.cfg = *cfg;
+  h.p = cfg->p; h.eta = cfg->eta; h.nw = cfg->n_walls;
+  h.nt = (h.p + TILE - 1) / TILE;
+  h.ntp = h.nt * (h.nt + 1) / 2;
+  h.slots = (size_t)h.eta * h.ntp * TILE * TILE;
+  h.stream = (cudaStream_t)cuda_stream;
+  h.L = L;
+  h.ws = static_cast<char*>(scratch);
+  h.own_ws = false;
+  h.h_res = nullptr;
+  h.k = 0;
+  h.cur = 0;
+
+  const size_t p = h.p;
+  CK(cudaMemcpyAsync(h.at<void>(L.start), start, p * 8, cudaMemcpyDeviceToDevice, h.stream));
+  CK(cudaMemcpyAsync(h.at<void>(L.goal), goal, p * 8, cudaMemcpyDeviceToDevice, h.stream));
+  CK(cudaMemcpyAsync(h.at<void>(L.radius), radius, p * 4, cudaMemcpyDeviceToDevice, h.stream));
+  if (h.nw)
+    CK(cudaMemcpyAsync(h.at<void>(L.walls), walls, (size_t)h.nw * 16, cudaMemcpyDeviceToDevice, h.stream));
+  // the scratch keeps the previous call's contents: clear what must start at zero
+  CK(cudaMemsetAsync(h.at<void>(L.status), 0, 4, h.stream));
+  if (h.cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) {
+    CK(cudaMemsetAsync(h.at<void>(L.ulo), 0, h.slots * 16, h.stream));
+    CK(cudaMemsetAsync(h.at<void>(L.uhi), 0, h.slots * 16, h.stream));
+  }
+  const int nprep = std::max(h.p * h.eta, h.ntp);
+  static_prep_kernel<<<(nprep + 255) / 256, 256, 0, h.stream>>>(
+      h.p, h.eta, h.nt, h.ntp, h.cfg.flags, cost_w, h.at<float>(L.cost), h.at<int2>(L.tiles));
+  CK(cudaGetLastError());
+  st = plan_import_state(&h, z_in, u_coll_in, u_kin_in, u_wall_in, k);
+  if (st == PLAN_OK) st = run_iteration(&h);
+  if (st == PLAN_OK)
+    st = plan_export_state(&h, z_out, h.p > 1 ? u_coll_out : nullptr, u_kin_out,
+                           h.nw ? u_wall_out : nullptr, h.p > 1 ? act_coll_out : nullptr,
+                           h.nw ? act_wall_out : nullptr, nullptr);
+  return st;
 }
 
 }  // extern "C"

@@ -108,3 +108,14 @@ def test_bad_parameters_are_rejected(lib):
 
 def test_backward_reports_unsupported(lib):
     assert lib.plan_backward(None, 1, None, None, None, None, None) == 7
+
+
+def test_static_entry_point_rejects_a_problem_that_does_not_fit(lib):
+    """plan_iterate_static refuses sizes beyond its static scratch array
+    before it touches any pointer."""
+    cfg = pk.make_config(1024, 16, n_walls=4)
+    dummy = np.zeros(8, dtype=np.float32)
+    ptr = ctypes.c_void_p(dummy.ctypes.data)
+    code = lib.plan_iterate_static(ctypes.byref(cfg), *([ptr] * 15), 0, None)
+    assert code == 2
+    assert b"static array" in lib.plan_last_error()
