@@ -73,7 +73,13 @@ struct Dev {
   float4 *ukin, *xkin;   // [eta][p]
   float4 *uwall, *xwall; // [nw][eta][p]
   uint32_t* wbits;       // [nw][eta][nt]
-  float* partial;        // [eta][nt][nt][6][32]
+  uint32_t* work;        // active collision slots of this iteration
+  unsigned* work_count;  // their number
+  unsigned* work_count_next;  // the counter the next iteration appends to
+  unsigned long long* accx;  // [p][eta+1] fixed-point sums of rho0-weighted m.x
+  unsigned long long* accy;  //                                 ... of m.y
+  unsigned* accc;        // [p][eta+1] number of rho0-weighted incoming edges
+  const float* fix;      // fixed-point scale (a power of two) and |m| bound
   unsigned* res_cur;     // residual slot of this iteration (consensus part)
   unsigned* res_prev;    // residual slot of the previous iteration (primal part)
   unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction
@@ -92,6 +98,23 @@ __device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, f
     return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
   }
   return keep ? u_prev : mk(0.f, 0.f);
+}
+
+// Step 5's sums in 64-bit fixed point: each FP32 m converts exactly (the scale
+// is a power of two chosen from the layout's extent), integer addition does not
+// depend on the order of the atomics, so z is deterministic and is the
+// correctly rounded mean of the incoming m's.  A non-finite or out-of-range m
+// sets status bit 1, which the consensus pass turns into a NaN residual.
+__device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m) {
+  const float scale = P.fix[0], bound = P.fix[1];
+  if (!(fabsf(m.x) <= bound && fabsf(m.y) <= bound)) {
+    atomicOr(P.status, 2u);
+    return;
+  }
+  const size_t node = (size_t)i * (P.eta + 1) + s;
+  atomicAdd(P.accx + node, (unsigned long long)__float2ll_rn(m.x * scale));
+  atomicAdd(P.accy + node, (unsigned long long)__float2ll_rn(m.y * scale));
+  atomicAdd(P.accc + node, 1u);
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return mk(v.x, v.y); }
@@ -136,42 +159,42 @@ __device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 nj
   }
 }
 
-// Kinetic factor (i, s): always active.  Adds its contributions to acc.
+// Kinetic factor (i, s): always active (it always sends rho0).  Finishes its
+// pending dual update, runs the closed-form minimizer and stores x and u.
 __device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float2 zl, float2 zh,
-                                               bool pin_lo, bool pin_hi, float* acc, float& res) {
-  size_t idx = (size_t)s * P.p + i;
-  float4 u4 = P.ukin[idx], x4 = P.xkin[idx];
-  float2 ul = finish_u(true, pin_lo, false, lo2(u4), lo2(x4), zl, P.alpha, res);
-  float2 uh = finish_u(true, pin_hi, false, hi2(u4), hi2(x4), zh, P.alpha, res);
-  float2 nl = zl - ul, nh = zh - uh;
+                                               bool pin_lo, bool pin_hi, float& res) {
+  const size_t idx = (size_t)s * P.p + i;
+  const float4 u4 = P.ukin[idx], x4 = P.xkin[idx];
+  const float2 ul = finish_u(true, pin_lo, false, lo2(u4), lo2(x4), zl, P.alpha, res);
+  const float2 uh = finish_u(true, pin_hi, false, hi2(u4), hi2(x4), zh, P.alpha, res);
   float2 xl, xh;
-  energy_prox(nl, nh, P.rho, pin_lo, pin_hi, P.cost[(size_t)i * P.eta + s], xl, xh);
+  energy_prox(zl - ul, zh - uh, P.rho, pin_lo, pin_hi, P.cost[(size_t)i * P.eta + s], xl, xh);
   P.xkin[idx] = pack(xl, xh);
   P.ukin[idx] = pack(ul, uh);
-  if (!pin_lo) { float2 m = xl + ul; acc[0] += m.x; acc[1] += m.y; acc[2] += 1.f; }
-  if (!pin_hi) { float2 m = xh + uh; acc[3] += m.x; acc[4] += m.y; acc[5] += 1.f; }
+  if (!pin_lo) contribute(P, i, s, xl + ul);
+  if (!pin_hi) contribute(P, i, s + 1, xh + uh);
 }
 
-// Wall factor (w, i, s).  Called by a full warp (lane = agent of the tile).
+// Wall factor (w, i, s).  Called by a full warp (lane = agent of tile I).
 __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
                                             float2 zl, float2 zh, float r, bool pin_lo,
-                                            bool pin_hi, float* acc, float& res) {
-  int lane = threadIdx.x & 31;
-  size_t widx = ((size_t)w * P.eta + s) * P.nt + I;
-  uint32_t word = P.wbits[widx];
-  bool bprev = vi && ((word >> lane) & 1u);
-  size_t idx = ((size_t)w * P.eta + s) * P.p + i;
+                                            bool pin_hi, float& res) {
+  const int lane = threadIdx.x & 31;
+  const size_t widx = ((size_t)w * P.eta + s) * P.nt + I;
+  const uint32_t word = P.wbits[widx];
+  const bool bprev = vi && ((word >> lane) & 1u);
+  const size_t idx = ((size_t)w * P.eta + s) * P.p + i;
   float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = u4;
   if (vi && (P.dense || bprev)) u4 = P.uwall[idx];
   if (bprev) x4 = P.xwall[idx];
-  float2 ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
-  float2 uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
-  float2 nl = zl - ul, nh = zh - uh;
-  float4 W = P.walls[w];
-  float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
-  bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
-  uint32_t nw = __ballot_sync(FULL, act);
-  if (lane == 0) P.wbits[widx] = nw;
+  const float2 ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
+  const float2 uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
+  const float2 nl = zl - ul, nh = zh - uh;
+  const float4 W = P.walls[w];
+  const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
+  const bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
+  const uint32_t nw = __ballot_sync(FULL, act);
+  if (lane == 0 && nw != word) P.wbits[widx] = nw;
   if (act) {
     float2 xl = nl, xh = nh;
     if (pin_lo && pin_hi) {
@@ -180,193 +203,282 @@ __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi,
     } else if (pin_hi) {
       if (!capsule_prox_pinned(nh, nl, c0, c1, r, xl)) atomicOr(P.status, 1u);
     } else {
-      float wgt = 0.5f * P.rho;
+      const float wgt = 0.5f * P.rho;
       capsule_prox_free(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
     }
     P.xwall[idx] = pack(xl, xh);
     P.uwall[idx] = pack(ul, uh);
-    if (!pin_lo) { float2 m = xl + ul; acc[0] += m.x; acc[1] += m.y; acc[2] += 1.f; }
-    if (!pin_hi) { float2 m = xh + uh; acc[3] += m.x; acc[4] += m.y; acc[5] += 1.f; }
+    if (!pin_lo) contribute(P, i, s, xl + ul);
+    if (!pin_hi) contribute(P, i, s + 1, xh + uh);
   } else if (vi && P.dense) {
     P.uwall[idx] = pack(ul, uh);
   }
 }
 
-__global__ void __launch_bounds__(THREADS) factor_kernel(Dev P) {
-  __shared__ float2 zI[2][TILE], zJ[2][TILE];
-  __shared__ float rI[TILE], rJ[TILE];
-  __shared__ float rowacc[6][TILE];
-  __shared__ float colacc[WARPS][6][TILE];
-  __shared__ float segacc[WARPS][6][TILE];
+// Collision test of the n-trajectories (Eq. f_coll_def): does the relative
+// segment [cl, ch] pass closer than R to the origin?  Strict, so touching is
+// inactive.  Division-free: for an interior closest point, dist^2 =
+// cross(cl, d)^2 / |d|^2 is compared as cross^2 < R^2 |d|^2.
+__device__ __forceinline__ bool collides(float2 cl, float2 ch, float R) {
+  const float2 d = ch - cl;
+  const float dd = dot(d, d);
+  const float t = -dot(cl, d);
+  const float R2 = R * R;
+  const float c = cross(cl, d);
+  // endpoints, or an interior closest point (0 < t < |d|^2)
+  return (dot(cl, cl) < R2) | (dot(ch, ch) < R2) | ((t > 0.f) & (t < dd) & (c * c < R2 * dd));
+}
 
+__device__ __forceinline__ int tile_pair(int nt, int I, int J) {  // I <= J
+  return I * nt - I * (I - 1) / 2 + (J - I);
+}
+
+// Pass 1 of an iteration.  One CTA of 4 warps per (segment s, agent tiles
+// I <= J) block of 32 x 32 collision factors; each warp takes 8 rows, lane =
+// column agent j, and the row agents' data is held one per lane and broadcast
+// by shuffles.  Per row, the warp finishes the pending dual update of the
+// pairs that were active (step 7 of the previous iteration), forms n = z - u
+// (step 1), runs the collision test (steps 2-3: weight rho0 or 0), stores the
+// row's activity bits, and appends its active pairs to the global worklist.
+// DENSE streams the u record of every pair (PLAN_DENSE_STATE).
+//
+// Early out (gated state): agent i's segment lies in the disk of centre m_i
+// (its midpoint) and radius h_i (half its length), so the relative segment of
+// a pair stays at distance >= |m_j - m_i| - h_i - h_j from the origin.  Rows
+// where every pair has |m_j - m_i| > (h_i + h_j + r_i + r_j)(1 + 1e-5) cannot
+// collide and skip the exact test; the margin keeps the outcome identical to
+// running the exact test everywhere.
+constexpr int TEST_WARPS = 4;
+constexpr int TEST_ROWS = TILE / TEST_WARPS;
+
+template <bool DENSE>
+__global__ void __launch_bounds__(32 * TEST_WARPS) test_kernel(Dev P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int blk = blockIdx.x;
+  const int E1 = P.eta + 1;
+  float res = 0.f;
+  if (blk == 0 && threadIdx.x == 0) *P.res_cur = 0u;
   const int s = blk / P.ntp;
-  const int tp = blk - s * P.ntp;
-  const int2 IJ = P.tiles[tp];
+  const int2 IJ = P.tiles[blk - s * P.ntp];
   const int I = IJ.x, J = IJ.y;
   const bool diag = (I == J);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int E1 = P.eta + 1;
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-
-  if (blk == 0 && tid == 0) *P.res_cur = 0u;
-
-  if (tid < 2 * TILE) {
-    int side = tid >> 5, a = tid & 31;
-    int ag = (side ? J : I) * TILE + a;
-    float2 zl = mk(0.f, 0.f), zh = mk(0.f, 0.f);
-    float rr = 0.f;
-    if (ag < P.p) { zl = P.z[(size_t)ag * E1 + s]; zh = P.z[(size_t)ag * E1 + s + 1]; rr = P.radius[ag]; }
-    if (side) { zJ[0][a] = zl; zJ[1][a] = zh; rJ[a] = rr; }
-    else { zI[0][a] = zl; zI[1][a] = zh; rI[a] = rr; }
-  }
-  __syncthreads();
-
-  float res = 0.f;
-  float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int j = J * TILE + lane;
-  const bool vj = j < P.p;
-  const float2 zjl = zJ[0][lane], zjh = zJ[1][lane];
-  const float rj = rJ[lane];
-
-#pragma unroll 1
-  for (int q = 0; q < ROWS; ++q) {
-    const int r = warp * ROWS + q;
-    const int i = I * TILE + r;
-    const bool vi = i < P.p;
-    const bool valid = vi && vj && (!diag || r < lane);
-    const size_t row = (size_t)blk * TILE + r;
-    const size_t fid = row * TILE + lane;
-    const uint32_t word = vi ? P.bits[row] : 0u;
-    const bool bprev = valid && ((word >> lane) & 1u);
-    float4 ul4 = make_float4(0.f, 0.f, 0.f, 0.f), uh4 = ul4, xl4 = ul4, xh4 = ul4;
-    if (valid && (P.dense || bprev)) { ul4 = P.ulo[fid]; uh4 = P.uhi[fid]; }
-    if (bprev) { xl4 = P.xlo[fid]; xh4 = P.xhi[fid]; }
-    const float2 zil = zI[0][r], zih = zI[1][r];
-    // step 7 of the previous iteration, then step 1
-    float2 uil = finish_u(bprev, pin_lo, P.keep, lo2(ul4), lo2(xl4), zil, P.alpha, res);
-    float2 ujl = finish_u(bprev, pin_lo, P.keep, hi2(ul4), hi2(xl4), zjl, P.alpha, res);
-    float2 uih = finish_u(bprev, pin_hi, P.keep, lo2(uh4), lo2(xh4), zih, P.alpha, res);
-    float2 ujh = finish_u(bprev, pin_hi, P.keep, hi2(uh4), hi2(xh4), zjh, P.alpha, res);
-    float2 nil = zil - uil, nih = zih - uih, njl = zjl - ujl, njh = zjh - ujh;
-    // steps 2-3: collision test of the n-trajectories (strict: touching is inactive)
-    const float R = rI[r] + rj;
-    const bool act = valid && dist2_origin_segment(njl - nil, njh - nih) < R * R;
-    const uint32_t nword = __ballot_sync(FULL, act);
-    if (lane == 0 && vi) P.bits[row] = nword;
-    float m[8];  // (i lo, i hi, j lo, j hi) x (x, y) of m = x + u, active lanes only
-#pragma unroll
-    for (int e = 0; e < 8; ++e) m[e] = 0.f;
-    if (act) {
-      float2 xil, xih, xjl, xjh;
-      coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, R, P.rho, xil, xih, xjl, xjh);
-      P.xlo[fid] = pack(xil, xjl);
-      P.xhi[fid] = pack(xih, xjh);
-      P.ulo[fid] = pack(uil, ujl);
-      P.uhi[fid] = pack(uih, ujh);
-      float2 a = xil + uil, b = xih + uih, c = xjl + ujl, d = xjh + ujh;
-      m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
-      m[4] = c.x; m[5] = c.y; m[6] = d.x; m[7] = d.y;
-    } else if (valid && P.dense) {
-      P.ulo[fid] = pack(uil, ujl);
-      P.uhi[fid] = pack(uih, ujh);
+  const int r0 = warp * TEST_ROWS;
+  const int nrows = min(TEST_ROWS, P.p - I * TILE - r0);
+  if (nrows > 0) {  // warp-uniform
+    // column agent of this lane
+    const int j = J * TILE + lane;
+    const bool vj = j < P.p;
+    float2 zjl = mk(0.f, 0.f), zjh = zjl;
+    float rj = 0.f;
+    if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
+    // row agents r0 .. r0 + 7, held by lanes 0 .. 7
+    float2 ill = mk(0.f, 0.f), ilh = ill;
+    float rl = 0.f;
+    uint32_t wordl = 0u;
+    if (lane < nrows) {
+      const int il = I * TILE + r0 + lane;
+      ill = P.z[(size_t)il * E1 + s]; ilh = P.z[(size_t)il * E1 + s + 1]; rl = P.radius[il];
+      wordl = P.bits[(size_t)blk * TILE + r0 + lane];
     }
-    const float wl = (act && !pin_lo) ? 1.f : 0.f, wh = (act && !pin_hi) ? 1.f : 0.f;
-    // column agent j: registers, fixed row order
-    col[0] += wl * m[4]; col[1] += wl * m[5]; col[2] += wl;
-    col[3] += wh * m[6]; col[4] += wh * m[7]; col[5] += wh;
-    // row agent i: warp reduction when any lane is active
-    float v[6] = {wl * m[0], wl * m[1], wl, wh * m[2], wh * m[3], wh};
-    if (nword != 0u) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int e = 0; e < 6; ++e) v[e] += __shfl_xor_sync(FULL, v[e], o);
-      }
+    float2 mj = mk(0.f, 0.f), ml = mj;
+    float bj = 0.f, bl = 0.f;
+    if (!DENSE) {
+      mj = 0.5f * (zjl + zjh);
+      bj = 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj;
+      ml = 0.5f * (ill + ilh);
+      bl = 0.5f * sqrtf(dot(ilh - ill, ilh - ill)) + rl;
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int e = 0; e < 6; ++e) rowacc[e][r] = v[e];
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < 6; ++e) colacc[warp][e][lane] = col[e];
-
-  // kinetic and wall factors of the diagonal tiles
-  if (diag) {
-    float seg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const int i = I * TILE + lane;
-    const bool vi = i < P.p;
-    const float2 zl = zI[0][lane], zh = zI[1][lane];
-    for (int f = warp; f < 1 + P.nw; f += WARPS) {
-      if (f == 0) {
-        if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, seg, res);
+#pragma unroll 2
+    for (int q = 0; q < nrows; ++q) {
+      const int r = r0 + q;
+      const uint32_t word = __shfl_sync(FULL, wordl, q);
+      const bool valid = vj && (!diag || r < lane);
+      const float ri = __shfl_sync(FULL, rl, q);
+      bool act = false;
+      float2 uil = mk(0.f, 0.f), ujl = uil, uih = uil, ujh = uil;
+      const size_t row = (size_t)blk * TILE + r;
+      const size_t fid = row * TILE + lane;
+      if (!DENSE && word == 0u) {
+        // no pair of this row was active: every u is 0 by the reset rule, n = z
+        const float2 mi = mk(__shfl_sync(FULL, ml.x, q), __shfl_sync(FULL, ml.y, q));
+        const float br = __shfl_sync(FULL, bl, q) + bj;
+        const float2 dm = mj - mi;
+        const bool near = valid && dot(dm, dm) <= br * br * 1.00002f;
+        if (__any_sync(FULL, near)) {
+          const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
+          const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
+          act = near && collides(zjl - zil, zjh - zih, ri + rj);
+        }
       } else {
-        wall_factor(P, f - 1, i, vi, s, I, zl, zh, rI[lane], pin_lo, pin_hi, seg, res);
+        const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
+        const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
+        const bool bprev = (word >> lane) & 1u;  // set only for valid pairs
+        if (DENSE && valid) {
+          const float4 a = P.ulo[fid], b = P.uhi[fid];
+          uil = lo2(a); ujl = hi2(a); uih = lo2(b); ujh = hi2(b);
+        }
+        if (bprev) {
+          // finish step 7 of the previous iteration for this pair
+          const float4 xa = P.xlo[fid], xb = P.xhi[fid];
+          float4 a, b;
+          if (DENSE) { a = pack(uil, ujl); b = pack(uih, ujh); }
+          else { a = P.ulo[fid]; b = P.uhi[fid]; }
+          uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zil, P.alpha, res);
+          ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), zjl, P.alpha, res);
+          uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
+          ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), zjh, P.alpha, res);
+        } else if (DENSE && !P.keep) {
+          uil = ujl = uih = ujh = mk(0.f, 0.f);  // reset rule: inactive edges carry u = 0
+        }
+        if (pin_lo) { uil = mk(0.f, 0.f); ujl = uil; }
+        if (pin_hi) { uih = mk(0.f, 0.f); ujh = uih; }
+        act = valid && collides((zjl - ujl) - (zil - uil), (zjh - ujh) - (zih - uih), ri + rj);
+        if (DENSE && valid) {
+          P.ulo[fid] = pack(uil, ujl);
+          P.uhi[fid] = pack(uih, ujh);
+        }
       }
-    }
-#pragma unroll
-    for (int e = 0; e < 6; ++e) segacc[warp][e][lane] = seg[e];
-  }
-  __syncthreads();
-
-  if (tid < 6 * TILE) {
-    const int e = tid >> 5, a = tid & 31;
-    float cs = 0.f;
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) cs += colacc[w][e][a];
-    float* base = P.partial;
-    if (diag) {
-      float ss = 0.f;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) ss += segacc[w][e][a];
-      float v = rowacc[e][a] + cs + ss;
-      base[((((size_t)s * P.nt + I) * P.nt + I) * 6 + e) * TILE + a] = v;
-    } else {
-      base[((((size_t)s * P.nt + I) * P.nt + J) * 6 + e) * TILE + a] = rowacc[e][a];
-      base[((((size_t)s * P.nt + J) * P.nt + I) * 6 + e) * TILE + a] = cs;
+      const uint32_t nword = __ballot_sync(FULL, act);
+      if (nword != word && lane == 0) P.bits[row] = nword;
+      if (nword) {
+        if (!DENSE && act) {
+          P.ulo[fid] = pack(uil, ujl);
+          P.uhi[fid] = pack(uih, ujh);
+        }
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(P.work_count, (unsigned)__popc(nword));
+        base = __shfl_sync(FULL, base, 0);
+        if (act) P.work[base + __popc(nword & ((1u << lane) - 1u))] = (uint32_t)fid;
+      }
     }
   }
   res = warp_max(res);
   if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
 }
 
-// Step 5: z = sum m / count over the tile partials of both adjacent segments.
+// Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
+// s and one agent tile: warp f < 1 + n_walls takes factor kind f (0 =
+// kinetic, else wall f - 1), lane = agent.
+__global__ void __launch_bounds__(THREADS) segment_kernel(Dev P) {
+  const int s = blockIdx.x / P.nt;
+  const int I = blockIdx.x - s * P.nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = I * TILE + lane;
+  const bool vi = i < P.p;
+  const int E1 = P.eta + 1;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  float2 zl = mk(0.f, 0.f), zh = zl;
+  float r = 0.f;
+  if (vi) { zl = P.z[(size_t)i * E1 + s]; zh = P.z[(size_t)i * E1 + s + 1]; r = P.radius[i]; }
+  float res = 0.f;
+  for (int f = warp; f < 1 + P.nw; f += blockDim.x >> 5) {
+    if (f == 0) {
+      if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
+    } else {
+      wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
+    }
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
+// Pass 2: the collision minimizer (Eq. coll_minimizer_problem through
+// App. C/D/I) of every active pair in the worklist, one thread per pair.
+__global__ void __launch_bounds__(256) prox_kernel(Dev P) {
+  const unsigned n = *P.work_count;
+  const int E1 = P.eta + 1;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const uint32_t fid = P.work[t];
+    const uint32_t row = fid >> 5, c = fid & 31;
+    const uint32_t blk = row >> 5, r = row & 31;
+    const int s = (int)(blk / P.ntp);
+    const int2 IJ = P.tiles[blk - (uint32_t)s * P.ntp];
+    const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
+    const float4 a = P.ulo[fid], b = P.uhi[fid];
+    const float2 nil = P.z[(size_t)i * E1 + s] - lo2(a), nih = P.z[(size_t)i * E1 + s + 1] - lo2(b);
+    const float2 njl = P.z[(size_t)j * E1 + s] - hi2(a), njh = P.z[(size_t)j * E1 + s + 1] - hi2(b);
+    float2 xil, xih, xjl, xjh;
+    const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+    coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, P.radius[i] + P.radius[j], P.rho,
+                   xil, xih, xjl, xjh);
+    P.xlo[fid] = pack(xil, xjl);
+    P.xhi[fid] = pack(xih, xjh);
+    if (!pin_lo) {
+      contribute(P, i, s, xil + lo2(a));
+      contribute(P, j, s, xjl + hi2(a));
+    }
+    if (!pin_hi) {
+      contribute(P, i, s + 1, xih + lo2(b));
+      contribute(P, j, s + 1, xjh + hi2(b));
+    }
+  }
+}
+
+// Pass 3 (steps 5-6): z = sum(rho m) / sum(rho) per free break-point from the
+// fixed-point sums (every weight is rho0, so z is the mean of the incoming m;
+// no incoming weight means z is unchanged).  Clears the sums for the next
+// iteration.
 __global__ void consensus_kernel(Dev P) {
   const int nfree = (P.eta - 1) * P.p;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *P.work_count_next = 0u;
   float dz = 0.f;
+  bool bad = false;
   if (t < nfree) {
     const int sp = 1 + t / P.p;
     const int i = t - (sp - 1) * P.p;
-    const int A = i / TILE, a = i - A * TILE;
-    float mx = 0.f, my = 0.f, cnt = 0.f;
-    const float* lo = P.partial + (((size_t)sp * P.nt + A) * P.nt) * 6 * TILE + a;
-    const float* hi = P.partial + (((size_t)(sp - 1) * P.nt + A) * P.nt) * 6 * TILE + a;
-    for (int B = 0; B < P.nt; ++B) {
-      mx += lo[(B * 6 + 0) * TILE];
-      my += lo[(B * 6 + 1) * TILE];
-      cnt += lo[(B * 6 + 2) * TILE];
-    }
-    for (int B = 0; B < P.nt; ++B) {
-      mx += hi[(B * 6 + 3) * TILE];
-      my += hi[(B * 6 + 4) * TILE];
-      cnt += hi[(B * 6 + 5) * TILE];
-    }
-    const size_t zi = (size_t)i * (P.eta + 1) + sp;
-    const float2 zo = P.z[zi];
+    const size_t node = (size_t)i * (P.eta + 1) + sp;
+    const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
+    const unsigned cnt = P.accc[node];
+    P.accx[node] = 0ull;
+    P.accy[node] = 0ull;
+    P.accc[node] = 0u;
+    const float2 zo = P.z[node];
     float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
-    if (cnt > 0.f) zn = mk(mx / cnt, my / cnt);
-    P.z_next[zi] = zn;
-    dz = fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f ? maxabs2(zn - zo) : -1.f;
+    if (cnt > 0u) {
+      const double den = (double)P.fix[0] * (double)cnt;
+      zn = mk((float)((double)sx / den), (float)((double)sy / den));
+    }
+    P.z_next[node] = zn;
+    bad = (*P.status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
+    dz = bad ? 0.f : maxabs2(zn - zo);
   }
-  // a NaN anywhere makes the residual NaN (reported as PLAN_ENUMERIC)
-  const bool bad = dz < 0.f;
-  dz = warp_max(bad ? 0.f : dz);
+  // a NaN or overflow anywhere makes the residual NaN (reported as PLAN_ENUMERIC)
+  dz = warp_max(dz);
   const bool anybad = __any_sync(FULL, bad);
   if ((threadIdx.x & 31) == 0) {
     if (anybad) atomicMax(P.res_cur, 0x7fc00000u);
     else if (dz > 0.f) atomic_max_nonneg(P.res_cur, dz);
+  }
+}
+
+// Fixed-point scale of the consensus sums: the largest power of two with
+// 8 (L + 1) x (max incoming edges) x scale <= 2^62, L the largest coordinate
+// magnitude of the endpoints and walls.  One block.
+__global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
+  __shared__ float red[256];
+  float L = 0.f;
+  for (int k = threadIdx.x; k < P.p; k += blockDim.x)
+    L = fmaxf(L, fmaxf(maxabs2(start[k]), maxabs2(goal[k])));
+  for (int k = threadIdx.x; k < P.nw; k += blockDim.x) {
+    const float4 w = P.walls[k];
+    L = fmaxf(L, fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w))));
+  }
+  red[threadIdx.x] = L;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * P.nw;
+    const double bound = 8.0 * ((double)red[0] + 1.0);
+    int e = (int)floor(log2(4.611686018427388e18 / (bound * edges)));
+    e = e < 8 ? 8 : (e > 60 ? 60 : e);
+    float* f = const_cast<float*>(P.fix);
+    f[0] = ldexpf(1.f, e);
+    f[1] = (float)bound;
   }
 }
 
@@ -624,7 +736,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, tiles;
-  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, partial, res, status, count;
+  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wcount, accx, accy, accc, fix,
+      res, status, count;
   size_t total;
 };
 
@@ -659,7 +772,12 @@ Layout layout_for(const plan_config* c) {
   L.uwall = take(nw * eta * p * 16);
   L.xwall = take(nw * eta * p * 16);
   L.wbits = take(nw * eta * nt * 4);
-  L.partial = take(eta * nt * nt * 6 * TILE * 4);
+  L.work = take(slots * 4);
+  L.wcount = take(2 * 4);
+  L.accx = take(p * (eta + 1) * 8);
+  L.accy = take(p * (eta + 1) * 8);
+  L.accc = take(p * (eta + 1) * 4);
+  L.fix = take(2 * 4);
   L.res = take(4 * 4);
   L.status = take(4);
   L.count = take(16);
@@ -717,6 +835,9 @@ struct plan_s {
   bool own_ws;
   int k;
   int cur;  // which z buffer holds z^k
+  int prox_grid = 0;  // CTAs of the minimizer pass (resident CTAs per SM x SMs)
+  cudaStream_t side = nullptr;   // second stream for the kinetic and wall factors
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned* h_res;  // pinned host word for residual readback
   std::vector<float> h_radius;
   std::vector<float> h_walls;
@@ -749,7 +870,13 @@ struct plan_s {
     P.ukin = at<float4>(L.ukin); P.xkin = at<float4>(L.xkin);
     P.uwall = at<float4>(L.uwall); P.xwall = at<float4>(L.xwall);
     P.wbits = at<uint32_t>(L.wbits);
-    P.partial = at<float>(L.partial);
+    P.work = at<uint32_t>(L.work);
+    P.work_count = at<unsigned>(L.wcount) + (kk & 1);
+    P.work_count_next = at<unsigned>(L.wcount) + ((kk + 1) & 1);
+    P.accx = at<unsigned long long>(L.accx);
+    P.accy = at<unsigned long long>(L.accy);
+    P.accc = at<unsigned>(L.accc);
+    P.fix = at<float>(L.fix);
     unsigned* res = at<unsigned>(L.res);
     P.res_cur = res + (kk & 1);
     P.res_prev = kk > 0 ? res + ((kk - 1) & 1) : nullptr;
@@ -760,14 +887,44 @@ struct plan_s {
 
 namespace {
 
+cudaError_t clear_sums(plan_t h) {
+  const size_t nodes = (size_t)h->p * (h->eta + 1);
+  cudaError_t e = cudaMemsetAsync(h->at<void>(h->L.accx), 0, nodes * 8, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->at<void>(h->L.accy), 0, nodes * 8, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->at<void>(h->L.accc), 0, nodes * 4, h->stream);
+  return e;
+}
+
 plan_status run_iteration(plan_t h) {
+  if (h->prox_grid == 0) {
+    int dev = 0, sms = 0, nb = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, prox_kernel, 256, 0));
+    h->prox_grid = std::max(1, sms * std::max(nb, 1));
+  }
   Dev P = h->dev(h->k);
   const unsigned grid = (unsigned)((size_t)h->eta * h->ntp);
-  factor_kernel<<<grid, THREADS, 0, h->stream>>>(P);
+  const int seg_threads = 32 * std::min(1 + h->nw, WARPS);
+  if (h->side) {
+    // kinetic and wall factors run beside the collision passes
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    segment_kernel<<<h->eta * h->nt, seg_threads, 0, h->side>>>(P);
+    CK(cudaEventRecord(h->ev_join, h->side));
+  } else {
+    segment_kernel<<<h->eta * h->nt, seg_threads, 0, h->stream>>>(P);
+  }
+  if (P.dense) test_kernel<true><<<grid, 32 * TEST_WARPS, 0, h->stream>>>(P);
+  else test_kernel<false><<<grid, 32 * TEST_WARPS, 0, h->stream>>>(P);
+  prox_kernel<<<h->prox_grid, 256, 0, h->stream>>>(P);
+  if (h->side) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  // the consensus kernel also clears the next iteration's worklist counter, so
+  // it runs even when there is no free break-point (eta = 1)
   const int nfree = (h->eta - 1) * h->p;
-  if (nfree > 0) consensus_kernel<<<(nfree + 255) / 256, 256, 0, h->stream>>>(P);
+  consensus_kernel<<<std::max(1, (nfree + 63) / 64), 64, 0, h->stream>>>(P);
   CK(cudaGetLastError());
-  if (nfree > 0) h->cur ^= 1;
+  if (h->eta > 1) h->cur ^= 1;
   h->k += 1;
   return PLAN_OK;
 }
@@ -842,7 +999,10 @@ plan_status plan_reset(plan_t h) {
     if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, (size_t)h->nw * h->eta * h->p * 16, h->stream));
   }
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
+  CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
+  fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
   const int n = std::max(h->p * (h->eta + 1), h->eta * h->p);
   reset_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(P, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1),
                                                       h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -915,6 +1075,12 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
     delete h;
     return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
   }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    plan_destroy(h);
+    return fail(PLAN_ECUDA, "stream or event creation failed");
+  }
   st = upload_inputs(h, start, goal, radius, cost_w, walls);
   if (st == PLAN_OK) st = plan_reset(h);
   if (st != PLAN_OK) {
@@ -928,8 +1094,12 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
 void plan_destroy(plan_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_res) cudaFreeHost(h->h_res);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
 }
 
@@ -944,6 +1114,7 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
   endpoints_kernel<<<(h->p + 255) / 256, 256, 0, h->stream>>>(
       h->p, h->eta, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1), h->at<float2>(h->L.start),
       h->at<float2>(h->L.goal));
+  fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
   CK(cudaGetLastError());
   // the caller's host buffers may be reused once this returns
   CK(cudaStreamSynchronize(h->stream));
@@ -1027,6 +1198,10 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
     import_wbits_kernel<<<(words * 32 + 255) / 256, 256, 0, h->stream>>>(P);
   }
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
+  CK(clear_sums(h));
+  CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
+  fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
   CK(cudaGetLastError());
   return PLAN_OK;
 }

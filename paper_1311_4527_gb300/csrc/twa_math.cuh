@@ -30,10 +30,11 @@
 // m_a / m_b are closed form: the arc point closest in angle to a (or b).
 //
 // Capsule (wall) regions use the same hinge energy with
-// h(n) = max(<xL,n>, <xR,n>) + r; candidates are the two kink directions,
-// per end-circle the global minimiser of its both-stretched piece and the
-// single-hinge directions, plus a 128-direction scan refined by golden
-// section search.
+// h(n) = max(<xL,n>, <xR,n>) + r, which is the disk energy of one end circle
+// on each half-plane of directions.  The global minimum is at one of the two
+// kink directions or at a local minimum of one end circle's energy: a local
+// minimum of its both-stretched piece (global or local-nonglobal, both from
+// the secular equation) or a single-hinge direction.  All are candidates.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -41,7 +42,13 @@
 
 namespace twa {
 
-#define TWA_DEV __device__ __forceinline__
+// Host and device: the same FP32 code is also compiled into a host-side test
+// harness (tests/minimizer_harness.cu) that compares it with the FP64 oracle.
+#define TWA_DEV __host__ __device__ __forceinline__
+#define TWA_NOINLINE __host__ __device__ __noinline__
+#ifndef TWA_ITER_HOOK
+#define TWA_ITER_HOOK(kind)
+#endif
 
 TWA_DEV float2 mk(float x, float y) { return make_float2(x, y); }
 TWA_DEV float2 operator+(float2 a, float2 b) { return mk(a.x + b.x, a.y + b.y); }
@@ -54,6 +61,24 @@ TWA_DEV float2 perp(float2 a) { return mk(-a.y, a.x); }
 TWA_DEV float2 normalized(float2 a) {
   float n = hypotf(a.x, a.y);
   return n > 0.f ? mk(a.x / n, a.y / n) : mk(1.f, 0.f);
+}
+
+// Fast division and reciprocal square root for the inner iterations of the
+// secular equations, which correct their own rounding; results use the
+// accurate operations.  The host build (test harness) uses the plain ones.
+TWA_DEV float fdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+TWA_DEV float frsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.f / sqrtf(x);
+#endif
 }
 
 // Angle of a unit vector in [0, 2 pi): the tie-break order of directions.
@@ -136,7 +161,7 @@ TWA_DEV float hinge_E(float2 a, float2 b, float wl, float wh, float R, float2 n)
 
 // Global minimiser(s) of f(n) = wl (R - <a,n>)^2 + wh (R - <b,n>)^2 on the
 // unit circle.  Writes 1 or 2 directions (2 only for exact ties).
-__device__ __noinline__ int trs_global(float2 a, float2 b, float wl, float wh, float R,
+TWA_NOINLINE int trs_global(float2 a, float2 b, float wl, float wh, float R,
                                        float2* out) {
   float m11 = wl * a.x * a.x + wh * b.x * b.x;
   float m22 = wl * a.y * a.y + wh * b.y * b.y;
@@ -161,22 +186,26 @@ __device__ __noinline__ int trs_global(float2 a, float2 b, float wl, float wh, f
     out[1] = (-n1) * e1 + n2 * e2;
     return 2;
   }
-  // root of h(t) = phi(t)^{-1/2} - 1 (increasing) with phi = (A1/t)^2 + (A2/(d+t))^2
+  // Root of h(t) = phi(t)^{-1/2} - 1 with phi = (A1/t)^2 + (A2/(d+t))^2.
+  // 1/|n(t)| is concave and increasing (Moré-Sorensen), so Newton from the
+  // left bracket end, where h <= 0, climbs monotonically to the root.
   float lo = fmaxf(fmaxf(A1, R * Sn - d), 0.f), hi = R * Sn;
   if (lo > hi) lo = hi;
-  float t = hi;
-  for (int it = 0; it < 60; ++it) {
-    if (!(t > 0.f)) t = 0.5f * (lo + hi);
-    float q1 = A1 / t, q2 = A2 / (d + t);
+  float t = lo > 0.f ? lo : 0.5f * hi;
+  for (int it = 0; it < 40; ++it) {
+    TWA_ITER_HOOK(0);
+    float it_ = fdiv(1.f, t), id = fdiv(1.f, d + t);
+    float q1 = A1 * it_, q2 = A2 * id;
     float phi = q1 * q1 + q2 * q2;
-    float ip = 1.f / sqrtf(phi);
+    float ip = frsqrt(phi);
     float h = ip - 1.f;
     if (h > 0.f) hi = t; else lo = t;
     if (h == 0.f) break;
-    float dh = ip * ip * ip * (q1 * q1 / t + q2 * q2 / (d + t));
-    float tn = t - h / dh;
+    float dh = ip * ip * ip * (q1 * q1 * it_ + q2 * q2 * id);
+    float tn = t - fdiv(h, dh);
     if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
-    if (fabsf(tn - t) <= 2e-7f * t || hi - lo <= 2e-7f * hi) { t = tn; break; }
+    // FP32 noise in h limits t to ~1e-7 relative; stop at 1e-6
+    if (fabsf(tn - t) <= 1e-6f * t || hi - lo <= 1e-6f * hi) { t = tn; break; }
     t = tn;
   }
   float p1 = (t > 0.f) ? R * s1 / t : copysignf(INFINITY, s1);
@@ -191,6 +220,80 @@ __device__ __noinline__ int trs_global(float2 a, float2 b, float wl, float wh, f
   }
   out[0] = normalized(n1 * e1 + n2 * e2);
   return 1;
+}
+
+// The other stationary points of f: mu in (lambda1, lambda2), where
+// t = mu - lambda1 solves (A1/t)^2 + (A2/(d - t))^2 = 1.  The left side is
+// convex on (0, d) with its minimum at t_m = d A1^(2/3) / (A1^(2/3) + A2^(2/3)),
+// so there are 0 or 2 roots (one is the local-but-not-global minimum); with
+// s1 = 0 or s2 = 0 the stationary points at mu = lambda1 or lambda2 are added.
+// Writes up to 4 directions; used by the wall minimizer, whose capsule
+// restricts each end circle to a half-plane of directions.
+TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, float2* out) {
+  float m11 = wl * a.x * a.x + wh * b.x * b.x;
+  float m22 = wl * a.y * a.y + wh * b.y * b.y;
+  float m12 = wl * a.x * a.y + wh * b.x * b.y;
+  float2 S = mk(wl * a.x + wh * b.x, wl * a.y + wh * b.y);
+  float hd = 0.5f * (m11 - m22);
+  float disc = hypotf(hd, m12);
+  float d = 2.f * disc;
+  if (!(d > 0.f)) return 0;
+  float2 e2 = (hd >= 0.f) ? normalized(mk(hd + disc, m12)) : normalized(mk(m12, disc - hd));
+  float2 e1 = perp(e2);
+  float s1 = dot(S, e1), s2 = dot(S, e2);
+  float A1 = R * fabsf(s1), A2 = R * fabsf(s2);
+  int n = 0;
+  if (A1 == 0.f && A2 == 0.f) return 0;
+  if (A2 == 0.f) {  // hard case at mu = lambda2, and the root t = A1
+    if (A1 < d) {
+      float n1 = -R * s1 / d;
+      float n2 = sqrtf(fmaxf(0.f, 1.f - n1 * n1));
+      out[n++] = n1 * e1 + n2 * e2;
+      out[n++] = n1 * e1 + (-n2) * e2;
+      out[n++] = (s1 > 0.f ? -1.f : 1.f) * e1;
+    }
+    return n;
+  }
+  if (A1 == 0.f) {  // the root t = d - A2
+    if (A2 < d) out[n++] = (s2 > 0.f ? 1.f : -1.f) * e2;
+    return n;
+  }
+  float c1 = cbrtf(A1 * A1), c2 = cbrtf(A2 * A2);
+  float tm = d * c1 / (c1 + c2);
+  float phim = (A1 / tm) * (A1 / tm) + (A2 / (d - tm)) * (A2 / (d - tm));
+  if (!(phim <= 1.f)) return 0;
+  for (int side = 0; side < 2; ++side) {
+    // h(t) = phi(t)^(-1/2) - 1 is increasing on (0, tm] and decreasing on
+    // [tm, d); each root is approached from its pole side, where h <= 0 (at
+    // t = A1, resp. t = d - A2), so that the Newton steps move monotonically.
+    float lo = side ? tm : 0.f, hi = side ? d : tm;
+    float t = side ? fminf(fmaxf(d - A2, tm), d) : fmaxf(fminf(A1, tm), 0.f);
+    if (!(t > lo && t < hi)) t = 0.5f * (lo + hi);
+    for (int it = 0; it < 40; ++it) {
+      TWA_ITER_HOOK(1);
+      float it_ = fdiv(1.f, t), id = fdiv(1.f, d - t);
+      float q1 = A1 * it_, q2 = A2 * id;
+      float phi = q1 * q1 + q2 * q2;
+      float ip = frsqrt(phi);
+      float h = ip - 1.f;
+      bool right = side ? (h < 0.f) : (h > 0.f);  // root lies left of t
+      if (right) hi = t; else lo = t;
+      if (h == 0.f || hi - lo <= 1e-6f * hi) break;
+      float dphi = -2.f * (q1 * q1 * it_) + 2.f * (q2 * q2 * id);
+      float dh = -0.5f * ip * ip * ip * dphi;
+      float tn = (dh != 0.f) ? t - fdiv(h, dh) : 0.5f * (lo + hi);
+      if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+      const bool done = fabsf(tn - t) <= 1e-6f * fmaxf(t, tn);
+      t = tn;
+      if (done) break;
+    }
+    float p1 = -R * s1 / t, p2 = R * s2 / (d - t);
+    float n1, n2;
+    if (fabsf(p1) <= fabsf(p2)) { n1 = p1; n2 = copysignf(sqrtf(fmaxf(0.f, 1.f - p1 * p1)), p2); }
+    else { n2 = p2; n1 = copysignf(sqrtf(fmaxf(0.f, 1.f - p2 * p2)), p1); }
+    out[n++] = normalized(n1 * e1 + n2 * e2);
+  }
+  return n;
 }
 
 // Tangent normals n with <q, n> = R from a point q (|q| >= R).
@@ -216,7 +319,7 @@ TWA_DEV float2 arc_argmax(float2 q, float R, float2 w) {
 
 // Collision minimizer core: disk of radius R at the origin, finite equal or
 // unequal weights, neither end pinned.  (a, b): targets; (vl, vh): result.
-__device__ __noinline__ void disk_prox_free(float2 a, float2 b, float wl, float wh, float R,
+TWA_NOINLINE void disk_prox_free(float2 a, float2 b, float wl, float wh, float R,
                                             float2& vl, float2& vh) {
   Best best;
   best.init();
@@ -239,7 +342,7 @@ __device__ __noinline__ void disk_prox_free(float2 a, float2 b, float wl, float 
 
 // One end pinned at q (weight infinite): the free end's target is w.  The
 // separating direction ranges over the arc {<q,n> >= R}.
-__device__ __noinline__ float2 disk_prox_pinned(float2 q, float2 w, float R) {
+TWA_NOINLINE float2 disk_prox_pinned(float2 q, float2 w, float R) {
   float2 n = arc_argmax(q, R, w);
   return w + fmaxf(R - dot(w, n), 0.f) * n;
 }
@@ -258,19 +361,13 @@ TWA_DEV float capsule_E(float2 a, float2 b, float wl, float wh, float2 c0, float
   return 0.5f * wl * ga * ga + 0.5f * wh * gb * gb;
 }
 
-TWA_DEV float2 dir(float th) {
-  float s, c;
-  sincosf(th, &s, &c);
-  return mk(c, s);
-}
-
-__device__ __noinline__ void capsule_prox_free(float2 a, float2 b, float wl, float wh, float2 c0,
+TWA_NOINLINE void capsule_prox_free(float2 a, float2 b, float wl, float wh, float2 c0,
                                                float2 c1, float r, float2& vl, float2& vh) {
   Best best;
   best.init();
   best.offer(mk(1.f, 0.f), capsule_E(a, b, wl, wh, c0, c1, r, mk(1.f, 0.f)));
   float2 e = c1 - c0;
-  if (e.x != 0.f || e.y != 0.f) {
+  if (e.x != 0.f || e.y != 0.f) {  // kinks: both end circles give the same support
     float2 k0 = normalized(perp(e));
     best.offer(k0, capsule_E(a, b, wl, wh, c0, c1, r, k0));
     best.offer(-k0, capsule_E(a, b, wl, wh, c0, c1, r, -k0));
@@ -278,8 +375,10 @@ __device__ __noinline__ void capsule_prox_free(float2 a, float2 b, float wl, flo
   for (int ci = 0; ci < 2; ++ci) {
     float2 cc = ci ? c1 : c0;
     float2 ac = a - cc, bc = b - cc;
-    float2 t[2];
+    float2 t[4];
     int nt = trs_global(ac, bc, wl, wh, r, t);
+    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]));
+    nt = trs_local(ac, bc, wl, wh, r, t);
     for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]));
     if (dot(ac, ac) > 0.f) {
       float2 n = normalized(ac);
@@ -290,26 +389,6 @@ __device__ __noinline__ void capsule_prox_free(float2 a, float2 b, float wl, flo
       best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n));
     }
   }
-  // scan + golden-section refinement of the best sampled direction
-  const int NS = 128;
-  const float step = 6.283185307179586f / NS;
-  float bestE = INFINITY, bestT = 0.f;
-  for (int k = 0; k < NS; ++k) {
-    float th = k * step;
-    float E = capsule_E(a, b, wl, wh, c0, c1, r, dir(th));
-    if (E < bestE) { bestE = E; bestT = th; }
-  }
-  float lo = bestT - step, hi = bestT + step;
-  const float g = 0.6180339887498949f;
-  float x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
-  float f1 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x1));
-  float f2 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x2));
-  for (int it = 0; it < 40; ++it) {
-    if (f1 <= f2) { hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x1)); }
-    else { lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = capsule_E(a, b, wl, wh, c0, c1, r, dir(x2)); }
-  }
-  float2 ng = dir(0.5f * (lo + hi));
-  best.offer(ng, capsule_E(a, b, wl, wh, c0, c1, r, ng));
   float2 n = best.n;
   float h = capsule_h(c0, c1, r, n);
   vl = a + fmaxf(h - dot(a, n), 0.f) * n;
@@ -320,7 +399,7 @@ __device__ __noinline__ void capsule_prox_free(float2 a, float2 b, float wl, flo
 // from q to both end circles, the kinks, and the single-hinge directions;
 // only directions that still separate q from the capsule are kept.
 // Returns false if no candidate separates q (q inside the capsule).
-__device__ __noinline__ bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, float r,
+TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, float r,
                                                  float2& vw) {
   float2 cand[8];
   int nc = 0;

@@ -1,0 +1,175 @@
+"""The CUDA path's FP32 minimizers (csrc/twa_math.cuh), compiled for the host
+by tests/minimizer_harness.cu, against the FP64 oracle on random inputs:
+feasible outputs and energies at the oracle's minimum up to FP32 rounding.
+CPU only (needs nvcc, which builds the harness)."""
+import ctypes
+import math
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import prox
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1311_4527_gb300", "csrc")
+FP = ctypes.POINTER(ctypes.c_float)
+
+
+@pytest.fixture(scope="module")
+def H():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp(prefix="twa_harness_")
+    so = os.path.join(d, "libharness.so")
+    subprocess.run([nvcc, "-x", "cu", "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                    "-I", CSRC, "-o", so, os.path.join(HERE, "minimizer_harness.cu")],
+                   check=True, capture_output=True)
+    lib = ctypes.CDLL(so)
+    lib.h_iters.restype = ctypes.c_longlong
+    return lib
+
+
+def _a(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    return a, a.ctypes.data_as(FP)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def _E(vl, vh, a, b, wl, wh):
+    return 0.5 * wl * np.sum((vl - a) ** 2) + 0.5 * wh * np.sum((vh - b) ** 2)
+
+
+def _disk(H, a, b, wl, wh, R):
+    A, pa = _a(a)
+    B, pb = _a(b)
+    out = np.zeros(4, np.float32)
+    H.h_disk_prox_free(pa, pb, ctypes.c_float(wl), ctypes.c_float(wh), ctypes.c_float(R),
+                       out.ctypes.data_as(FP))
+    return out[:2].astype(np.float64), out[2:].astype(np.float64)
+
+
+def _capsule(H, a, b, wl, wh, c0, c1, r):
+    A, pa = _a(a)
+    B, pb = _a(b)
+    C0, p0 = _a(c0)
+    C1, p1 = _a(c1)
+    out = np.zeros(4, np.float32)
+    H.h_capsule_prox_free(pa, pb, ctypes.c_float(wl), ctypes.c_float(wh), p0, p1, ctypes.c_float(r),
+                          out.ctypes.data_as(FP))
+    return out[:2].astype(np.float64), out[2:].astype(np.float64)
+
+
+def _tol(e, scale):
+    # FP32 rounding of positions of size `scale` costs ~1e-6 scale in each
+    # displacement, i.e. ~1e-6 scale sqrt(E) in energy
+    return 1e-5 * e + 4e-6 * scale * math.sqrt(e) + 1e-10
+
+
+def test_disk_minimizer_matches_the_oracle(H):
+    rng = np.random.default_rng(21)
+    zero = np.zeros(2)
+    n = 0
+    for _ in range(3000):
+        R = float(np.float32(rng.uniform(0.2, 1.0)))
+        a, b = _f32(rng.normal(size=(2, 2)) * 0.8)
+        if prox.dist_point_segment(zero, a, b) >= R:
+            continue
+        wl, wh = (0.5, 0.5) if n % 2 else tuple(_f32(rng.uniform(0.2, 3.0, size=2)))
+        vl, vh = _disk(H, a, b, wl, wh, R)
+        ol, oh, _ = prox.region_prox(a, b, wl, wh, zero, zero, R)
+        assert prox.dist_point_segment(zero, vl, vh) >= R * (1 - 1e-6)
+        e_g, e_o = _E(vl, vh, a, b, wl, wh), _E(ol, oh, a, b, wl, wh)
+        assert e_g <= e_o + _tol(e_o, 2.0), (a, b, wl, wh, R, e_g, e_o)
+        n += 1
+    assert n > 1000
+
+
+def test_capsule_minimizer_matches_the_oracle(H):
+    rng = np.random.default_rng(22)
+    n = 0
+    for k in range(2000):
+        if k % 2:
+            c0, c1 = _f32([0.0, 0.0]), _f32([40.0, 0.0])      # a long wall, agent near it
+            a = _f32([rng.uniform(1, 39), rng.uniform(0.0, 0.5)])
+            b = _f32(a + rng.normal(size=2) * 0.8)
+            scale = 40.0
+        else:
+            c0, c1 = _f32(rng.normal(size=(2, 2)))
+            a, b = _f32(rng.normal(size=(2, 2)) * 1.2)
+            scale = 3.0
+        r = float(np.float32(rng.uniform(0.1, 0.5)))
+        if prox.dist_segment_segment(a, b, c0, c1) >= r:
+            continue
+        wl, wh = tuple(_f32(rng.uniform(0.2, 3.0, size=2)))
+        vl, vh = _capsule(H, a, b, wl, wh, c0, c1, r)
+        ol, oh, _ = prox.region_prox(a, b, wl, wh, c0, c1, r)
+        assert prox.dist_segment_segment(vl, vh, c0, c1) >= r * (1 - 1e-5) - 1e-6 * scale
+        e_g, e_o = _E(vl, vh, a, b, wl, wh), _E(ol, oh, a, b, wl, wh)
+        assert e_g <= e_o + _tol(e_o, scale), (a, b, wl, wh, c0, c1, r, e_g, e_o)
+        n += 1
+    assert n > 500
+
+
+def test_pinned_minimizers_match_the_oracle(H):
+    rng = np.random.default_rng(23)
+    zero = np.zeros(2)
+    n = 0
+    for _ in range(2000):
+        R = float(np.float32(rng.uniform(0.2, 0.8)))
+        q = _f32(rng.normal(size=2) * 1.5)
+        w = _f32(rng.normal(size=2))
+        if np.linalg.norm(q) <= R * 1.001 or prox.dist_point_segment(zero, q, w) >= R:
+            continue
+        Q, pq = _a(q)
+        W, pw = _a(w)
+        out = np.zeros(2, np.float32)
+        H.h_disk_prox_pinned(pq, pw, ctypes.c_float(R), out.ctypes.data_as(FP))
+        v = out.astype(np.float64)
+        ol, oh, _ = prox.region_prox(q, w, math.inf, 1.0, zero, zero, R)
+        assert prox.dist_point_segment(zero, q, v) >= R * (1 - 1e-6)
+        e_g, e_o = 0.5 * np.sum((v - w) ** 2), 0.5 * np.sum((oh - w) ** 2)
+        assert e_g <= e_o + _tol(e_o, 2.0)
+        n += 1
+    assert n > 500
+
+
+def test_energy_minimizer_matches_the_oracle(H):
+    rng = np.random.default_rng(24)
+    for _ in range(500):
+        nl, nh = _f32(rng.normal(size=(2, 2)) * 10)
+        rho, c = float(np.float32(rng.uniform(0.1, 3))), float(np.float32(rng.uniform(0, 2)))
+        for pl, ph in ((0, 0), (1, 0), (0, 1)):
+            N1, p1 = _a(nl)
+            N2, p2 = _a(nh)
+            out = np.zeros(4, np.float32)
+            H.h_energy_prox(p1, p2, ctypes.c_float(rho), pl, ph, ctypes.c_float(c), out.ctypes.data_as(FP))
+            ol, oh = prox.energy_prox(nl, nh, math.inf if pl else rho, math.inf if ph else rho, c)
+            assert np.allclose(out[:2], ol, atol=2e-5 * 10) and np.allclose(out[2:], oh, atol=2e-5 * 10)
+
+
+def test_secular_iterations_stay_few(H):
+    """Newton on the concave secular function from the left converges in a
+    handful of steps (the latency of the minimizer pass)."""
+    rng = np.random.default_rng(25)
+    zero = np.zeros(2)
+    calls = iters = worst = 0
+    for _ in range(2000):
+        R = float(rng.uniform(0.2, 1.0))
+        a, b = rng.normal(size=(2, 2)) * 0.8
+        if prox.dist_point_segment(zero, a, b) >= R:
+            continue
+        H.h_reset_iters()
+        _disk(H, a, b, 0.5, 0.5, R)
+        k = H.h_iters(0)
+        iters += k
+        worst = max(worst, k)
+        calls += 1
+    assert iters / calls < 5 and worst <= 12
