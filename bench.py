@@ -1,20 +1,21 @@
-"""Benchmark of one TWA planner iteration (every collision, kinetic, position
-and wall factor, then the consensus and dual updates) on one GB300.
+"""Benchmark of the TWA trajectory planner on one GB300.
 
-Default workload: p=1024 agents in [0,40]^2 with 4 walls, eta=16 segments:
-8,380,416 collision + 16,384 kinetic + 65,536 wall + 2,048 position factors
-per iteration.  A step is one iteration; the metric is factor updates per
-second (every factor's minimizer plus its edge updates counts once).
+Headline: factor updates per second of one full TWA iteration (every
+collision, kinetic, position and wall factor, then the consensus and dual
+updates) on the p=1024, eta=16 random square with 4 walls: 8,380,416
+collision + 16,384 kinetic + 65,536 wall + 2,048 position factors per
+iteration.  A step is one iteration; every factor's minimizer plus its edge
+updates counts as one update.  Also reported: the dense-state mode (every u
+record streamed) against the HBM roofline, time to converge, the end-to-end
+call with host buffers, and the FP64 oracle on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--mode gated|dense] [--workload NAME]
 
 Under torchrun (N > 1) every rank plans its own replica of the workload
 (there is no exchange between instances); value is the sum over ranks.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -29,8 +30,13 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-METRIC = "factor-updates/s (one TWA iteration over every factor), 1 GB300"
+METRIC = "factor-updates/s and time-to-converge (1 GB300) vs FP64 CPU oracle; % HBM roofline"
 UNIT = "factor-updates/s"
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the current test kernels on square1024_eta16, from one single-pass ncu
+# capture of two launches each (profiles/test_kernel_traffic_square1024.md).
+TRAFFIC_SQUARE1024 = {"gated": 9.099e6, "dense": 482.39e6}
 
 
 def factor_counts(inst):
@@ -38,13 +44,18 @@ def factor_counts(inst):
     return dict(coll=eta * p * (p - 1) // 2, kin=eta * p, wall=inst.n_walls * eta * p, pos=2 * p)
 
 
-def dense_bytes_per_iter(inst):
-    """Algorithmic HBM bytes of one iteration under the dense state model:
-    per collision factor its 8-float u record read and written (64 B) plus 2
-    bits of activity; per kinetic or wall factor a 4-float u read and written
-    (32 B).  z and the consensus partials stay in L2 and are not counted."""
+def dense_coll_bytes(inst):
+    """Algorithmic HBM bytes of the collision test pass under the dense state
+    model: per collision factor its 8-float u record read and written (64 B)
+    plus 2 bits of activity (read and written)."""
     c = factor_counts(inst)
-    return c["coll"] * 64 + (c["kin"] + c["wall"]) * 32 + c["coll"] * 2 / 8
+    return c["coll"] * 64 + c["coll"] * 2 / 8
+
+
+def dense_bytes_per_iter(inst):
+    """... plus per kinetic or wall factor a 4-float u read and written."""
+    c = factor_counts(inst)
+    return dense_coll_bytes(inst) + (c["kin"] + c["wall"]) * 32
 
 
 def peaks():
@@ -52,9 +63,14 @@ def peaks():
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class Clocks:
@@ -102,6 +118,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(ms_local, units_local, world, dist=None, device=None):
+    """Whole-job numbers across ranks: the step time is the slowest rank's,
+    the units are summed.  Returns (ms_per_step, total_units)."""
+    if world == 1 or dist is None:
+        return ms_local, units_local
+    import torch
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0].item()), float(sm[1].item())
+
+
 def cpu_baseline(inst, budget_s=20.0):
     """The FP64 oracle, as it stands, on this host: whole iterations of the
     same workload, as many as fit the budget (at least one)."""
@@ -109,8 +139,7 @@ def cpu_baseline(inst, budget_s=20.0):
     prob = twa.Problem.from_instance(inst)
     st = twa.initial_state(prob)
     st, _ = twa.iterate(prob, st)  # untimed: reach a mid-solve iterate
-    c = factor_counts(inst)
-    total = sum(c.values())
+    total = sum(factor_counts(inst).values())
     n, t0 = 0, time.perf_counter()
     while True:
         st, _ = twa.iterate(prob, st)
@@ -125,20 +154,17 @@ def cpu_baseline(inst, budget_s=20.0):
 
 def run_reference(args, inst):
     """--impl reference: the FP64 oracle on the host cores, bounded."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     from oracle import twa
     prob = twa.Problem.from_instance(inst)
     st = twa.initial_state(prob)
-    c = factor_counts(inst)
-    total = sum(c.values())
-    for _ in range(args.warmup if args.warmup <= 1 else 1):
-        st, _ = twa.iterate(prob, st)
+    total = sum(factor_counts(inst).values())
+    st, _ = twa.iterate(prob, st)  # one untimed warm-up iteration
     budget = 150.0
     times = []
     t_all = time.perf_counter()
-    for k in range(args.steps):
+    for _ in range(args.steps):
         t0 = time.perf_counter()
         st, _ = twa.iterate(prob, st)
         times.append(time.perf_counter() - t0)
@@ -147,12 +173,11 @@ def run_reference(args, inst):
     n = len(times)
     ms = 1e3 * sum(times) / n
     value = total / (ms / 1e3)
-    sample = (f"{n} of {args.steps} requested iterations of {inst.name} (capped at {budget:.0f} s), "
-              f"after {min(args.warmup, 1)} untimed warm-up iteration(s)")
+    sample = (f"{n} of {args.steps} requested iterations of {inst.name} (capped at {budget:.0f} s) "
+              f"after 1 untimed warm-up iteration; numpy FP64, single thread")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": n,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": inst.name, "p": inst.p, "eta": inst.eta,
                        "walls": inst.n_walls, "factors_per_step": total},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -161,13 +186,70 @@ def run_reference(args, inst):
     print(json.dumps(line), flush=True)
 
 
+def timed_iterations(pl, stream, steps, flush):
+    """Each iteration timed alone with CUDA events on the planner's stream,
+    L2 flushed (256 MB write) before it.  Returns ms per iteration."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        pl.iterate(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def kernel_times(pl, stream, steps, flush):
+    """Average per-kernel ms over `steps` iterations (events inside the
+    library, on the streams the kernels run on), L2 flushed before each."""
+    import torch
+    pl.profile_start()
+    for k in range(steps):
+        flush.fill_(float(k))
+        pl.iterate(1)
+    torch.cuda.synchronize()
+    return pl.profile_stop()
+
+
+def time_to_converge(pk, names, oracle_names):
+    """plan_solve to the workload's tolerance (or its iteration cap) on the
+    GPU; the FP64 oracle's own solve time for the small workloads."""
+    import torch
+    from oracle import twa
+    out = {}
+    for name in names:
+        inst = workloads.by_name(name)
+        prob = twa.Problem.from_instance(inst)
+        with pk.Planner.from_instance(inst, check_every=10) as pl:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            conv, it, res = pl.solve()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            z = pl.trajectory().cpu().numpy().astype(np.float64)
+        coll, wall = twa.min_clearance(prob, z)
+        rec = {"converged": conv, "iterations": it, "residual": res, "tol": inst.tol,
+               "gpu_ms": 1e3 * dt, "total_cost": twa.total_cost(prob, z),
+               "min_clearance_ratio": coll}
+        if name in oracle_names:
+            t0 = time.perf_counter()
+            _, oit, ores = twa.solve(prob, inst.tol, inst.max_iter)
+            rec.update(oracle_ms=1e3 * (time.perf_counter() - t0), oracle_iterations=oit,
+                       oracle_cores=1)
+        out[name] = rec
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="gated", choices=["gated", "dense"])
+    ap.add_argument("--mode", default="gated", choices=["gated", "dense"],
+                    help="state mode of the headline measurement")
     ap.add_argument("--workload", default="square1024_eta16",
                     help="a named workload, or 'square' for a random square of --p agents")
     ap.add_argument("--p", type=int, default=768)
@@ -176,12 +258,13 @@ def main():
     ap.add_argument("--start-iter", type=int, default=20,
                     help="untimed iterations before warm-up (a mid-solve iterate)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: no dense companion, convergence or e2e legs")
     args = ap.parse_args()
     if args.workload == "square":
         inst = workloads.small_square(args.p, args.eta, seed=args.seed)
     else:
         inst = workloads.by_name(args.workload)
-
     if args.impl == "reference":
         return run_reference(args, inst)
 
@@ -196,73 +279,63 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    warmup = max(3, args.warmup)
-
-    flags = pk.PLAN_DENSE_STATE if args.mode == "dense" else 0
-    pl = pk.Planner.from_instance(inst, flags=flags)
     stream = torch.cuda.current_stream(dev)
-    pl.iterate(args.start_iter)
-    for _ in range(warmup):
-        pl.iterate(1)
-    # L2 flush buffer: 2 x the 129 MB L2, written between timed iterations
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    warmup = max(3, args.warmup)
+    hbm_peak, sm_max, peak_kind = peaks()
     c = factor_counts(inst)
     total = sum(c.values())
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def prepared(flags):
+        pl = pk.Planner.from_instance(inst, flags=flags)
+        pl.iterate(args.start_iter)
+        for _ in range(warmup):
+            pl.iterate(1)
+        torch.cuda.synchronize()
+        return pl
+
+    head_flags = pk.PLAN_DENSE_STATE if args.mode == "dense" else 0
+    pl = prepared(head_flags)
     if world > 1:
         dist.barrier()
+    torch.cuda.synchronize()
     clocks = Clocks(local)
     time.sleep(0.3)
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        pl.iterate(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    ms_local = timed_iterations(pl, stream, args.steps, flush)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    per = [a.elapsed_time(b) for a, b in ev]  # ms, each iteration between events
-    ms_step = sum(per) / len(per)
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    ms_step, units = aggregate(ms_local, total, world, dist if world > 1 else None, dev)
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_step = float(t.item())
-    value = total * world / (ms_step / 1e3)
+    value = units / (ms_step / 1e3)
+    kt = kernel_times(pl, stream, min(args.steps, 20), flush)
     info = pl.info()
+    pl.close()
 
-    # kernel-level timing of the dominant kernel on the same stream: the
-    # factor kernel alone, via a second planner call pattern (iterate = factor
-    # + consensus); the consensus kernel is timed by the profile summary
-    # under profiles/, here both are attributed to the iteration.
-    hbm_peak, peak_kind = peaks()
-    dense_b = dense_bytes_per_iter(inst)
-
-    # end-to-end: host endpoints in, one iteration, host trajectory out
-    e2e_steps = max(5, min(args.steps, 20))
-    start_h = torch.from_numpy(inst.start.astype(np.float32)).pin_memory()
-    goal_h = torch.from_numpy(inst.goal.astype(np.float32)).pin_memory()
-    z_h = torch.empty((inst.p, inst.eta + 1, 2), dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        pl.set_endpoints(start_h.numpy(), goal_h.numpy())
-        pl.iterate(1)
-        pl.trajectory_host(z_h.numpy())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": total * world / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(2 * inst.p * 2 * 4),
-           "d2h_bytes_per_step": int(inst.p * (inst.eta + 1) * 2 * 4),
-           "ms_per_step": e2e_ms,
-           "path": "plan_set_endpoints(host) + plan_iterate(1) + plan_get_trajectory(host)"}
+    def roofline_for(mode, ktimes):
+        if mode == "dense":
+            b = dense_coll_bytes(inst)
+            t = ktimes["test"] / 1e3
+            ach = b / t / 1e9
+            traffic = TRAFFIC_SQUARE1024["dense"] if inst.name == "square1024_eta16" else None
+            return {"bound": "hbm", "kernel": "test_kernel<dense>", "achieved": ach,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic,
+                    "peak_kind": peak_kind,
+                    "note": f"algorithmic bytes {b:.4g} per launch (64 B u record read+written "
+                            f"and 2 bits per collision factor) / live kernel time "
+                            f"{ktimes['test'] * 1e3:.1f} us"}
+        flops = 30.0 * c["coll"]
+        t = ktimes["test"] / 1e3
+        ach = flops / t / 1e12
+        pk_t = fp32_peak_tflops(sm_max)
+        traffic = TRAFFIC_SQUARE1024["gated"] if inst.name == "square1024_eta16" else None
+        return {"bound": "alu", "kernel": "test_kernel<gated>", "achieved": ach, "peak": pk_t,
+                "unit": "TFLOP/s", "frac": ach / pk_t, "traffic": traffic,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "note": f"algorithmic 30 FP32 flops per collision factor (the exact distance "
+                        f"test) / live kernel time {ktimes['test'] * 1e3:.1f} us; the early-out "
+                        f"skips most of them, the kernel is bound by instruction issue"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -271,33 +344,61 @@ def main():
         "config": {"workload": inst.name, "p": inst.p, "eta": inst.eta, "walls": inst.n_walls,
                    "factors_per_step": total, "coll_factors": c["coll"], "kin_factors": c["kin"],
                    "wall_factors": c["wall"], "pos_factors": c["pos"], "mode": args.mode,
-                   "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) before every timed iteration",
+                   "parallelism": f"replicas{world}",
+                   "l2": "flushed (256 MB write) before every timed iteration",
                    "start_iter": args.start_iter,
                    "active_coll_last": info["active_coll"], "active_wall_last": info["active_wall"]},
         "coll_factor_updates_per_s": c["coll"] * world / (ms_step / 1e3),
+        "kernel_ms": kt,
         "wall_s": wall,
         "clocks": clk,
-        "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 4 * args.steps,
+        "roofline": roofline_for(args.mode, kt),
     }
-    if args.mode == "dense":
-        ach = dense_b / (ms_step / 1e3) / 1e9
-        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": ach / hbm_peak, "traffic": None,
-                            "note": f"dense-model bytes {dense_b:.4g}/iteration over the whole "
-                                    f"iteration time (factor + consensus kernels); peak {peak_kind}"}
-    else:
-        ach = dense_b / (ms_step / 1e3) / 1e9
-        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": ach / hbm_peak, "traffic": None,
-                            "note": "dense-model bytes over the gated kernel's time: the gated "
-                                    "state skips the zero u records, so this is an equivalent "
-                                    f"rate, not DRAM traffic; peak {peak_kind}"}
+    if not args.quick:
+        # the other state mode, same workload, same timing rules
+        other = "gated" if args.mode == "dense" else "dense"
+        pl = prepared(pk.PLAN_DENSE_STATE if other == "dense" else 0)
+        ms_o = timed_iterations(pl, stream, args.steps, flush)
+        kt_o = kernel_times(pl, stream, min(args.steps, 20), flush)
+        pl.close()
+        ms_o, units_o = aggregate(ms_o, total, world, dist if world > 1 else None, dev)
+        b = dense_bytes_per_iter(inst)
+        line[other] = {"ms_per_step": ms_o, "value": units_o / (ms_o / 1e3), "kernel_ms": kt_o,
+                       "roofline": roofline_for(other, kt_o),
+                       "iteration_hbm_frac": (b / (ms_o / 1e3) / 1e9) / hbm_peak
+                       if other == "dense" else None}
+
+        # end to end through the C ABI with host buffers: new endpoints in,
+        # one iteration, the trajectory back to pinned host memory
+        pl = prepared(head_flags)
+        e2e_steps = max(5, min(args.steps, 20))
+        start_h = torch.from_numpy(inst.start.astype(np.float32)).pin_memory()
+        goal_h = torch.from_numpy(inst.goal.astype(np.float32)).pin_memory()
+        z_h = torch.empty((inst.p, inst.eta + 1, 2), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pl.set_endpoints(start_h.numpy(), goal_h.numpy())
+            pl.iterate(1)
+            pl.trajectory_host(z_h.numpy())
+        torch.cuda.synchronize()
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+        pl.close()
+        e2e_ms, units_e = aggregate(e2e_ms, total, world, dist if world > 1 else None, dev)
+        line["e2e"] = {"value": units_e / (e2e_ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(2 * inst.p * 2 * 4),
+                       "d2h_bytes_per_step": int(inst.p * (inst.eta + 1) * 2 * 4),
+                       "ms_per_step": e2e_ms,
+                       "path": "plan_set_endpoints(host) + plan_iterate(1) + "
+                               "plan_get_trajectory(host), pinned buffers"}
+    if rank == 0 and world == 1 and not args.quick:
+        line["time_to_converge"] = time_to_converge(
+            pk, ["circle4_eta4", "circle100_eta8", "square1024_eta16"], ["circle4_eta4"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    pl.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -159,6 +159,15 @@ typedef struct {
 /* Sizes and counters (synchronises to count the active factors). */
 plan_status plan_get_info(plan_t plan, plan_info* info);
 
+/* Per-kernel timing of the next iterations (CUDA events on the streams the
+ * kernels run on).  enable = 1 starts collecting (and synchronises once per
+ * iteration, so timings are taken without overlap between iterations);
+ * enable = 0 stops and writes the average milliseconds per iteration of the
+ * four kernels to ms[0..3] = {collision test, collision minimizer, kinetic and
+ * wall factors, consensus} and their count to *iterations (either may be
+ * NULL).  Errors: PLAN_EINVAL, PLAN_ECUDA. */
+plan_status plan_profile(plan_t plan, int enable, float* ms, int* iterations);
+
 /* Gradient of a trajectory loss through unrolled iterations (not built yet:
  * returns PLAN_EUNSUPPORTED). */
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,

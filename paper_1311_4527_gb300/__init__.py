@@ -34,7 +34,7 @@ STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: 
 EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_set_endpoints",
                     "plan_iterate", "plan_solve", "plan_get_trajectory", "plan_export_state",
                     "plan_import_state", "plan_get_info", "plan_backward", "plan_destroy",
-                    "plan_last_error", "plan_iterate_static"]
+                    "plan_last_error", "plan_iterate_static", "plan_profile"]
 
 
 class PlanError(RuntimeError):
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
     lib.plan_get_info.argtypes = [c_void_p, POINTER(plan_info)]
     lib.plan_backward.argtypes = [c_void_p, c_int, fp, fp, fp, fp, fp]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
+    lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
     lib.plan_destroy.argtypes = [c_void_p]
     lib.plan_destroy.restype = None
     lib.plan_last_error.restype = ctypes.c_char_p
@@ -260,6 +261,17 @@ class Planner:
         ptr = lambda x: c_void_p(x.data_ptr()) if x is not None else None
         _check(_lib.plan_import_state(self._h, ptr(zt), ptr(uc), ptr(uk), ptr(uw), int(k)))
         torch.cuda.current_stream(dev).synchronize()
+
+    def profile_start(self):
+        """Time each kernel of the following iterations with CUDA events."""
+        _check(_lib.plan_profile(self._h, 1, None, None))
+
+    def profile_stop(self):
+        """Average ms per iteration of {test, minimizer, segment, consensus}."""
+        ms = (c_float * 4)()
+        n = c_int(0)
+        _check(_lib.plan_profile(self._h, 0, ms, byref(n)))
+        return dict(test=ms[0], minimizer=ms[1], segment=ms[2], consensus=ms[3], iterations=n.value)
 
     def info(self):
         inf = plan_info()

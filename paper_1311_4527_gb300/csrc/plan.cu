@@ -799,18 +799,49 @@ double seg_point_dist(double px, double py, double ax, double ay, double bx, dou
   return std::sqrt(cx * cx + cy * cy);
 }
 
-// Host-side input check: fixed configurations must be feasible.
+// Host-side input check: fixed configurations must be feasible (two disks
+// closer than r_i + r_j, or a disk closer than r_i to a wall, make the
+// fixed-end minimizers infeasible).  Pairs are found with a uniform grid of
+// cell size max(r_i + r_j), so the check is linear in p.
 plan_status check_endpoints(int p, const float* start, const float* goal, const float* radius,
                             int nw, const float* walls) {
+  float rmax = 0.f;
+  for (int i = 0; i < p; ++i) rmax = std::max(rmax, radius[i]);
+  const double cell = std::max(2.0 * rmax, 1e-6);
   for (int which = 0; which < 2; ++which) {
     const float* X = which ? goal : start;
+    double x0 = X[0], y0 = X[1], x1 = X[0], y1 = X[1];
+    for (int i = 1; i < p; ++i) {
+      x0 = std::min(x0, (double)X[2 * i]); x1 = std::max(x1, (double)X[2 * i]);
+      y0 = std::min(y0, (double)X[2 * i + 1]); y1 = std::max(y1, (double)X[2 * i + 1]);
+    }
+    // cells at least `cell` wide, so overlapping disks sit in neighbouring cells
+    const long nx = std::max<long>(1, std::min<long>(4096, (long)((x1 - x0) / cell)));
+    const long ny = std::max<long>(1, std::min<long>(4096, (long)((y1 - y0) / cell)));
+    const double sx = (x1 - x0) / nx + 1e-300, sy = (y1 - y0) / ny + 1e-300;
+    std::vector<int> head(nx * ny, -1), next(p, -1);
+    std::vector<long> cx(p), cy(p);
     for (int i = 0; i < p; ++i) {
-      for (int j = i + 1; j < p; ++j) {
-        double dx = (double)X[2 * j] - X[2 * i], dy = (double)X[2 * j + 1] - X[2 * i + 1];
-        double R = (double)radius[i] + radius[j];
-        if (dx * dx + dy * dy < R * R)
-          return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %d and %d overlap",
-                      which ? "goal" : "start", i, j);
+      cx[i] = std::min(nx - 1, (long)((X[2 * i] - x0) / sx));
+      cy[i] = std::min(ny - 1, (long)((X[2 * i + 1] - y0) / sy));
+      const long c = cy[i] * nx + cx[i];
+      next[i] = head[c];
+      head[c] = i;
+    }
+    for (int i = 0; i < p; ++i) {
+      for (long dy = -1; dy <= 1; ++dy) {
+        for (long dx = -1; dx <= 1; ++dx) {
+          const long gx = cx[i] + dx, gy = cy[i] + dy;
+          if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) continue;
+          for (int j = head[gy * nx + gx]; j >= 0; j = next[j]) {
+            if (j <= i) continue;
+            const double ddx = (double)X[2 * j] - X[2 * i], ddy = (double)X[2 * j + 1] - X[2 * i + 1];
+            const double R = (double)radius[i] + radius[j];
+            if (ddx * ddx + ddy * ddy < R * R)
+              return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %d and %d overlap",
+                          which ? "goal" : "start", std::min(i, j), std::max(i, j));
+          }
+        }
       }
       for (int w = 0; w < nw; ++w) {
         const float* W = walls + 4 * w;
@@ -837,7 +868,14 @@ struct plan_s {
   int cur;  // which z buffer holds z^k
   int prox_grid = 0;  // CTAs of the minimizer pass (resident CTAs per SM x SMs)
   cudaStream_t side = nullptr;   // second stream for the kinetic and wall factors
+  cudaStream_t cap = nullptr;    // private stream for capturing the iteration graphs
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool profiling = false;        // plan_profile: per-kernel event timing
+  cudaEvent_t pev[6] = {};
+  cudaEvent_t pend = nullptr;
+  cudaGraphExec_t gexec[4] = {};  // captured iterations by (k parity, z buffer)
+  double ptime[4] = {0, 0, 0, 0};
+  int pcount = 0;
   unsigned* h_res;  // pinned host word for residual readback
   std::vector<float> h_radius;
   std::vector<float> h_walls;
@@ -895,7 +933,7 @@ cudaError_t clear_sums(plan_t h) {
   return e;
 }
 
-plan_status run_iteration(plan_t h) {
+plan_status ensure_prox_grid(plan_t h) {
   if (h->prox_grid == 0) {
     int dev = 0, sms = 0, nb = 0;
     CK(cudaGetDevice(&dev));
@@ -903,27 +941,79 @@ plan_status run_iteration(plan_t h) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, prox_kernel, 256, 0));
     h->prox_grid = std::max(1, sms * std::max(nb, 1));
   }
+  return PLAN_OK;
+}
+
+// Enqueue the kernels of iteration h->k (no state change on the host).
+plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   Dev P = h->dev(h->k);
   const unsigned grid = (unsigned)((size_t)h->eta * h->ntp);
   const int seg_threads = 32 * std::min(1 + h->nw, WARPS);
+  const bool prof = h->profiling && h->side;
   if (h->side) {
     // kinetic and wall factors run beside the collision passes
-    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaEventRecord(h->ev_fork, ms));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    if (prof) CK(cudaEventRecord(h->pev[4], h->side));
     segment_kernel<<<h->eta * h->nt, seg_threads, 0, h->side>>>(P);
+    if (prof) CK(cudaEventRecord(h->pev[5], h->side));
     CK(cudaEventRecord(h->ev_join, h->side));
   } else {
-    segment_kernel<<<h->eta * h->nt, seg_threads, 0, h->stream>>>(P);
+    segment_kernel<<<h->eta * h->nt, seg_threads, 0, ms>>>(P);
   }
-  if (P.dense) test_kernel<true><<<grid, 32 * TEST_WARPS, 0, h->stream>>>(P);
-  else test_kernel<false><<<grid, 32 * TEST_WARPS, 0, h->stream>>>(P);
-  prox_kernel<<<h->prox_grid, 256, 0, h->stream>>>(P);
-  if (h->side) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  if (prof) CK(cudaEventRecord(h->pev[0], ms));
+  if (P.dense) test_kernel<true><<<grid, 32 * TEST_WARPS, 0, ms>>>(P);
+  else test_kernel<false><<<grid, 32 * TEST_WARPS, 0, ms>>>(P);
+  if (prof) CK(cudaEventRecord(h->pev[1], ms));
+  prox_kernel<<<h->prox_grid, 256, 0, ms>>>(P);
+  if (prof) CK(cudaEventRecord(h->pev[2], ms));
+  if (h->side) CK(cudaStreamWaitEvent(ms, h->ev_join, 0));
+  if (prof) CK(cudaEventRecord(h->pev[3], ms));
   // the consensus kernel also clears the next iteration's worklist counter, so
   // it runs even when there is no free break-point (eta = 1)
   const int nfree = (h->eta - 1) * h->p;
-  consensus_kernel<<<std::max(1, (nfree + 63) / 64), 64, 0, h->stream>>>(P);
+  consensus_kernel<<<std::max(1, (nfree + 63) / 64), 64, 0, ms>>>(P);
+  if (prof) {
+    CK(cudaEventRecord(h->pend, ms));
+    CK(cudaEventSynchronize(h->pend));
+    float t[4];
+    CK(cudaEventElapsedTime(&t[0], h->pev[0], h->pev[1]));
+    CK(cudaEventElapsedTime(&t[1], h->pev[1], h->pev[2]));
+    CK(cudaEventElapsedTime(&t[2], h->pev[4], h->pev[5]));
+    CK(cudaEventElapsedTime(&t[3], h->pev[3], h->pend));
+    for (int q = 0; q < 4; ++q) h->ptime[q] += t[q];
+    h->pcount += 1;
+  }
   CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+// One iteration: replay a captured CUDA graph of the four kernels when one
+// fits (past the rho warm-up, not profiling), else launch them directly.
+plan_status run_iteration(plan_t h) {
+  plan_status st = ensure_prox_grid(h);
+  if (st != PLAN_OK) return st;
+  const bool graphable = h->cap && h->side && !h->profiling && h->k >= std::max(1, h->cfg.warm_iters);
+  if (graphable) {
+    const int key = ((h->k & 1) << 1) | h->cur;
+    if (!h->gexec[key]) {
+      cudaGraph_t g = nullptr;
+      // captured on a private stream: the legacy default stream cannot be
+      // captured, and the graph does not depend on the stream it came from
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      plan_status cst = enqueue_iteration(h, h->cap);
+      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+      if (cst != PLAN_OK) { if (g) cudaGraphDestroy(g); return cst; }
+      if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h->gexec[key], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(h->gexec[key], h->stream));
+  } else {
+    st = enqueue_iteration(h, h->stream);
+    if (st != PLAN_OK) return st;
+  }
   if (h->eta > 1) h->cur ^= 1;
   h->k += 1;
   return PLAN_OK;
@@ -1076,6 +1166,7 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
     return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
   }
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     plan_destroy(h);
@@ -1099,7 +1190,13 @@ void plan_destroy(plan_t h) {
   if (h->h_res) cudaFreeHost(h->h_res);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (int q = 0; q < 6; ++q)
+    if (h->pev[q]) cudaEventDestroy(h->pev[q]);
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec[q]) cudaGraphExecDestroy(h->gexec[q]);
+  if (h->pend) cudaEventDestroy(h->pend);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
 
@@ -1226,6 +1323,25 @@ plan_status plan_get_info(plan_t h, plan_info* info) {
   CK(cudaStreamSynchronize(h->stream));
   info->active_coll = (long long)hc[0];
   info->active_wall = (long long)hc[1];
+  return PLAN_OK;
+}
+
+plan_status plan_profile(plan_t h, int enable, float* ms, int* iterations) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  if (!h->side) return fail(PLAN_EINVAL, "this plan has no second stream to time");
+  if (enable) {
+    for (int q = 0; q < 6; ++q)
+      if (!h->pev[q]) CK(cudaEventCreate(&h->pev[q]));
+    if (!h->pend) CK(cudaEventCreate(&h->pend));
+    for (int q = 0; q < 4; ++q) h->ptime[q] = 0.0;
+    h->pcount = 0;
+    h->profiling = true;
+    return PLAN_OK;
+  }
+  h->profiling = false;
+  for (int q = 0; q < 4; ++q)
+    if (ms) ms[q] = h->pcount ? (float)(h->ptime[q] / h->pcount) : 0.f;
+  if (iterations) *iterations = h->pcount;
   return PLAN_OK;
 }
 

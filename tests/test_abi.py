@@ -119,3 +119,23 @@ def test_static_entry_point_rejects_a_problem_that_does_not_fit(lib):
     code = lib.plan_iterate_static(ctypes.byref(cfg), *([ptr] * 15), 0, None)
     assert code == 2
     assert b"static array" in lib.plan_last_error()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_grid_overlap_check_matches_brute_force(lib, seed):
+    """The host check finds an overlapping pair anywhere in a large layout
+    (its neighbour grid must not miss pairs across cell borders)."""
+    import workloads
+    inst = workloads.small_square(300, 4, seed=100 + seed)
+    start = inst.start.copy()
+    rng = np.random.default_rng(seed)
+    i, j = rng.choice(300, size=2, replace=False)
+    # move agent j to overlap agent i by a small amount, in a random direction
+    ang = rng.uniform(0, 2 * np.pi)
+    d = (inst.radius[i] + inst.radius[j]) * 0.999
+    start[j] = start[i] + d * np.array([np.cos(ang), np.sin(ang)])
+    code, msg = _create(lib, _cfg(300, 4, n_walls=0), start, inst.goal, inst.radius)
+    assert code == 6 and "start" in msg
+    # and the unmodified layout passes the check (fails later only for lack of a GPU)
+    code, msg = _create(lib, _cfg(300, 4, n_walls=0), inst.start, inst.goal, inst.radius)
+    assert code != 6
