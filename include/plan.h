@@ -55,6 +55,8 @@ typedef enum {
 #define PLAN_COST_PER_SEGMENT  (1u << 2) /* cost_w holds p x eta values C_{i,s} (else p values C_i) */
 #define PLAN_DENSE_STATE       (1u << 3) /* stream the u record of every collision factor each
                                             iteration, zeros included (else only active ones) */
+#define PLAN_ADMM              (1u << 4) /* standard ADMM (App. B): every factor always sends
+                                            rho0; implies the dense state */
 
 typedef struct {
   int p;              /* agents, >= 1 */

@@ -25,7 +25,11 @@ Fig. special_update_rules):
 * ties inside a minimizer go to the lowest energy, then the smallest angle
   (see ``oracle.prox``);
 * initial state: z = start for every break-point except the goal node,
-  u = 0, back weights rho0 inside and infinity at the fixed ends.
+  u = 0, back weights rho0 inside and infinity at the fixed ends;
+* standard-ADMM mode (``admm``): Appendix B notes that with every weight at
+  rho0 the method is classical ADMM.  Collision and wall factors then always
+  send rho0 (their minimizer still returns x = n when the n-trajectories are
+  feasible); the fixed ends stay constants with weight infinity.
 
 Weights are kept as classes 0 (zero), 1 (rho0), 2 (infinity).
 """
@@ -55,6 +59,7 @@ class Problem:
     alpha: float = 0.1
     u_keep: bool = False
     cost_unnorm: bool = False
+    admm: bool = False          # standard ADMM: every factor always sends rho0
     warm_iters: int = 0
     warm_rho: float = 0.0
 
@@ -201,7 +206,15 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
             if record_branches:
                 coll_gap[s, q] = out[5]
         active_coll[s] = act
-        coll_x.append((idx, xa))
+        if prob.admm:
+            # every pair is weighted: x = n for the feasible ones
+            idx_w = np.arange(iu.shape[0])
+            xw = n.copy()
+            xw[idx] = xa
+            coll_x.append((idx_w, xw))
+            idx, xa = idx_w, xw
+        else:
+            coll_x.append((idx, xa))
         if idx.shape[0]:
             ma = xa + u[idx]
             nodes_i = (iu[idx], iu[idx], ju[idx], ju[idx])
@@ -231,13 +244,14 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
             act = dw < prob.radius
             if record_branches:
                 wall_margin[w, s] = (dw - prob.radius) / prob.radius
-            for i in np.nonzero(act)[0]:
+            weighted = np.ones(p, dtype=bool) if prob.admm else act
+            for i in np.nonzero(weighted)[0]:
                 out = prox.wall_prox(n_lo[i], n_hi[i], _wnum(wb[i, s], rho0),
                                      _wnum(wb[i, s + 1], rho0), xL, xR, prob.radius[i],
                                      want_gap=record_branches)
                 x_lo, x_hi, a = out[:3]
-                assert a
-                if record_branches:
+                assert a == act[i]
+                if record_branches and a:
                     wall_gap[w, s, i] = out[3]
                 wall_x[(w, s, i)] = (x_lo, x_hi)
                 for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):

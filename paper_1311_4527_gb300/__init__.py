@@ -21,12 +21,13 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 __all__ = ["Planner", "PlanError", "load_library", "PLAN_U_KEEP", "PLAN_COST_UNNORM",
-           "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE", "EXPORTED_SYMBOLS"]
+           "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE", "PLAN_ADMM", "EXPORTED_SYMBOLS"]
 
 PLAN_U_KEEP = 1 << 0
 PLAN_COST_UNNORM = 1 << 1
 PLAN_COST_PER_SEGMENT = 1 << 2
 PLAN_DENSE_STATE = 1 << 3
+PLAN_ADMM = 1 << 4
 
 STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: "PLAN_ENOTCONV",
           5: "PLAN_ENUMERIC", 6: "PLAN_EINFEASIBLE_INPUT", 7: "PLAN_EUNSUPPORTED"}

@@ -61,9 +61,9 @@ constexpr unsigned FULL = 0xffffffffu;
 struct Dev {
   int p, eta, nw, nt, ntp;
   float rho, alpha;
-  int dense, keep;
+  int dense, keep, admm;
   const float2* z;       // z^k, [p][eta+1]
-  float2* z_next;        // z^{k+1}
+  float2* z_next;        // z^{k+1}; until the consensus pass writes it, z^{k-1}
   const float* radius;   // [p]
   const float* cost;     // [p][eta], kinetic coefficients c_{i,s}
   const float4* walls;   // [nw] (xL.x, xL.y, xR.x, xR.y)
@@ -115,6 +115,16 @@ __device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m)
   atomicAdd(P.accx + node, (unsigned long long)__float2ll_rn(m.x * scale));
   atomicAdd(P.accy + node, (unsigned long long)__float2ll_rn(m.y * scale));
   atomicAdd(P.accc + node, 1u);
+}
+
+// Standard-ADMM mode, a factor that was feasible in the previous iteration:
+// its x^k was n^{k-1} = z^{k-1} - u^{k-1}, so step 7 needs no stored x.
+__device__ __forceinline__ float2 finish_u_feasible(bool pinned, float2 u_prev, float2 z_prev,
+                                                    float2 zk, float alpha, float& res) {
+  if (pinned) return mk(0.f, 0.f);
+  const float2 d = (z_prev - u_prev) - zk;
+  res = fmaxf(res, maxabs2(d));
+  return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return mk(v.x, v.y); }
@@ -187,8 +197,15 @@ __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi,
   float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = u4;
   if (vi && (P.dense || bprev)) u4 = P.uwall[idx];
   if (bprev) x4 = P.xwall[idx];
-  const float2 ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
-  const float2 uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
+  float2 ul, uh;
+  if (P.admm && vi && !bprev) {
+    const int E1 = P.eta + 1;
+    ul = finish_u_feasible(pin_lo, lo2(u4), P.z_next[(size_t)i * E1 + s], zl, P.alpha, res);
+    uh = finish_u_feasible(pin_hi, hi2(u4), P.z_next[(size_t)i * E1 + s + 1], zh, P.alpha, res);
+  } else {
+    ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
+    uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
+  }
   const float2 nl = zl - ul, nh = zh - uh;
   const float4 W = P.walls[w];
   const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
@@ -328,6 +345,15 @@ __global__ void __launch_bounds__(32 * TEST_WARPS) test_kernel(Dev P) {
           ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), zjl, P.alpha, res);
           uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
           ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), zjh, P.alpha, res);
+        } else if (DENSE && P.admm && valid) {
+          // standard ADMM: the pair was feasible, so x^k = z^{k-1} - u^{k-1}
+          const float2 pil = P.z_next[(size_t)(I * TILE + r) * E1 + s];
+          const float2 pih = P.z_next[(size_t)(I * TILE + r) * E1 + s + 1];
+          const float2 pjl = P.z_next[(size_t)j * E1 + s], pjh = P.z_next[(size_t)j * E1 + s + 1];
+          uil = finish_u_feasible(pin_lo, uil, pil, zil, P.alpha, res);
+          ujl = finish_u_feasible(pin_lo, ujl, pjl, zjl, P.alpha, res);
+          uih = finish_u_feasible(pin_hi, uih, pih, zih, P.alpha, res);
+          ujh = finish_u_feasible(pin_hi, ujh, pjh, zjh, P.alpha, res);
         } else if (DENSE && !P.keep) {
           uil = ujl = uih = ujh = mk(0.f, 0.f);  // reset rule: inactive edges carry u = 0
         }
@@ -436,7 +462,15 @@ __global__ void consensus_kernel(Dev P) {
     P.accc[node] = 0u;
     const float2 zo = P.z[node];
     float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
-    if (cnt > 0u) {
+    if (P.admm) {
+      // every edge is weighted; each feasible collision or wall factor sent
+      // m = n + u = z^k, added here in the same exact fixed point
+      const unsigned deg = 2u * (unsigned)(P.p - 1) + 2u + 2u * (unsigned)P.nw;
+      const long long rest = (long long)(deg - cnt);
+      const long long qx = __float2ll_rn(zo.x * P.fix[0]), qy = __float2ll_rn(zo.y * P.fix[0]);
+      const double den = (double)P.fix[0] * (double)deg;
+      zn = mk((float)((double)(sx + rest * qx) / den), (float)((double)(sy + rest * qy) / den));
+    } else if (cnt > 0u) {
       const double den = (double)P.fix[0] * (double)cnt;
       zn = mk((float)((double)sx / den), (float)((double)sy / den));
     }
@@ -493,6 +527,26 @@ __global__ void residual_kernel(Dev P) {
   const size_t nrows = (size_t)P.eta * P.ntp * TILE;
   for (size_t row = gw; row < nrows; row += nwarps) {
     uint32_t word = P.bits[row];
+    if (P.admm && !((word >> lane) & 1u)) {
+      // standard ADMM: a feasible pair's x is z^{k-1} - u^{k-1}
+      const size_t blk = row / TILE;
+      const int r = (int)(row - blk * TILE);
+      const int s = (int)(blk / P.ntp);
+      const int2 IJ = P.tiles[blk - (size_t)s * P.ntp];
+      const int i = IJ.x * TILE + r, j = IJ.y * TILE + lane;
+      if (i >= P.p || j >= P.p || (IJ.x == IJ.y && r >= lane)) continue;
+      const size_t fid = row * TILE + lane;
+      const float4 a = P.ulo[fid], b = P.uhi[fid];
+      if (s != 0) {
+        finish_u_feasible(false, lo2(a), P.z_next[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s], P.alpha, res);
+        finish_u_feasible(false, hi2(a), P.z_next[(size_t)j * E1 + s], P.z[(size_t)j * E1 + s], P.alpha, res);
+      }
+      if (s != P.eta - 1) {
+        finish_u_feasible(false, lo2(b), P.z_next[(size_t)i * E1 + s + 1], P.z[(size_t)i * E1 + s + 1], P.alpha, res);
+        finish_u_feasible(false, hi2(b), P.z_next[(size_t)j * E1 + s + 1], P.z[(size_t)j * E1 + s + 1], P.alpha, res);
+      }
+      continue;
+    }
     if (!((word >> lane) & 1u)) continue;
     const size_t blk = row / TILE;
     const int r = (int)(row - blk * TILE);
@@ -523,7 +577,14 @@ __global__ void residual_kernel(Dev P) {
     const int ws = t / P.p;
     const int s = ws % P.eta;
     const uint32_t word = P.wbits[(size_t)ws * P.nt + i / TILE];
-    if (!((word >> (i % TILE)) & 1u)) continue;
+    if (!((word >> (i % TILE)) & 1u)) {
+      if (P.admm) {  // feasible wall factor in standard ADMM: x = z^{k-1} - u^{k-1}
+        const float4 u = P.uwall[t];
+        if (s != 0) finish_u_feasible(false, lo2(u), P.z_next[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s], P.alpha, res);
+        if (s != P.eta - 1) finish_u_feasible(false, hi2(u), P.z_next[(size_t)i * E1 + s + 1], P.z[(size_t)i * E1 + s + 1], P.alpha, res);
+      }
+      continue;
+    }
     float4 x = P.xwall[t];
     if (s != 0) res = fmaxf(res, maxabs2(lo2(x) - P.z[(size_t)i * E1 + s]));
     if (s != P.eta - 1) res = fmaxf(res, maxabs2(hi2(x) - P.z[(size_t)i * E1 + s + 1]));
@@ -588,10 +649,18 @@ __global__ void export_coll_kernel(Dev P, float* u_coll, uint8_t* act) {
   if (bprev) { xl4 = P.xlo[slot]; xh4 = P.xhi[slot]; }
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
   float dummy = 0.f;
-  float2 uil = finish_u(bprev, pin_lo, P.keep, lo2(ul4), lo2(xl4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
-  float2 ujl = finish_u(bprev, pin_lo, P.keep, hi2(ul4), hi2(xl4), P.z[(size_t)j * E1 + s], P.alpha, dummy);
-  float2 uih = finish_u(bprev, pin_hi, P.keep, lo2(uh4), lo2(xh4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
-  float2 ujh = finish_u(bprev, pin_hi, P.keep, hi2(uh4), hi2(xh4), P.z[(size_t)j * E1 + s + 1], P.alpha, dummy);
+  float2 uil, ujl, uih, ujh;
+  if (P.admm && !bprev) {
+    uil = finish_u_feasible(pin_lo, lo2(ul4), P.z_next[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s], P.alpha, dummy);
+    ujl = finish_u_feasible(pin_lo, hi2(ul4), P.z_next[(size_t)j * E1 + s], P.z[(size_t)j * E1 + s], P.alpha, dummy);
+    uih = finish_u_feasible(pin_hi, lo2(uh4), P.z_next[(size_t)i * E1 + s + 1], P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    ujh = finish_u_feasible(pin_hi, hi2(uh4), P.z_next[(size_t)j * E1 + s + 1], P.z[(size_t)j * E1 + s + 1], P.alpha, dummy);
+  } else {
+    uil = finish_u(bprev, pin_lo, P.keep, lo2(ul4), lo2(xl4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+    ujl = finish_u(bprev, pin_lo, P.keep, hi2(ul4), hi2(xl4), P.z[(size_t)j * E1 + s], P.alpha, dummy);
+    uih = finish_u(bprev, pin_hi, P.keep, lo2(uh4), lo2(xh4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    ujh = finish_u(bprev, pin_hi, P.keep, hi2(uh4), hi2(xh4), P.z[(size_t)j * E1 + s + 1], P.alpha, dummy);
+  }
   const size_t P2 = (size_t)P.p * (P.p - 1) / 2;
   const size_t q = (size_t)s * P2 + pair_index(P.p, i, j);
   if (u_coll) {
@@ -622,8 +691,14 @@ __global__ void export_seg_kernel(Dev P, float* u_kin, float* u_wall, uint8_t* a
     const bool bprev = (P.wbits[(size_t)ws * P.nt + i / TILE] >> (i % TILE)) & 1u;
     float4 u4 = P.uwall[t], x4 = P.xwall[t];
     if (!P.dense && !bprev) u4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 ul = finish_u(bprev, s == 0, P.keep, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
-    float2 uh = finish_u(bprev, s == P.eta - 1, P.keep, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    float2 ul, uh;
+    if (P.admm && !bprev) {
+      ul = finish_u_feasible(s == 0, lo2(u4), P.z_next[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s], P.alpha, dummy);
+      uh = finish_u_feasible(s == P.eta - 1, hi2(u4), P.z_next[(size_t)i * E1 + s + 1], P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    } else {
+      ul = finish_u(bprev, s == 0, P.keep, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+      uh = finish_u(bprev, s == P.eta - 1, P.keep, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    }
     if (u_wall) {
       float* o = u_wall + (size_t)t * 4;
       o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
@@ -655,7 +730,9 @@ __global__ void import_coll_kernel(Dev P, const float* u_coll) {
       uh = make_float4(u[2], u[3], u[6], u[7]);
       xl = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)j * E1 + s]);
       xh = pack(P.z[(size_t)i * E1 + s + 1], P.z[(size_t)j * E1 + s + 1]);
-      nz = ul.x != 0.f || ul.y != 0.f || ul.z != 0.f || ul.w != 0.f ||
+      // flagged pairs finish from the stored x = z^k, which reproduces u^k
+      // exactly; in standard ADMM every pair must take that path after import
+      nz = P.admm || ul.x != 0.f || ul.y != 0.f || ul.z != 0.f || ul.w != 0.f ||
            uh.x != 0.f || uh.y != 0.f || uh.z != 0.f || uh.w != 0.f;
     }
     P.ulo[slot] = ul; P.uhi[slot] = uh; P.xlo[slot] = xl; P.xhi[slot] = xh;
@@ -694,7 +771,7 @@ __global__ void import_wbits_kernel(Dev P) {
     const int i = tile * TILE + lane;
     if (i < P.p) {
       float4 u = P.uwall[(size_t)ws * P.p + i];
-      nz = u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f;
+      nz = P.admm || u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f;
     }
   }
   uint32_t word = __ballot_sync(FULL, nz);
@@ -891,8 +968,10 @@ struct plan_s {
     P.p = p; P.eta = eta; P.nw = nw; P.nt = nt; P.ntp = ntp;
     P.rho = rho_at(kk);
     P.alpha = cfg.alpha;
-    // keeping u on inactive edges needs every u record, so it implies the dense state
-    P.dense = (cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) ? 1 : 0;
+    // keeping u on inactive edges (or standard ADMM, which updates every u)
+    // needs every u record, so both imply the dense state
+    P.dense = (cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM)) ? 1 : 0;
+    P.admm = (cfg.flags & PLAN_ADMM) ? 1 : 0;
     P.keep = (cfg.flags & PLAN_U_KEEP) ? 1 : 0;
     float2* z0 = at<float2>(L.z0);
     float2* z1 = at<float2>(L.z1);
@@ -1083,7 +1162,7 @@ plan_status plan_reset(plan_t h) {
   (void)zbytes;
   CK(cudaMemsetAsync(h->at<void>(h->L.bits), 0, (size_t)h->eta * h->ntp * TILE * 4, h->stream));
   if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.wbits), 0, (size_t)h->nw * h->eta * h->nt * 4, h->stream));
-  if (h->cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) {
+  if (h->cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM)) {
     CK(cudaMemsetAsync(h->at<void>(h->L.ulo), 0, h->slots * 16, h->stream));
     CK(cudaMemsetAsync(h->at<void>(h->L.uhi), 0, h->slots * 16, h->stream));
     if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, (size_t)h->nw * h->eta * h->p * 16, h->stream));
@@ -1112,7 +1191,8 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
   if (cfg->warm_iters < 0 || (cfg->warm_iters > 0 && !(cfg->warm_rho > 0.f)))
     return fail(PLAN_EINVAL, "warm_rho must be positive when warm_iters > 0");
   if (cfg->max_iter < 0) return fail(PLAN_EINVAL, "max_iter must be >= 0");
-  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT | PLAN_DENSE_STATE;
+  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
+                         PLAN_DENSE_STATE | PLAN_ADMM;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
   const size_t p = cfg->p, eta = cfg->eta;
   const size_t ncost = (cfg->flags & PLAN_COST_PER_SEGMENT) ? p * eta : p;
@@ -1417,7 +1497,8 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
   if (cfg->n_walls > 0 && (!walls || !u_wall_in || !u_wall_out)) return fail(PLAN_EINVAL, "null wall array");
   if (!(cfg->rho0 > 0.f) || !(cfg->alpha > 0.f)) return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
-  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT | PLAN_DENSE_STATE;
+  const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
+                         PLAN_DENSE_STATE | PLAN_ADMM;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
   const Layout L = layout_for(cfg);
   if (L.total > PLAN_STATIC_SCRATCH_BYTES)
@@ -1450,7 +1531,7 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
     CK(cudaMemcpyAsync(h.at<void>(L.walls), walls, (size_t)h.nw * 16, cudaMemcpyDeviceToDevice, h.stream));
   // the scratch keeps the previous call's contents: clear what must start at zero
   CK(cudaMemsetAsync(h.at<void>(L.status), 0, 4, h.stream));
-  if (h.cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP)) {
+  if (h.cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM)) {
     CK(cudaMemsetAsync(h.at<void>(L.ulo), 0, h.slots * 16, h.stream));
     CK(cudaMemsetAsync(h.at<void>(L.uhi), 0, h.slots * 16, h.stream));
   }

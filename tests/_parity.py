@@ -40,6 +40,8 @@ def make_planner(prob, flags=0, **kw):
     flags = flags | (pk.PLAN_COST_UNNORM if prob.cost_unnorm else 0)
     if prob.u_keep:
         flags |= pk.PLAN_U_KEEP
+    if prob.admm:
+        flags |= pk.PLAN_ADMM
     return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=cost,
                       walls=prob.walls if prob.n_walls else None, rho0=prob.rho0,
                       alpha=prob.alpha, flags=flags, **kw)

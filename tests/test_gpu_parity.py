@@ -102,3 +102,10 @@ def test_full_size_square1024_one_iteration():
     for s in stats:
         assert s["coll_active"] > 10000
         assert s["coll_excluded"] < 0.01 * s["coll_active"], s
+
+
+def test_standard_admm_mode_parity():
+    prob = _prob(workloads.circle4(), admm=True)
+    _run(prob, [0, 4, 40])
+    prob = _prob(workloads.small_square(40, 5, seed=9), cost_unnorm=True, admm=True)
+    _run(prob, [0, 6])

@@ -136,3 +136,20 @@ def test_info_counts():
     ex = pl.export_state()
     assert inf["active_coll"] == int(ex["act_coll"].sum().item())
     pl.close()
+
+
+def test_admm_and_twa_converge_on_circle4_like_the_oracle():
+    """Standard ADMM and TWA on the p = 4 circle: each GPU solve converges to
+    the oracle's cost for that mode, and TWA needs fewer iterations."""
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.circle4()
+    its = {}
+    for admm in (False, True):
+        prob = twa.Problem.from_instance(inst, admm=admm)
+        st, o_it, _ = twa.solve(prob, inst.tol, inst.max_iter)
+        conv, it, res, z = _solve(inst, flags=pk.PLAN_ADMM if admm else 0)
+        assert conv
+        assert abs(twa.total_cost(prob, z) - twa.total_cost(prob, st.z)) <= 1e-3 * twa.total_cost(prob, st.z)
+        assert abs(it - o_it) <= 0.05 * o_it + 5
+        its[admm] = it
+    assert its[False] < its[True]

@@ -212,3 +212,42 @@ def test_wall_factor_pushes_a_passing_agent_clear():
     assert wall_sl < 1.0          # the unconstrained optimum was infeasible
     # mirror symmetry of the problem about x = 0 survives in the plan
     assert np.allclose(st.z[0, :, 0], -st.z[0, ::-1, 0], atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# standard-ADMM mode (Appendix B: every weight rho0)
+# ---------------------------------------------------------------------------
+
+def _separated(admm):
+    start = [[0.0, 0.0], [0.0, 5.0], [0.0, 10.0]]
+    goal = [[4.0, 1.0], [4.0, 6.0], [4.0, 11.0]]
+    return _problem(start, goal, [0.3, 0.3, 0.3], eta=4, cost_unnorm=True, admm=admm)
+
+
+def test_admm_first_step_is_damped_by_the_node_degree():
+    """From the same start, every feasible collision factor sends m = z, so
+    an interior node's move is the TWA move over p (2 kinetic edges among
+    2(p-1) + 2)."""
+    a, _ = twa.iterate(_separated(False), twa.initial_state(_separated(False)))
+    b, _ = twa.iterate(_separated(True), twa.initial_state(_separated(True)))
+    z0 = twa.initial_state(_separated(False)).z
+    assert np.allclose((b.z - z0)[:, 1:-1], (a.z - z0)[:, 1:-1] / 3, atol=1e-14)
+
+
+def test_admm_mode_still_reaches_the_straight_lines():
+    """The feasible collision factors' pull towards the previous iterate
+    vanishes at the fixed point, which stays the constant-velocity lines."""
+    prob = _separated(True)
+    st, it, res = twa.solve(prob, 1e-9, 50000)
+    assert res < 1e-9
+    assert np.allclose(st.z, twa.straight_lines(prob), atol=1e-7)
+    assert np.abs(st.u_coll).max() < 1e-6
+
+
+def test_admm_mode_updates_u_on_feasible_factors():
+    prob = _separated(True)
+    st = twa.initial_state(prob)
+    for _ in range(3):
+        st, info = twa.iterate(prob, st)
+    assert not info.active_coll.any()
+    assert np.any(st.u_coll != 0.0)  # weighted although never colliding
