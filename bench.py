@@ -242,6 +242,54 @@ def time_to_converge(pk, names, oracle_names):
     return out
 
 
+def batching(pk, n=512, max_iter=2000, check_every=50):
+    """Row f1: n uneven instances (p ~ U{8..256}, eta in {4, 8, 16}, circle
+    swap or random square 50/50) solved as one batch (one launch per pass,
+    CUDA graphs, autotuned launch shapes) against looping the plain solver
+    over the same instances, both to the same tolerance / iteration cap and
+    the same residual checks (equal accuracy: each member stops at the same
+    iteration either way)."""
+    import torch
+    insts = workloads.batch_instances(n)
+    for m in insts:
+        m.max_iter = max_iter
+    factors = [sum(factor_counts(m).values()) for m in insts]
+    # the autotuner's timing iterations are real iterations, so it tunes on a
+    # throwaway batch of the same instances; the timed solve starts afresh
+    with pk.PlannerBatch(insts, check_every=check_every) as B:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        choice = B.autotune(8)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t0
+    with pk.PlannerBatch(insts, check_every=check_every) as B:
+        B.set_shape(**choice)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, res, nconv = B.solve()
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    # the same instances, one plain planner at a time
+    t_loop = 0.0
+    its_loop = []
+    for m in insts:
+        with pk.Planner.from_instance(m, check_every=check_every) as pl:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            conv, it, r = pl.solve()
+            torch.cuda.synchronize()
+            t_loop += time.perf_counter() - t0
+            its_loop.append(it)
+    upd = float(sum(f * i for f, i in zip(factors, its)))
+    return {"workload": f"batch{n}: p ~ U{{8..256}}, eta in {{4,8,16}}, circle/square 50/50",
+            "members": n, "max_iter": max_iter, "check_every": check_every,
+            "converged": nconv, "iterations_total": int(sum(its)),
+            "same_iterations_as_loop": its == its_loop,
+            "batch_s": t_batch, "loop_s": t_loop, "speedup_vs_loop": t_loop / t_batch,
+            "batch_factor_updates_per_s": upd / t_batch, "loop_factor_updates_per_s": upd / t_loop,
+            "autotuned": choice, "autotune_s": t_tune}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +441,7 @@ def main():
                        "path": "plan_set_endpoints(host) + plan_iterate(1) + "
                                "plan_get_trajectory(host), pinned buffers"}
     if rank == 0 and world == 1 and not args.quick:
+        line["batching"] = batching(pk)
         line["time_to_converge"] = time_to_converge(
             pk, ["circle4_eta4", "circle100_eta8", "square1024_eta16"], ["circle4_eta4"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -170,6 +170,49 @@ plan_status plan_get_info(plan_t plan, plan_info* info);
  * NULL).  Errors: PLAN_EINVAL, PLAN_ECUDA. */
 plan_status plan_profile(plan_t plan, int enable, float* ms, int* iterations);
 
+/*
+ * Batches: n independent problems (uneven p, eta, walls) advanced together.
+ * Every pass of an iteration is one launch over all members' blocks, and
+ * iterations are replayed from CUDA graphs (the spec batching form; the
+ * paper solves one problem at a time).  Members must share the state-mode
+ * flags (PLAN_DENSE_STATE, PLAN_U_KEEP, PLAN_ADMM).  Arguments are arrays of
+ * n host pointers laid out as for plan_create; walls may be NULL (no member
+ * has walls) or hold NULL entries.  workspace: plan_batch_workspace_size()
+ * bytes of device memory, 256-byte aligned, or NULL to let the library
+ * allocate.  Errors as for plan_create, with the member index in the message.
+ */
+typedef struct plan_batch_s* plan_batch_t;
+plan_status plan_batch_workspace_size(int n, const plan_config* cfgs, size_t* bytes);
+plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const* start,
+                              const float* const* goal, const float* const* radius,
+                              const float* const* cost_w, const float* const* walls,
+                              void* workspace, size_t workspace_bytes, void* cuda_stream,
+                              plan_batch_t* out);
+/* k_iters iterations of every member not yet converged (enqueued, no sync). */
+plan_status plan_batch_iterate(plan_batch_t batch, int k_iters);
+/* Iterate until every member's residual is below its tol or it reached its
+ * max_iter (checked every min check_every iterations, rounded up to even);
+ * converged members are frozen.  iters_done / residual: n host values (may be
+ * NULL): the iteration at which each member converged (or the last one run)
+ * and its last residual.  n_converged: how many converged.  PLAN_ENUMERIC on
+ * a non-finite residual. */
+plan_status plan_batch_solve(plan_batch_t batch, int* iters_done, float* residual,
+                             int* n_converged);
+/* Break-points of one member, as plan_get_trajectory. */
+plan_status plan_batch_get_trajectory(plan_batch_t batch, int member, float* z, int on_device);
+/* Time the launch-shape candidates (rows per warp of the collision test
+ * {4, 8, 16}, minimizer CTAs per SM {1, 2, 4} x the base grid, iterations per
+ * graph {2, 8}) on this batch, iters_per_candidate iterations each (they are
+ * real iterations: results do not depend on the shape), and keep the fastest.
+ * choice: 3 host ints receiving the chosen values (may be NULL). */
+plan_status plan_batch_autotune(plan_batch_t batch, int iters_per_candidate, int* choice);
+/* Set the launch shape directly (for example one found by the autotuner on
+ * another batch of the same instances): rows_per_warp in {4, 8, 16},
+ * prox_ctas_per_sm in 1..8, iterations_per_graph even and >= 2. */
+plan_status plan_batch_set_shape(plan_batch_t batch, int rows_per_warp, int prox_ctas_per_sm,
+                                 int iterations_per_graph);
+void plan_batch_destroy(plan_batch_t batch);
+
 /* Gradient of a trajectory loss through unrolled iterations (not built yet:
  * returns PLAN_EUNSUPPORTED). */
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,

@@ -35,7 +35,10 @@ STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: 
 EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_set_endpoints",
                     "plan_iterate", "plan_solve", "plan_get_trajectory", "plan_export_state",
                     "plan_import_state", "plan_get_info", "plan_backward", "plan_destroy",
-                    "plan_last_error", "plan_iterate_static", "plan_profile"]
+                    "plan_last_error", "plan_iterate_static", "plan_profile",
+                    "plan_batch_workspace_size", "plan_batch_create", "plan_batch_iterate",
+                    "plan_batch_solve", "plan_batch_get_trajectory", "plan_batch_autotune",
+                    "plan_batch_set_shape", "plan_batch_destroy"]
 
 
 class PlanError(RuntimeError):
@@ -87,12 +90,23 @@ def load_library(path: str | None = None):
     lib.plan_backward.argtypes = [c_void_p, c_int, fp, fp, fp, fp, fp]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
+    pp = POINTER(c_void_p)
+    lib.plan_batch_workspace_size.argtypes = [c_int, POINTER(plan_config), POINTER(c_size_t)]
+    lib.plan_batch_create.argtypes = [c_int, POINTER(plan_config), pp, pp, pp, pp, pp, c_void_p,
+                                      c_size_t, c_void_p, POINTER(c_void_p)]
+    lib.plan_batch_iterate.argtypes = [c_void_p, c_int]
+    lib.plan_batch_solve.argtypes = [c_void_p, POINTER(c_int), fp, POINTER(c_int)]
+    lib.plan_batch_get_trajectory.argtypes = [c_void_p, c_int, c_void_p, c_int]
+    lib.plan_batch_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    lib.plan_batch_set_shape.argtypes = [c_void_p, c_int, c_int, c_int]
+    lib.plan_batch_destroy.argtypes = [c_void_p]
+    lib.plan_batch_destroy.restype = None
     lib.plan_destroy.argtypes = [c_void_p]
     lib.plan_destroy.restype = None
     lib.plan_last_error.restype = ctypes.c_char_p
     for name in EXPORTED_SYMBOLS:
         f = getattr(lib, name)
-        if name not in ("plan_destroy", "plan_last_error"):
+        if name not in ("plan_destroy", "plan_last_error", "plan_batch_destroy"):
             f.restype = c_int
     _lib = lib
     return lib
@@ -278,3 +292,89 @@ class Planner:
         inf = plan_info()
         _check(_lib.plan_get_info(self._h, byref(inf)))
         return {f: getattr(inf, f) for f, _ in plan_info._fields_}
+
+
+class PlannerBatch:
+    """Many independent problems advanced together (one launch per pass).
+
+    ``PlannerBatch([inst, ...], flags=0, check_every=50)`` with
+    ``workloads.Instance`` members; members must share the state-mode flags.
+    """
+
+    def __init__(self, instances, flags=0, check_every=50, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PlannerBatch needs a CUDA device (there is no CPU fallback)")
+        lib = load_library()
+        self.instances = list(instances)
+        n = len(self.instances)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        cfgs = (plan_config * n)()
+        self._arrays = []
+        ptrs = {k: (c_void_p * n)() for k in ("start", "goal", "radius", "cost", "walls")}
+        for b, inst in enumerate(self.instances):
+            cw = np.asarray(inst.cost_w, dtype=np.float64)
+            fl = flags | (PLAN_COST_PER_SEGMENT if cw.ndim == 2 else 0)
+            cfgs[b] = make_config(inst.p, inst.eta, inst.rho0, inst.alpha, inst.tol, inst.max_iter,
+                                  inst.n_walls, fl, check_every, 0, 0.0, inst.T)
+            arrs = dict(start=_f32(inst.start, (inst.p, 2))[0], goal=_f32(inst.goal, (inst.p, 2))[0],
+                        radius=_f32(inst.radius, (inst.p,))[0], cost=_f32(cw, cw.shape)[0],
+                        walls=_f32(inst.walls, (-1, 4))[0] if inst.n_walls else None)
+            self._arrays.append(arrs)
+            for k, a in arrs.items():
+                ptrs[k][b] = a.ctypes.data if a is not None else None
+        self.cfgs = cfgs
+        nbytes = c_size_t(0)
+        _check(lib.plan_batch_workspace_size(n, cfgs, byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        h = c_void_p()
+        _check(lib.plan_batch_create(n, cfgs, ptrs["start"], ptrs["goal"], ptrs["radius"],
+                                     ptrs["cost"], ptrs["walls"], c_void_p(self.workspace.data_ptr()),
+                                     nbytes.value, c_void_p(self.stream.cuda_stream), byref(h)))
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.plan_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def iterate(self, k=1):
+        _check(_lib.plan_batch_iterate(self._h, int(k)))
+
+    def solve(self):
+        """Returns (iterations per member, residual per member, number converged)."""
+        its = (c_int * self.n)()
+        res = (c_float * self.n)()
+        nc = c_int(0)
+        _check(_lib.plan_batch_solve(self._h, its, res, byref(nc)))
+        return list(its), list(res), nc.value
+
+    def autotune(self, iters_per_candidate=8):
+        ch = (c_int * 3)()
+        _check(_lib.plan_batch_autotune(self._h, int(iters_per_candidate), ch))
+        return dict(rows_per_warp=ch[0], prox_ctas_per_sm=ch[1], iterations_per_graph=ch[2])
+
+    def set_shape(self, rows_per_warp, prox_ctas_per_sm, iterations_per_graph):
+        _check(_lib.plan_batch_set_shape(self._h, int(rows_per_warp), int(prox_ctas_per_sm),
+                                         int(iterations_per_graph)))
+
+    def trajectory(self, member):
+        import torch
+        inst = self.instances[member]
+        z = torch.empty((inst.p, inst.eta + 1, 2), dtype=torch.float32, device=self.device)
+        _check(_lib.plan_batch_get_trajectory(self._h, int(member), c_void_p(z.data_ptr()), 1))
+        return z

@@ -1,39 +1,18 @@
-// plan.cu -- GB300 (sm_103a) kernels and C ABI of the three-weight ADMM
-// trajectory planner (Bento, Derbinsky, Alonso-Mora, Yedidia, NIPS 2013).
+// plan.cu -- GB300 (sm_103a) C ABI of the three-weight ADMM trajectory
+// planner (Bento, Derbinsky, Alonso-Mora, Yedidia, NIPS 2013): workspace
+// layout, input checks, state reset / import / export, the residual, and the
+// per-iteration launch sequence.  The iteration's per-block work lives in
+// twa_iter.cuh; one iteration is four kernels:
 //
-// One iteration = Appendix B steps 1-7 over the factor graph of Section 3.3,
-// run as two kernels:
+//   test_kernel      every collision factor: deferred u step, n = z - u,
+//                    collision test, activity bits, worklist of active pairs
+//   segment_kernel   kinetic and wall factors (on a second stream, beside the
+//                    collision passes)
+//   prox_kernel      the collision minimizer of every active pair, adding
+//                    m = x + u into exact fixed-point consensus sums
+//   consensus_kernel z = sum m / count per free break-point
 //
-//   factor_kernel  one CTA per (segment s, agent tile I, agent tile J >= I):
-//                  every collision factor (s, i in I, j in J, i < j) of the
-//                  tile -- and, in the diagonal CTAs, the kinetic and wall
-//                  factors of the agents of I at segment s.  Per factor: finish
-//                  the pending dual update of the previous iteration (step 7),
-//                  form n = z - u (step 1), run the minimizer and its weight
-//                  logic (steps 2-3), form m = x + u (step 4) and add the
-//                  weighted m into per-tile consensus partial sums (warp
-//                  shuffles for the row agent, registers + shared memory for
-//                  the column agent).  One store per (tile, agent, component).
-//   consensus_kernel  one thread per free break-point: z = sum(rho m) /
-//                  sum(rho) over the tile partials in a fixed order (step 5,
-//                  deterministic), and |z_new - z_old| for the residual.
-//
-// Step 7 needs z^{k+1}, which exists only after every factor ran.  The factor
-// kernel therefore stores x^{k+1} of the factors that sent rho0 and finishes
-// u^{k+1} = u^k + alpha (x^{k+1} - z^{k+1}) at the start of the next
-// iteration.  Back weights (step 6) are rho0 at every interior node, because
-// the kinetic factors always send rho0 there, and infinity at the fixed ends;
-// u on an edge whose forward weight was 0, or whose node is fixed, is 0.
-//
-// Collision-factor state lives in tile order: for CTA blk = s * ntp + tp the
-// 32 x 32 pair slots (row r = i - 32 I, column c = j - 32 J) are contiguous,
-// so a warp streams one row as 32 consecutive float4 (512 B).  Per slot:
-//   ulo[slot] = (u_i(s), u_j(s))       uhi[slot] = (u_i(s+1), u_j(s+1))
-//   xlo / xhi = pending x^{k+1}, read and written only for active factors
-//   bits[blk * 32 + r] bit c = forward weight rho0 in the last iteration.
-// With PLAN_DENSE_STATE the u record of every slot is read and written each
-// iteration; otherwise only those of factors whose bit is set (every other u
-// is 0 by the reset rule), which leaves 1 bit per factor of state traffic.
+// Iterations after the first are replayed from captured CUDA graphs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,445 +25,35 @@
 #include <vector>
 
 #include "plan.h"
-#include "twa_math.cuh"
-
-using namespace twa;
+#include "twa_iter.cuh"
 
 namespace {
 
-constexpr int TILE = 32;
-constexpr int WARPS = 8;
-constexpr int THREADS = TILE * WARPS;
-constexpr int ROWS = TILE / WARPS;  // rows of a tile per warp
-constexpr unsigned FULL = 0xffffffffu;
-
-struct Dev {
-  int p, eta, nw, nt, ntp;
-  float rho, alpha;
-  int dense, keep, admm;
-  const float2* z;       // z^k, [p][eta+1]
-  float2* z_next;        // z^{k+1}; until the consensus pass writes it, z^{k-1}
-  const float* radius;   // [p]
-  const float* cost;     // [p][eta], kinetic coefficients c_{i,s}
-  const float4* walls;   // [nw] (xL.x, xL.y, xR.x, xR.y)
-  const int2* tiles;     // [ntp] (I, J), I <= J
-  float4 *ulo, *uhi, *xlo, *xhi;
-  uint32_t* bits;        // [eta * ntp * 32]
-  float4 *ukin, *xkin;   // [eta][p]
-  float4 *uwall, *xwall; // [nw][eta][p]
-  uint32_t* wbits;       // [nw][eta][nt]
-  uint32_t* work;        // active collision slots of this iteration
-  unsigned* work_count;  // their number
-  unsigned* work_count_next;  // the counter the next iteration appends to
-  unsigned long long* accx;  // [p][eta+1] fixed-point sums of rho0-weighted m.x
-  unsigned long long* accy;  //                                 ... of m.y
-  unsigned* accc;        // [p][eta+1] number of rho0-weighted incoming edges
-  const float* fix;      // fixed-point scale (a power of two) and |m| bound
-  unsigned* res_cur;     // residual slot of this iteration (consensus part)
-  unsigned* res_prev;    // residual slot of the previous iteration (primal part)
-  unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction
-};
-
-__device__ __forceinline__ float maxabs2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
-
-// Step 7 of the previous iteration for one edge: u^k from the stored u^{k-1},
-// the pending x^k and z^k.
-__device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, float2 u_prev,
-                                           float2 x_pend, float2 zk, float alpha, float& res) {
-  if (pinned) return mk(0.f, 0.f);
-  if (bprev) {
-    float2 d = x_pend - zk;
-    res = fmaxf(res, maxabs2(d));
-    return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
-  }
-  return keep ? u_prev : mk(0.f, 0.f);
-}
-
-// Step 5's sums in 64-bit fixed point: each FP32 m converts exactly (the scale
-// is a power of two chosen from the layout's extent), integer addition does not
-// depend on the order of the atomics, so z is deterministic and is the
-// correctly rounded mean of the incoming m's.  A non-finite or out-of-range m
-// sets status bit 1, which the consensus pass turns into a NaN residual.
-__device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m) {
-  const float scale = P.fix[0], bound = P.fix[1];
-  if (!(fabsf(m.x) <= bound && fabsf(m.y) <= bound)) {
-    atomicOr(P.status, 2u);
-    return;
-  }
-  const size_t node = (size_t)i * (P.eta + 1) + s;
-  atomicAdd(P.accx + node, (unsigned long long)__float2ll_rn(m.x * scale));
-  atomicAdd(P.accy + node, (unsigned long long)__float2ll_rn(m.y * scale));
-  atomicAdd(P.accc + node, 1u);
-}
-
-// Standard-ADMM mode, a factor that was feasible in the previous iteration:
-// its x^k was n^{k-1} = z^{k-1} - u^{k-1}, so step 7 needs no stored x.
-__device__ __forceinline__ float2 finish_u_feasible(bool pinned, float2 u_prev, float2 z_prev,
-                                                    float2 zk, float alpha, float& res) {
-  if (pinned) return mk(0.f, 0.f);
-  const float2 d = (z_prev - u_prev) - zk;
-  res = fmaxf(res, maxabs2(d));
-  return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
-}
-
-__device__ __forceinline__ float2 lo2(float4 v) { return mk(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return mk(v.z, v.w); }
-__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned* slot, float v) {
-  atomicMax(slot, __float_as_uint(v));
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
-  return v;
-}
-
-// Collision minimizer of one pair (Appendix C with equal weights rho on each
-// end, or infinite at a fixed end).  n: (i lo, i hi, j lo, j hi).
-__device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 njl, float2 njh,
-                                               bool pin_lo, bool pin_hi, float R, float rho,
-                                               float2& xil, float2& xih, float2& xjl, float2& xjh) {
-  float2 cl = njl - nil, ch = njh - nih;     // relative targets v = x_j - x_i
-  float2 sl = nil + njl, sh = nih + njh;     // sum coordinates x_i + x_j
-  xil = nil; xih = nih; xjl = njl; xjh = njh;
-  if (pin_lo && pin_hi) return;
-  if (pin_lo) {
-    float2 vh = disk_prox_pinned(cl, ch, R);
-    xih = 0.5f * (sh - vh);
-    xjh = 0.5f * (sh + vh);
-  } else if (pin_hi) {
-    float2 vl = disk_prox_pinned(ch, cl, R);
-    xil = 0.5f * (sl - vl);
-    xjl = 0.5f * (sl + vl);
-  } else {
-    float2 vl, vh;
-    float w = 0.5f * rho;  // rho rho / (rho + rho)
-    disk_prox_free(cl, ch, w, w, R, vl, vh);
-    xil = 0.5f * (sl - vl);
-    xjl = 0.5f * (sl + vl);
-    xih = 0.5f * (sh - vh);
-    xjh = 0.5f * (sh + vh);
-  }
-}
-
-// Kinetic factor (i, s): always active (it always sends rho0).  Finishes its
-// pending dual update, runs the closed-form minimizer and stores x and u.
-__device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float2 zl, float2 zh,
-                                               bool pin_lo, bool pin_hi, float& res) {
-  const size_t idx = (size_t)s * P.p + i;
-  const float4 u4 = P.ukin[idx], x4 = P.xkin[idx];
-  const float2 ul = finish_u(true, pin_lo, false, lo2(u4), lo2(x4), zl, P.alpha, res);
-  const float2 uh = finish_u(true, pin_hi, false, hi2(u4), hi2(x4), zh, P.alpha, res);
-  float2 xl, xh;
-  energy_prox(zl - ul, zh - uh, P.rho, pin_lo, pin_hi, P.cost[(size_t)i * P.eta + s], xl, xh);
-  P.xkin[idx] = pack(xl, xh);
-  P.ukin[idx] = pack(ul, uh);
-  if (!pin_lo) contribute(P, i, s, xl + ul);
-  if (!pin_hi) contribute(P, i, s + 1, xh + uh);
-}
-
-// Wall factor (w, i, s).  Called by a full warp (lane = agent of tile I).
-__device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
-                                            float2 zl, float2 zh, float r, bool pin_lo,
-                                            bool pin_hi, float& res) {
-  const int lane = threadIdx.x & 31;
-  const size_t widx = ((size_t)w * P.eta + s) * P.nt + I;
-  const uint32_t word = P.wbits[widx];
-  const bool bprev = vi && ((word >> lane) & 1u);
-  const size_t idx = ((size_t)w * P.eta + s) * P.p + i;
-  float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = u4;
-  if (vi && (P.dense || bprev)) u4 = P.uwall[idx];
-  if (bprev) x4 = P.xwall[idx];
-  float2 ul, uh;
-  if (P.admm && vi && !bprev) {
-    const int E1 = P.eta + 1;
-    ul = finish_u_feasible(pin_lo, lo2(u4), P.z_next[(size_t)i * E1 + s], zl, P.alpha, res);
-    uh = finish_u_feasible(pin_hi, hi2(u4), P.z_next[(size_t)i * E1 + s + 1], zh, P.alpha, res);
-  } else {
-    ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
-    uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
-  }
-  const float2 nl = zl - ul, nh = zh - uh;
-  const float4 W = P.walls[w];
-  const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
-  const bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
-  const uint32_t nw = __ballot_sync(FULL, act);
-  if (lane == 0 && nw != word) P.wbits[widx] = nw;
-  if (act) {
-    float2 xl = nl, xh = nh;
-    if (pin_lo && pin_hi) {
-    } else if (pin_lo) {
-      if (!capsule_prox_pinned(nl, nh, c0, c1, r, xh)) atomicOr(P.status, 1u);
-    } else if (pin_hi) {
-      if (!capsule_prox_pinned(nh, nl, c0, c1, r, xl)) atomicOr(P.status, 1u);
-    } else {
-      const float wgt = 0.5f * P.rho;
-      capsule_prox_free(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
-    }
-    P.xwall[idx] = pack(xl, xh);
-    P.uwall[idx] = pack(ul, uh);
-    if (!pin_lo) contribute(P, i, s, xl + ul);
-    if (!pin_hi) contribute(P, i, s + 1, xh + uh);
-  } else if (vi && P.dense) {
-    P.uwall[idx] = pack(ul, uh);
-  }
-}
-
-// Collision test of the n-trajectories (Eq. f_coll_def): does the relative
-// segment [cl, ch] pass closer than R to the origin?  Strict, so touching is
-// inactive.  Division-free: for an interior closest point, dist^2 =
-// cross(cl, d)^2 / |d|^2 is compared as cross^2 < R^2 |d|^2.
-__device__ __forceinline__ bool collides(float2 cl, float2 ch, float R) {
-  const float2 d = ch - cl;
-  const float dd = dot(d, d);
-  const float t = -dot(cl, d);
-  const float R2 = R * R;
-  const float c = cross(cl, d);
-  // endpoints, or an interior closest point (0 < t < |d|^2)
-  return (dot(cl, cl) < R2) | (dot(ch, ch) < R2) | ((t > 0.f) & (t < dd) & (c * c < R2 * dd));
-}
-
-__device__ __forceinline__ int tile_pair(int nt, int I, int J) {  // I <= J
-  return I * nt - I * (I - 1) / 2 + (J - I);
-}
-
-// Pass 1 of an iteration.  One CTA of 4 warps per (segment s, agent tiles
-// I <= J) block of 32 x 32 collision factors; each warp takes 8 rows, lane =
-// column agent j, and the row agents' data is held one per lane and broadcast
-// by shuffles.  Per row, the warp finishes the pending dual update of the
-// pairs that were active (step 7 of the previous iteration), forms n = z - u
-// (step 1), runs the collision test (steps 2-3: weight rho0 or 0), stores the
-// row's activity bits, and appends its active pairs to the global worklist.
-// DENSE streams the u record of every pair (PLAN_DENSE_STATE).
-//
-// Early out (gated state): agent i's segment lies in the disk of centre m_i
-// (its midpoint) and radius h_i (half its length), so the relative segment of
-// a pair stays at distance >= |m_j - m_i| - h_i - h_j from the origin.  Rows
-// where every pair has |m_j - m_i| > (h_i + h_j + r_i + r_j)(1 + 1e-5) cannot
-// collide and skip the exact test; the margin keeps the outcome identical to
-// running the exact test everywhere.
+// The single-planner kernels: thin wrappers over the per-block work.
 constexpr int TEST_WARPS = 4;
 constexpr int TEST_ROWS = TILE / TEST_WARPS;
 
 template <bool DENSE>
 __global__ void __launch_bounds__(32 * TEST_WARPS) test_kernel(Dev P) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int blk = blockIdx.x;
-  const int E1 = P.eta + 1;
-  float res = 0.f;
-  if (blk == 0 && threadIdx.x == 0) *P.res_cur = 0u;
-  const int s = blk / P.ntp;
-  const int2 IJ = P.tiles[blk - s * P.ntp];
-  const int I = IJ.x, J = IJ.y;
-  const bool diag = (I == J);
-  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-  const int r0 = warp * TEST_ROWS;
-  const int nrows = min(TEST_ROWS, P.p - I * TILE - r0);
-  if (nrows > 0) {  // warp-uniform
-    // column agent of this lane
-    const int j = J * TILE + lane;
-    const bool vj = j < P.p;
-    float2 zjl = mk(0.f, 0.f), zjh = zjl;
-    float rj = 0.f;
-    if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
-    // row agents r0 .. r0 + 7, held by lanes 0 .. 7
-    float2 ill = mk(0.f, 0.f), ilh = ill;
-    float rl = 0.f;
-    uint32_t wordl = 0u;
-    if (lane < nrows) {
-      const int il = I * TILE + r0 + lane;
-      ill = P.z[(size_t)il * E1 + s]; ilh = P.z[(size_t)il * E1 + s + 1]; rl = P.radius[il];
-      wordl = P.bits[(size_t)blk * TILE + r0 + lane];
-    }
-    float2 mj = mk(0.f, 0.f), ml = mj;
-    float bj = 0.f, bl = 0.f;
-    if (!DENSE) {
-      mj = 0.5f * (zjl + zjh);
-      bj = 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj;
-      ml = 0.5f * (ill + ilh);
-      bl = 0.5f * sqrtf(dot(ilh - ill, ilh - ill)) + rl;
-    }
-#pragma unroll 2
-    for (int q = 0; q < nrows; ++q) {
-      const int r = r0 + q;
-      const uint32_t word = __shfl_sync(FULL, wordl, q);
-      const bool valid = vj && (!diag || r < lane);
-      const float ri = __shfl_sync(FULL, rl, q);
-      bool act = false;
-      float2 uil = mk(0.f, 0.f), ujl = uil, uih = uil, ujh = uil;
-      const size_t row = (size_t)blk * TILE + r;
-      const size_t fid = row * TILE + lane;
-      if (!DENSE && word == 0u) {
-        // no pair of this row was active: every u is 0 by the reset rule, n = z
-        const float2 mi = mk(__shfl_sync(FULL, ml.x, q), __shfl_sync(FULL, ml.y, q));
-        const float br = __shfl_sync(FULL, bl, q) + bj;
-        const float2 dm = mj - mi;
-        const bool near = valid && dot(dm, dm) <= br * br * 1.00002f;
-        if (__any_sync(FULL, near)) {
-          const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
-          const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
-          act = near && collides(zjl - zil, zjh - zih, ri + rj);
-        }
-      } else {
-        const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
-        const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
-        const bool bprev = (word >> lane) & 1u;  // set only for valid pairs
-        if (DENSE && valid) {
-          const float4 a = P.ulo[fid], b = P.uhi[fid];
-          uil = lo2(a); ujl = hi2(a); uih = lo2(b); ujh = hi2(b);
-        }
-        if (bprev) {
-          // finish step 7 of the previous iteration for this pair
-          const float4 xa = P.xlo[fid], xb = P.xhi[fid];
-          float4 a, b;
-          if (DENSE) { a = pack(uil, ujl); b = pack(uih, ujh); }
-          else { a = P.ulo[fid]; b = P.uhi[fid]; }
-          uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zil, P.alpha, res);
-          ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), zjl, P.alpha, res);
-          uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
-          ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), zjh, P.alpha, res);
-        } else if (DENSE && P.admm && valid) {
-          // standard ADMM: the pair was feasible, so x^k = z^{k-1} - u^{k-1}
-          const float2 pil = P.z_next[(size_t)(I * TILE + r) * E1 + s];
-          const float2 pih = P.z_next[(size_t)(I * TILE + r) * E1 + s + 1];
-          const float2 pjl = P.z_next[(size_t)j * E1 + s], pjh = P.z_next[(size_t)j * E1 + s + 1];
-          uil = finish_u_feasible(pin_lo, uil, pil, zil, P.alpha, res);
-          ujl = finish_u_feasible(pin_lo, ujl, pjl, zjl, P.alpha, res);
-          uih = finish_u_feasible(pin_hi, uih, pih, zih, P.alpha, res);
-          ujh = finish_u_feasible(pin_hi, ujh, pjh, zjh, P.alpha, res);
-        } else if (DENSE && !P.keep) {
-          uil = ujl = uih = ujh = mk(0.f, 0.f);  // reset rule: inactive edges carry u = 0
-        }
-        if (pin_lo) { uil = mk(0.f, 0.f); ujl = uil; }
-        if (pin_hi) { uih = mk(0.f, 0.f); ujh = uih; }
-        act = valid && collides((zjl - ujl) - (zil - uil), (zjh - ujh) - (zih - uih), ri + rj);
-        if (DENSE && valid) {
-          P.ulo[fid] = pack(uil, ujl);
-          P.uhi[fid] = pack(uih, ujh);
-        }
-      }
-      const uint32_t nword = __ballot_sync(FULL, act);
-      if (nword != word && lane == 0) P.bits[row] = nword;
-      if (nword) {
-        if (!DENSE && act) {
-          P.ulo[fid] = pack(uil, ujl);
-          P.uhi[fid] = pack(uih, ujh);
-        }
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(P.work_count, (unsigned)__popc(nword));
-        base = __shfl_sync(FULL, base, 0);
-        if (act) P.work[base + __popc(nword & ((1u << lane) - 1u))] = (uint32_t)fid;
-      }
-    }
-  }
-  res = warp_max(res);
-  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+  test_block<DENSE, TEST_ROWS>(P, blockIdx.x);
 }
 
-// Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
-// s and one agent tile: warp f < 1 + n_walls takes factor kind f (0 =
-// kinetic, else wall f - 1), lane = agent.
-__global__ void __launch_bounds__(THREADS) segment_kernel(Dev P) {
-  const int s = blockIdx.x / P.nt;
-  const int I = blockIdx.x - s * P.nt;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = I * TILE + lane;
-  const bool vi = i < P.p;
-  const int E1 = P.eta + 1;
-  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-  float2 zl = mk(0.f, 0.f), zh = zl;
-  float r = 0.f;
-  if (vi) { zl = P.z[(size_t)i * E1 + s]; zh = P.z[(size_t)i * E1 + s + 1]; r = P.radius[i]; }
-  float res = 0.f;
-  for (int f = warp; f < 1 + P.nw; f += blockDim.x >> 5) {
-    if (f == 0) {
-      if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
-    } else {
-      wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
-    }
-  }
-  res = warp_max(res);
-  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
-}
+__global__ void __launch_bounds__(THREADS) segment_kernel(Dev P) { segment_block(P, blockIdx.x); }
 
-// Pass 2: the collision minimizer (Eq. coll_minimizer_problem through
-// App. C/D/I) of every active pair in the worklist, one thread per pair.
 __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
   const unsigned n = *P.work_count;
-  const int E1 = P.eta + 1;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const uint32_t fid = P.work[t];
-    const uint32_t row = fid >> 5, c = fid & 31;
-    const uint32_t blk = row >> 5, r = row & 31;
-    const int s = (int)(blk / P.ntp);
-    const int2 IJ = P.tiles[blk - (uint32_t)s * P.ntp];
-    const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
-    const float4 a = P.ulo[fid], b = P.uhi[fid];
-    const float2 nil = P.z[(size_t)i * E1 + s] - lo2(a), nih = P.z[(size_t)i * E1 + s + 1] - lo2(b);
-    const float2 njl = P.z[(size_t)j * E1 + s] - hi2(a), njh = P.z[(size_t)j * E1 + s + 1] - hi2(b);
-    float2 xil, xih, xjl, xjh;
-    const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-    coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, P.radius[i] + P.radius[j], P.rho,
-                   xil, xih, xjl, xjh);
-    P.xlo[fid] = pack(xil, xjl);
-    P.xhi[fid] = pack(xih, xjh);
-    if (!pin_lo) {
-      contribute(P, i, s, xil + lo2(a));
-      contribute(P, j, s, xjl + hi2(a));
-    }
-    if (!pin_hi) {
-      contribute(P, i, s + 1, xih + lo2(b));
-      contribute(P, j, s + 1, xjh + hi2(b));
-    }
-  }
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    prox_item(P, P.work[t]);
 }
 
-// Pass 3 (steps 5-6): z = sum(rho m) / sum(rho) per free break-point from the
-// fixed-point sums (every weight is rho0, so z is the mean of the incoming m;
-// no incoming weight means z is unchanged).  Clears the sums for the next
-// iteration.
 __global__ void consensus_kernel(Dev P) {
   const int nfree = (P.eta - 1) * P.p;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.work_count_next = 0u;
   float dz = 0.f;
   bool bad = false;
-  if (t < nfree) {
-    const int sp = 1 + t / P.p;
-    const int i = t - (sp - 1) * P.p;
-    const size_t node = (size_t)i * (P.eta + 1) + sp;
-    const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
-    const unsigned cnt = P.accc[node];
-    P.accx[node] = 0ull;
-    P.accy[node] = 0ull;
-    P.accc[node] = 0u;
-    const float2 zo = P.z[node];
-    float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
-    if (P.admm) {
-      // every edge is weighted; each feasible collision or wall factor sent
-      // m = n + u = z^k, added here in the same exact fixed point
-      const unsigned deg = 2u * (unsigned)(P.p - 1) + 2u + 2u * (unsigned)P.nw;
-      const long long rest = (long long)(deg - cnt);
-      const long long qx = __float2ll_rn(zo.x * P.fix[0]), qy = __float2ll_rn(zo.y * P.fix[0]);
-      const double den = (double)P.fix[0] * (double)deg;
-      zn = mk((float)((double)(sx + rest * qx) / den), (float)((double)(sy + rest * qy) / den));
-    } else if (cnt > 0u) {
-      const double den = (double)P.fix[0] * (double)cnt;
-      zn = mk((float)((double)sx / den), (float)((double)sy / den));
-    }
-    P.z_next[node] = zn;
-    bad = (*P.status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
-    dz = bad ? 0.f : maxabs2(zn - zo);
-  }
-  // a NaN or overflow anywhere makes the residual NaN (reported as PLAN_ENUMERIC)
-  dz = warp_max(dz);
-  const bool anybad = __any_sync(FULL, bad);
-  if ((threadIdx.x & 31) == 0) {
-    if (anybad) atomicMax(P.res_cur, 0x7fc00000u);
-    else if (dz > 0.f) atomic_max_nonneg(P.res_cur, dz);
-  }
+  if (t < nfree) consensus_node(P, t, dz, bad);
+  consensus_reduce(P, dz, bad);
 }
 
 // Fixed-point scale of the consensus sums: the largest power of two with
@@ -1179,9 +748,16 @@ plan_status plan_reset(plan_t h) {
   return PLAN_OK;
 }
 
-plan_status plan_create(const plan_config* cfg, const float* start, const float* goal,
+}  // extern "C"
+
+namespace {
+
+// Shared by plan_create and the batch: a batch member (member = true) has no
+// streams, events or pinned buffer of its own; the batch drives it.
+plan_status create_plan(const plan_config* cfg, const float* start, const float* goal,
                         const float* radius, const float* cost_w, const float* walls,
-                        void* workspace, size_t workspace_bytes, void* cuda_stream, plan_t* out) {
+                        void* workspace, size_t workspace_bytes, void* cuda_stream, bool member,
+                        plan_t* out) {
   if (!cfg || !start || !goal || !radius || !cost_w || !out) return fail(PLAN_EINVAL, "null argument");
   *out = nullptr;
   if (!sizes_ok(cfg)) return fail(PLAN_EINVAL, "p, eta or n_walls out of range");
@@ -1239,18 +815,20 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
     h->ws = static_cast<char*>(mem);
     h->own_ws = true;
   }
-  cudaError_t e = cudaMallocHost(&h->h_res, 16);
-  if (e != cudaSuccess) {
-    if (h->own_ws) cudaFree(h->ws);
-    delete h;
-    return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
-  }
-  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-    plan_destroy(h);
-    return fail(PLAN_ECUDA, "stream or event creation failed");
+  if (!member) {
+    cudaError_t e = cudaMallocHost(&h->h_res, 16);
+    if (e != cudaSuccess) {
+      if (h->own_ws) cudaFree(h->ws);
+      delete h;
+      return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+    }
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      plan_destroy(h);
+      return fail(PLAN_ECUDA, "stream or event creation failed");
+    }
   }
   st = upload_inputs(h, start, goal, radius, cost_w, walls);
   if (st == PLAN_OK) st = plan_reset(h);
@@ -1260,6 +838,17 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
   }
   *out = h;
   return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plan_status plan_create(const plan_config* cfg, const float* start, const float* goal,
+                        const float* radius, const float* cost_w, const float* walls,
+                        void* workspace, size_t workspace_bytes, void* cuda_stream, plan_t* out) {
+  return create_plan(cfg, start, goal, radius, cost_w, walls, workspace, workspace_bytes,
+                     cuda_stream, false, out);
 }
 
 void plan_destroy(plan_t h) {
@@ -1546,6 +1135,451 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
                            h.nw ? u_wall_out : nullptr, h.p > 1 ? act_coll_out : nullptr,
                            h.nw ? act_wall_out : nullptr, nullptr);
   return st;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many independent problems advanced together, one launch per pass
+// ---------------------------------------------------------------------------
+// Each member is an ordinary plan (its own workspace slice, no streams of its
+// own).  Every pass of an iteration is a single launch over the union of all
+// members' blocks: a block finds its member by binary search over a prefix
+// table of block counts and runs the same per-block code as a single plan,
+// on the member's descriptor copied into shared memory.  All members advance
+// in lockstep, so the descriptors only depend on the iteration's parity; a
+// member that has converged is frozen (its passes do nothing and its z is
+// carried over unchanged).  Iterations are replayed from CUDA graphs, and
+// three launch-shape knobs are chosen by timing (plan_batch_autotune).
+
+namespace {
+
+__device__ __forceinline__ int find_member(const int* pre, int n, int x) {
+  int lo = 0, hi = n - 1;  // largest b with pre[b] <= x (pre is non-decreasing)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool DENSE, int TROWS>
+__global__ void __launch_bounds__(32 * (TILE / TROWS)) batch_test_kernel(const Dev* tab, const int* pre,
+                                                                          int n, const uint8_t* frozen) {
+  __shared__ Dev sP;
+  __shared__ int sb, sblk;
+  if (threadIdx.x == 0) {
+    const int b = find_member(pre, n, blockIdx.x);
+    sb = b;
+    sblk = blockIdx.x - pre[b];
+    sP = tab[b];
+  }
+  __syncthreads();
+  if (frozen[sb]) return;
+  test_block<DENSE, TROWS>(sP, sblk);
+}
+
+__global__ void batch_segment_kernel(const Dev* tab, const int* pre, int n, const uint8_t* frozen) {
+  __shared__ Dev sP;
+  __shared__ int sb, sblk;
+  if (threadIdx.x == 0) {
+    const int b = find_member(pre, n, blockIdx.x);
+    sb = b;
+    sblk = blockIdx.x - pre[b];
+    sP = tab[b];
+  }
+  __syncthreads();
+  if (frozen[sb]) return;
+  segment_block(sP, sblk);
+}
+
+// Exclusive prefix of the members' worklist lengths (frozen members: 0).
+__global__ void batch_scan_kernel(const Dev* tab, int n, const uint8_t* frozen, int* pre_work) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  int sum = 0;
+  for (int b = t * per; b < min(n, (t + 1) * per); ++b) sum += frozen[b] ? 0 : (int)*tab[b].work_count;
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int q = 0; q < (int)blockDim.x; ++q) { const int v = part[q]; part[q] = acc; acc += v; }
+    pre_work[n] = acc;
+  }
+  __syncthreads();
+  int acc = part[t];
+  for (int b = t * per; b < min(n, (t + 1) * per); ++b) {
+    pre_work[b] = acc;
+    acc += frozen[b] ? 0 : (int)*tab[b].work_count;
+  }
+}
+
+__global__ void __launch_bounds__(256) batch_prox_kernel(const Dev* tab, const int* pre_work, int n) {
+  const int total = pre_work[n];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int b = find_member(pre_work, n, t);
+    const Dev& P = tab[b];
+    prox_item(P, P.work[t - pre_work[b]]);
+  }
+}
+
+// One thread per free break-point; each member's range is padded to whole
+// warps (and at least one warp, which also clears the member's next worklist
+// counter), so a warp never spans two members.
+__global__ void batch_consensus_kernel(const Dev* tab, const int* pre, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pre[n]) return;  // whole warps past the end
+  const int b = find_member(pre, n, t);
+  const Dev& P = tab[b];
+  const int tl = t - pre[b];
+  if (tl == 0) *P.work_count_next = 0u;
+  float dz = 0.f;
+  bool bad = false;
+  if (tl < (P.eta - 1) * P.p) consensus_node(P, tl, dz, bad);
+  consensus_reduce(P, dz, bad);
+}
+
+// The residual slot of each member's last iteration, gathered contiguously.
+__global__ void batch_gather_res(const Dev* tab, int n, float* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) out[b] = __uint_as_float(*tab[b].res_prev);
+}
+
+}  // namespace
+
+struct plan_batch_s {
+  int n = 0;
+  std::vector<plan_t> m;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  char* ws = nullptr;
+  bool own_ws = false;
+  size_t total = 0;
+  int k = 0;
+  bool dense = false;
+  // device tables (in the workspace tail)
+  Dev* tab[2] = {nullptr, nullptr};
+  int *pre_test = nullptr, *pre_seg = nullptr, *pre_node = nullptr, *pre_work = nullptr;
+  uint8_t* frozen = nullptr;
+  float* res = nullptr;
+  int ntest = 0, nseg = 0, nnode = 0;
+  std::vector<uint8_t> h_frozen;
+  std::vector<int> conv_iter;
+  int warm = 0;  // largest warm-up length among members
+  // launch-shape knobs: rows per warp of the test pass, prox CTAs per SM, graph length
+  int trows = 8, prox_mult = 2, glen = 8;
+  int prox_grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int gexec_trows = 0, gexec_mult = 0, gexec_len = 0;
+};
+
+namespace {
+
+size_t batch_tables_bytes(int n) {
+  return a256(2 * (size_t)n * sizeof(Dev)) + 4 * a256(((size_t)n + 1) * 4) + a256(n) + a256((size_t)n * 4);
+}
+
+plan_status batch_tables(plan_batch_s* B) {
+  // descriptors of both parities; members advance together, so their z buffer
+  // is the iteration's parity (no flip for eta = 1)
+  for (int par = 0; par < 2; ++par) {
+    std::vector<Dev> d(B->n);
+    for (int b = 0; b < B->n; ++b) {
+      plan_t h = B->m[b];
+      const int kk = (B->k & ~1) + par;
+      h->k = kk;
+      h->cur = (h->eta > 1) ? (kk & 1) : 0;
+      d[b] = h->dev(kk);
+      // the table serves every later iteration of this parity, so the
+      // previous iteration's residual slot is always the other one
+      d[b].res_prev = h->at<unsigned>(h->L.res) + ((kk + 1) & 1);
+    }
+    CK(cudaMemcpyAsync(B->tab[par], d.data(), d.size() * sizeof(Dev), cudaMemcpyHostToDevice, B->stream));
+  }
+  for (int b = 0; b < B->n; ++b) {  // restore the members' own counters
+    plan_t h = B->m[b];
+    h->k = B->k;
+    h->cur = (h->eta > 1) ? (B->k & 1) : 0;
+  }
+  CK(cudaStreamSynchronize(B->stream));
+  return PLAN_OK;
+}
+
+template <int TROWS>
+void launch_batch_test(plan_batch_s* B, const Dev* tab, cudaStream_t s) {
+  constexpr int threads = 32 * (TILE / TROWS);
+  if (B->dense) batch_test_kernel<true, TROWS><<<B->ntest, threads, 0, s>>>(tab, B->pre_test, B->n, B->frozen);
+  else batch_test_kernel<false, TROWS><<<B->ntest, threads, 0, s>>>(tab, B->pre_test, B->n, B->frozen);
+}
+
+plan_status enqueue_batch_iteration(plan_batch_s* B, int parity, cudaStream_t s) {
+  const Dev* tab = B->tab[parity];
+  if (B->trows == 4) launch_batch_test<4>(B, tab, s);
+  else if (B->trows == 16) launch_batch_test<16>(B, tab, s);
+  else launch_batch_test<8>(B, tab, s);
+  batch_segment_kernel<<<B->nseg, THREADS, 0, s>>>(tab, B->pre_seg, B->n, B->frozen);
+  batch_scan_kernel<<<1, 1024, 0, s>>>(tab, B->n, B->frozen, B->pre_work);
+  batch_prox_kernel<<<B->prox_grid * B->prox_mult, 256, 0, s>>>(tab, B->pre_work, B->n);
+  batch_consensus_kernel<<<(B->nnode + 255) / 256, 256, 0, s>>>(tab, B->pre_node, B->n);
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+void batch_advance(plan_batch_s* B, int iters) {
+  B->k += iters;
+  for (plan_t h : B->m) {
+    h->k = B->k;
+    h->cur = (h->eta > 1) ? (B->k & 1) : 0;
+  }
+}
+
+// iters iterations: graphs of glen (even) iterations while past every
+// member's rho warm-up, direct launches otherwise.
+plan_status batch_run(plan_batch_s* B, int iters) {
+  while (iters > 0) {
+    const bool graphable = B->k >= B->warm && (B->k & 1) == 0 && iters >= B->glen;
+    if (graphable) {
+      if (!B->gexec || B->gexec_trows != B->trows || B->gexec_mult != B->prox_mult ||
+          B->gexec_len != B->glen) {
+        if (B->gexec) { cudaGraphExecDestroy(B->gexec); B->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+        plan_status st = PLAN_OK;
+        for (int q = 0; q < B->glen && st == PLAN_OK; ++q) st = enqueue_batch_iteration(B, q & 1, B->cap);
+        cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+        if (st != PLAN_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return fail(PLAN_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&B->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(PLAN_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+        B->gexec_trows = B->trows; B->gexec_mult = B->prox_mult; B->gexec_len = B->glen;
+      }
+      CK(cudaGraphLaunch(B->gexec, B->stream));
+      batch_advance(B, B->glen);
+      iters -= B->glen;
+    } else {
+      if (B->k < B->warm) {  // rho changes with k during the warm-up
+        plan_status st = batch_tables(B);
+        if (st != PLAN_OK) return st;
+      }
+      plan_status st = enqueue_batch_iteration(B, B->k & 1, B->stream);
+      if (st != PLAN_OK) return st;
+      batch_advance(B, 1);
+      iters -= 1;
+    }
+  }
+  return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plan_status plan_batch_workspace_size(int n, const plan_config* cfgs, size_t* bytes) {
+  if (n < 1 || !cfgs || !bytes) return fail(PLAN_EINVAL, "null argument or n < 1");
+  size_t tot = 0;
+  for (int b = 0; b < n; ++b) {
+    if (!sizes_ok(&cfgs[b])) return fail(PLAN_EINVAL, "member %d: p, eta or n_walls out of range", b);
+    tot += a256(layout_for(&cfgs[b]).total);
+  }
+  *bytes = tot + batch_tables_bytes(n);
+  return PLAN_OK;
+}
+
+plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const* start,
+                              const float* const* goal, const float* const* radius,
+                              const float* const* cost_w, const float* const* walls,
+                              void* workspace, size_t workspace_bytes, void* cuda_stream,
+                              plan_batch_t* out) {
+  if (n < 1 || !cfgs || !start || !goal || !radius || !cost_w || !out)
+    return fail(PLAN_EINVAL, "null argument or n < 1");
+  *out = nullptr;
+  const unsigned modes = PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM;
+  for (int b = 1; b < n; ++b)
+    if ((cfgs[b].flags & modes) != (cfgs[0].flags & modes))
+      return fail(PLAN_EINVAL, "batch members must share the state-mode flags");
+  size_t need = 0;
+  plan_status st = plan_batch_workspace_size(n, cfgs, &need);
+  if (st != PLAN_OK) return st;
+  plan_batch_s* B = new plan_batch_s();
+  B->n = n;
+  B->stream = (cudaStream_t)cuda_stream;
+  B->dense = (cfgs[0].flags & modes) != 0;
+  if (workspace) {
+    if (workspace_bytes < need) { delete B; return fail(PLAN_ENOMEM, "workspace of %zu bytes, %zu needed", workspace_bytes, need); }
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) { delete B; return fail(PLAN_EINVAL, "workspace must be 256-byte aligned"); }
+    B->ws = static_cast<char*>(workspace);
+  } else {
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, need) != cudaSuccess) { delete B; return fail(PLAN_ENOMEM, "cudaMalloc(%zu) failed", need); }
+    B->ws = static_cast<char*>(mem);
+    B->own_ws = true;
+  }
+  B->total = need;
+  size_t off = 0;
+  for (int b = 0; b < n; ++b) {
+    const size_t sz = a256(layout_for(&cfgs[b]).total);
+    plan_t h = nullptr;
+    st = create_plan(&cfgs[b], start[b], goal[b], radius[b], cost_w[b], walls ? walls[b] : nullptr,
+                     B->ws + off, sz, cuda_stream, true, &h);
+    if (st != PLAN_OK) {
+      plan_batch_destroy(B);
+      char msg[600];
+      snprintf(msg, sizeof msg, "member %d: %s", b, g_err.c_str());
+      return fail(st, "%s", msg);
+    }
+    B->m.push_back(h);
+    B->warm = std::max(B->warm, cfgs[b].warm_iters);
+    off += sz;
+  }
+  char* t = B->ws + off;
+  B->tab[0] = reinterpret_cast<Dev*>(t);
+  B->tab[1] = B->tab[0] + n;
+  t += a256(2 * (size_t)n * sizeof(Dev));
+  B->pre_test = reinterpret_cast<int*>(t); t += a256(((size_t)n + 1) * 4);
+  B->pre_seg = reinterpret_cast<int*>(t); t += a256(((size_t)n + 1) * 4);
+  B->pre_node = reinterpret_cast<int*>(t); t += a256(((size_t)n + 1) * 4);
+  B->pre_work = reinterpret_cast<int*>(t); t += a256(((size_t)n + 1) * 4);
+  B->frozen = reinterpret_cast<uint8_t*>(t); t += a256(n);
+  B->res = reinterpret_cast<float*>(t);
+  std::vector<int> pt(n + 1, 0), ps(n + 1, 0), pn(n + 1, 0);
+  for (int b = 0; b < n; ++b) {
+    plan_t h = B->m[b];
+    pt[b + 1] = pt[b] + h->eta * h->ntp;
+    ps[b + 1] = ps[b] + h->eta * h->nt;
+    const int nfree = (h->eta - 1) * h->p;
+    pn[b + 1] = pn[b] + std::max(32, (nfree + 31) / 32 * 32);
+  }
+  B->ntest = pt[n]; B->nseg = ps[n]; B->nnode = pn[n];
+  B->h_frozen.assign(n, 0);
+  B->conv_iter.assign(n, -1);
+  cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->pre_test, pt.data(), (n + 1) * 4, cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->pre_seg, ps.data(), (n + 1) * 4, cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->pre_node, pn.data(), (n + 1) * 4, cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->frozen, B->h_frozen.data(), n, cudaMemcpyHostToDevice, B->stream);
+  if (e != cudaSuccess) { plan_batch_destroy(B); return fail(PLAN_ECUDA, "batch setup failed: %s", cudaGetErrorString(e)); }
+  st = ensure_prox_grid(B->m[0]);
+  if (st == PLAN_OK) { B->prox_grid = std::max(1, B->m[0]->prox_grid / 4); st = batch_tables(B); }
+  if (st != PLAN_OK) { plan_batch_destroy(B); return st; }
+  *out = B;
+  return PLAN_OK;
+}
+
+plan_status plan_batch_iterate(plan_batch_t B, int k_iters) {
+  if (!B || k_iters < 0) return fail(PLAN_EINVAL, "bad argument");
+  return batch_run(B, k_iters);
+}
+
+plan_status plan_batch_solve(plan_batch_t B, int* iters_done, float* residual, int* n_converged) {
+  if (!B) return fail(PLAN_EINVAL, "null batch");
+  int max_iter = 0, check = 1 << 30;
+  for (plan_t h : B->m) { max_iter = std::max(max_iter, h->cfg.max_iter); check = std::min(check, h->cfg.check_every); }
+  check = std::max(check, 2);
+  if (check & 1) ++check;  // graph chunks are whole pairs of iterations
+  std::vector<float> res(B->n, INFINITY);
+  int nconv = 0;
+  for (int b = 0; b < B->n; ++b) nconv += B->h_frozen[b] ? 1 : 0;
+  while (B->k < max_iter && nconv < B->n) {
+    const int iters = std::min(check, max_iter - B->k);
+    plan_status st = batch_run(B, iters);
+    if (st != PLAN_OK) return st;
+    // residual of every member's last iteration: the consensus part is in its
+    // slot; the primal part needs the next finishing step
+    for (int b = 0; b < B->n; ++b) {
+      if (B->h_frozen[b]) continue;
+      plan_t h = B->m[b];
+      Dev P = h->dev(h->k);
+      residual_kernel<<<64, 256, 0, B->stream>>>(P);
+    }
+    batch_gather_res<<<(B->n + 255) / 256, 256, 0, B->stream>>>(B->tab[B->k & 1], B->n, B->res);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(res.data(), B->res, B->n * 4, cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    bool changed = false;
+    for (int b = 0; b < B->n; ++b) {
+      if (B->h_frozen[b]) continue;
+      plan_t h = B->m[b];
+      if (!(res[b] == res[b])) return fail(PLAN_ENUMERIC, "member %d: non-finite residual", b);
+      if (res[b] < h->cfg.tol || B->k >= h->cfg.max_iter) {
+        B->h_frozen[b] = 1;
+        if (res[b] < h->cfg.tol) { B->conv_iter[b] = B->k; ++nconv; }
+        changed = true;
+      }
+    }
+    if (changed) CK(cudaMemcpyAsync(B->frozen, B->h_frozen.data(), B->n, cudaMemcpyHostToDevice, B->stream));
+    int frozen = 0;
+    for (int b = 0; b < B->n; ++b) frozen += B->h_frozen[b];
+    if (frozen == B->n) break;
+  }
+  CK(cudaStreamSynchronize(B->stream));
+  for (int b = 0; b < B->n; ++b) {
+    if (iters_done) iters_done[b] = B->conv_iter[b] >= 0 ? B->conv_iter[b] : B->k;
+    if (residual) residual[b] = res[b];
+  }
+  if (n_converged) *n_converged = nconv;
+  return PLAN_OK;
+}
+
+plan_status plan_batch_get_trajectory(plan_batch_t B, int member, float* z, int on_device) {
+  if (!B || member < 0 || member >= B->n) return fail(PLAN_EINVAL, "bad member index");
+  return plan_get_trajectory(B->m[member], z, on_device);
+}
+
+plan_status plan_batch_autotune(plan_batch_t B, int iters_per_candidate, int* choice) {
+  if (!B || iters_per_candidate < 2) return fail(PLAN_EINVAL, "bad argument");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int tr[3] = {4, 8, 16}, mu[3] = {1, 2, 4}, gl[2] = {2, 8};
+  float best = INFINITY;
+  int bt = B->trows, bm = B->prox_mult, bg = B->glen;
+  if (B->k & 1) { plan_status st = batch_run(B, 1); if (st != PLAN_OK) return st; }
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c)
+      for (int g = 0; g < 2; ++g) {
+        B->trows = tr[a]; B->prox_mult = mu[c]; B->glen = gl[g];
+        const int iters = std::max(iters_per_candidate / gl[g], 1) * gl[g];
+        plan_status st = batch_run(B, gl[g]);  // capture outside the timing
+        if (st != PLAN_OK) return st;
+        CK(cudaEventRecord(e0, B->stream));
+        st = batch_run(B, iters);
+        if (st != PLAN_OK) return st;
+        CK(cudaEventRecord(e1, B->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / iters < best) { best = ms / iters; bt = tr[a]; bm = mu[c]; bg = gl[g]; }
+      }
+  B->trows = bt; B->prox_mult = bm; B->glen = bg;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (choice) { choice[0] = bt; choice[1] = bm; choice[2] = bg; }
+  return PLAN_OK;
+}
+
+plan_status plan_batch_set_shape(plan_batch_t B, int rows_per_warp, int prox_ctas_per_sm,
+                                 int iterations_per_graph) {
+  if (!B) return fail(PLAN_EINVAL, "null batch");
+  if (rows_per_warp != 4 && rows_per_warp != 8 && rows_per_warp != 16)
+    return fail(PLAN_EINVAL, "rows_per_warp must be 4, 8 or 16");
+  if (prox_ctas_per_sm < 1 || prox_ctas_per_sm > 8) return fail(PLAN_EINVAL, "prox_ctas_per_sm must be 1..8");
+  if (iterations_per_graph < 2 || (iterations_per_graph & 1))
+    return fail(PLAN_EINVAL, "iterations_per_graph must be even and >= 2");
+  B->trows = rows_per_warp;
+  B->prox_mult = prox_ctas_per_sm;
+  B->glen = iterations_per_graph;
+  return PLAN_OK;
+}
+
+void plan_batch_destroy(plan_batch_t B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream); else cudaDeviceSynchronize();
+  for (plan_t h : B->m) plan_destroy(h);
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->own_ws && B->ws) cudaFree(B->ws);
+  delete B;
 }
 
 }  // extern "C"

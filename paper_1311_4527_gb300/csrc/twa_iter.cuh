@@ -1,0 +1,467 @@
+// twa_iter.cuh -- the per-block work of one TWA iteration (Appendix B steps
+// 1-7 over the factor graph of Section 3.3 of Bento et al., NIPS 2013), shared
+// by the single-planner kernels (plan.cu) and the batched ones (batch.cu).
+//
+// Pass 1, test_block: one block per (segment s, agent tiles I <= J) of 32 x 32
+//   collision factors: finish the deferred dual update of the pairs that were
+//   active (step 7 of the previous iteration), n = z - u (step 1), collision
+//   test and weight (steps 2-3), activity bits, worklist of active pairs.
+// segment_block: the kinetic and wall factors of one (segment, agent tile).
+// Pass 2, prox_item: the collision minimizer of one active pair; adds its
+//   m = x + u to the consensus sums.
+// Pass 3, consensus_node: z = sum m / count per free break-point (step 5).
+//
+// Step 7 needs z^{k+1}, which exists only after every factor ran, so x^{k+1}
+// of the active factors is stored and u^{k+1} = u^k + alpha (x^{k+1} -
+// z^{k+1}) is finished at the start of the next iteration.  Back weights
+// (step 6) are rho0 at every interior node (the kinetic factors always send
+// rho0 there) and infinity at the fixed ends; u on an edge whose forward
+// weight was 0, or whose node is fixed, is 0.
+//
+// Collision-factor state lives in tile order: block blk = s * ntp + tp holds
+// the 32 x 32 pair slots (row r = i - 32 I, column c = j - 32 J), so a warp
+// streams one row as 32 consecutive float4 (512 B).  Per slot:
+//   ulo[slot] = (u_i(s), u_j(s))       uhi[slot] = (u_i(s+1), u_j(s+1))
+//   xlo / xhi = pending x^{k+1}, read and written only for active factors
+//   bits[blk * 32 + r] bit c = forward weight rho0 in the last iteration.
+// With the dense state the u record of every slot is read and written each
+// iteration; otherwise only those of factors whose bit is set (every other u
+// is 0 by the reset rule), which leaves 1 bit per factor of state traffic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "twa_math.cuh"
+
+namespace {
+
+using namespace twa;
+
+constexpr int TILE = 32;
+constexpr int WARPS = 8;
+constexpr int THREADS = TILE * WARPS;
+constexpr int ROWS = TILE / WARPS;  // rows of a tile per warp
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Dev {
+  int p, eta, nw, nt, ntp;
+  float rho, alpha;
+  int dense, keep, admm;
+  const float2* z;       // z^k, [p][eta+1]
+  float2* z_next;        // z^{k+1}; until the consensus pass writes it, z^{k-1}
+  const float* radius;   // [p]
+  const float* cost;     // [p][eta], kinetic coefficients c_{i,s}
+  const float4* walls;   // [nw] (xL.x, xL.y, xR.x, xR.y)
+  const int2* tiles;     // [ntp] (I, J), I <= J
+  float4 *ulo, *uhi, *xlo, *xhi;
+  uint32_t* bits;        // [eta * ntp * 32]
+  float4 *ukin, *xkin;   // [eta][p]
+  float4 *uwall, *xwall; // [nw][eta][p]
+  uint32_t* wbits;       // [nw][eta][nt]
+  uint32_t* work;        // active collision slots of this iteration
+  unsigned* work_count;  // their number
+  unsigned* work_count_next;  // the counter the next iteration appends to
+  unsigned long long* accx;  // [p][eta+1] fixed-point sums of rho0-weighted m.x
+  unsigned long long* accy;  //                                 ... of m.y
+  unsigned* accc;        // [p][eta+1] number of rho0-weighted incoming edges
+  const float* fix;      // fixed-point scale (a power of two) and |m| bound
+  unsigned* res_cur;     // residual slot of this iteration (consensus part)
+  unsigned* res_prev;    // residual slot of the previous iteration (primal part)
+  unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction
+};
+
+__device__ __forceinline__ float maxabs2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+
+// Step 7 of the previous iteration for one edge: u^k from the stored u^{k-1},
+// the pending x^k and z^k.
+__device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, float2 u_prev,
+                                           float2 x_pend, float2 zk, float alpha, float& res) {
+  if (pinned) return mk(0.f, 0.f);
+  if (bprev) {
+    float2 d = x_pend - zk;
+    res = fmaxf(res, maxabs2(d));
+    return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
+  }
+  return keep ? u_prev : mk(0.f, 0.f);
+}
+
+// Step 5's sums in 64-bit fixed point: each FP32 m converts exactly (the scale
+// is a power of two chosen from the layout's extent), integer addition does not
+// depend on the order of the atomics, so z is deterministic and is the
+// correctly rounded mean of the incoming m's.  A non-finite or out-of-range m
+// sets status bit 1, which the consensus pass turns into a NaN residual.
+__device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m) {
+  const float scale = P.fix[0], bound = P.fix[1];
+  if (!(fabsf(m.x) <= bound && fabsf(m.y) <= bound)) {
+    atomicOr(P.status, 2u);
+    return;
+  }
+  const size_t node = (size_t)i * (P.eta + 1) + s;
+  atomicAdd(P.accx + node, (unsigned long long)__float2ll_rn(m.x * scale));
+  atomicAdd(P.accy + node, (unsigned long long)__float2ll_rn(m.y * scale));
+  atomicAdd(P.accc + node, 1u);
+}
+
+// Standard-ADMM mode, a factor that was feasible in the previous iteration:
+// its x^k was n^{k-1} = z^{k-1} - u^{k-1}, so step 7 needs no stored x.
+__device__ __forceinline__ float2 finish_u_feasible(bool pinned, float2 u_prev, float2 z_prev,
+                                                    float2 zk, float alpha, float& res) {
+  if (pinned) return mk(0.f, 0.f);
+  const float2 d = (z_prev - u_prev) - zk;
+  res = fmaxf(res, maxabs2(d));
+  return mk(u_prev.x + alpha * d.x, u_prev.y + alpha * d.y);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return mk(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return mk(v.z, v.w); }
+__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* slot, float v) {
+  atomicMax(slot, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// Collision minimizer of one pair (Appendix C with equal weights rho on each
+// end, or infinite at a fixed end).  n: (i lo, i hi, j lo, j hi).
+__device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 njl, float2 njh,
+                                               bool pin_lo, bool pin_hi, float R, float rho,
+                                               float2& xil, float2& xih, float2& xjl, float2& xjh) {
+  float2 cl = njl - nil, ch = njh - nih;     // relative targets v = x_j - x_i
+  float2 sl = nil + njl, sh = nih + njh;     // sum coordinates x_i + x_j
+  xil = nil; xih = nih; xjl = njl; xjh = njh;
+  if (pin_lo && pin_hi) return;
+  if (pin_lo) {
+    float2 vh = disk_prox_pinned(cl, ch, R);
+    xih = 0.5f * (sh - vh);
+    xjh = 0.5f * (sh + vh);
+  } else if (pin_hi) {
+    float2 vl = disk_prox_pinned(ch, cl, R);
+    xil = 0.5f * (sl - vl);
+    xjl = 0.5f * (sl + vl);
+  } else {
+    float2 vl, vh;
+    float w = 0.5f * rho;  // rho rho / (rho + rho)
+    disk_prox_free(cl, ch, w, w, R, vl, vh);
+    xil = 0.5f * (sl - vl);
+    xjl = 0.5f * (sl + vl);
+    xih = 0.5f * (sh - vh);
+    xjh = 0.5f * (sh + vh);
+  }
+}
+
+// Kinetic factor (i, s): always active (it always sends rho0).  Finishes its
+// pending dual update, runs the closed-form minimizer and stores x and u.
+__device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float2 zl, float2 zh,
+                                               bool pin_lo, bool pin_hi, float& res) {
+  const size_t idx = (size_t)s * P.p + i;
+  const float4 u4 = P.ukin[idx], x4 = P.xkin[idx];
+  const float2 ul = finish_u(true, pin_lo, false, lo2(u4), lo2(x4), zl, P.alpha, res);
+  const float2 uh = finish_u(true, pin_hi, false, hi2(u4), hi2(x4), zh, P.alpha, res);
+  float2 xl, xh;
+  energy_prox(zl - ul, zh - uh, P.rho, pin_lo, pin_hi, P.cost[(size_t)i * P.eta + s], xl, xh);
+  P.xkin[idx] = pack(xl, xh);
+  P.ukin[idx] = pack(ul, uh);
+  if (!pin_lo) contribute(P, i, s, xl + ul);
+  if (!pin_hi) contribute(P, i, s + 1, xh + uh);
+}
+
+// Wall factor (w, i, s).  Called by a full warp (lane = agent of tile I).
+__device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
+                                            float2 zl, float2 zh, float r, bool pin_lo,
+                                            bool pin_hi, float& res) {
+  const int lane = threadIdx.x & 31;
+  const size_t widx = ((size_t)w * P.eta + s) * P.nt + I;
+  const uint32_t word = P.wbits[widx];
+  const bool bprev = vi && ((word >> lane) & 1u);
+  const size_t idx = ((size_t)w * P.eta + s) * P.p + i;
+  float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = u4;
+  if (vi && (P.dense || bprev)) u4 = P.uwall[idx];
+  if (bprev) x4 = P.xwall[idx];
+  float2 ul, uh;
+  if (P.admm && vi && !bprev) {
+    const int E1 = P.eta + 1;
+    ul = finish_u_feasible(pin_lo, lo2(u4), P.z_next[(size_t)i * E1 + s], zl, P.alpha, res);
+    uh = finish_u_feasible(pin_hi, hi2(u4), P.z_next[(size_t)i * E1 + s + 1], zh, P.alpha, res);
+  } else {
+    ul = finish_u(bprev, pin_lo, P.keep, lo2(u4), lo2(x4), zl, P.alpha, res);
+    uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
+  }
+  const float2 nl = zl - ul, nh = zh - uh;
+  const float4 W = P.walls[w];
+  const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
+  const bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
+  const uint32_t nw = __ballot_sync(FULL, act);
+  if (lane == 0 && nw != word) P.wbits[widx] = nw;
+  if (act) {
+    float2 xl = nl, xh = nh;
+    if (pin_lo && pin_hi) {
+    } else if (pin_lo) {
+      if (!capsule_prox_pinned(nl, nh, c0, c1, r, xh)) atomicOr(P.status, 1u);
+    } else if (pin_hi) {
+      if (!capsule_prox_pinned(nh, nl, c0, c1, r, xl)) atomicOr(P.status, 1u);
+    } else {
+      const float wgt = 0.5f * P.rho;
+      capsule_prox_free(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
+    }
+    P.xwall[idx] = pack(xl, xh);
+    P.uwall[idx] = pack(ul, uh);
+    if (!pin_lo) contribute(P, i, s, xl + ul);
+    if (!pin_hi) contribute(P, i, s + 1, xh + uh);
+  } else if (vi && P.dense) {
+    P.uwall[idx] = pack(ul, uh);
+  }
+}
+
+// Collision test of the n-trajectories (Eq. f_coll_def): does the relative
+// segment [cl, ch] pass closer than R to the origin?  Strict, so touching is
+// inactive.  Division-free: for an interior closest point, dist^2 =
+// cross(cl, d)^2 / |d|^2 is compared as cross^2 < R^2 |d|^2.
+__device__ __forceinline__ bool collides(float2 cl, float2 ch, float R) {
+  const float2 d = ch - cl;
+  const float dd = dot(d, d);
+  const float t = -dot(cl, d);
+  const float R2 = R * R;
+  const float c = cross(cl, d);
+  // endpoints, or an interior closest point (0 < t < |d|^2)
+  return (dot(cl, cl) < R2) | (dot(ch, ch) < R2) | ((t > 0.f) & (t < dd) & (c * c < R2 * dd));
+}
+
+__device__ __forceinline__ int tile_pair(int nt, int I, int J) {  // I <= J
+  return I * nt - I * (I - 1) / 2 + (J - I);
+}
+
+// Pass 1 of an iteration.  One CTA of 4 warps per (segment s, agent tiles
+// I <= J) block of 32 x 32 collision factors; each warp takes 8 rows, lane =
+// column agent j, and the row agents' data is held one per lane and broadcast
+// by shuffles.  Per row, the warp finishes the pending dual update of the
+// pairs that were active (step 7 of the previous iteration), forms n = z - u
+// (step 1), runs the collision test (steps 2-3: weight rho0 or 0), stores the
+// row's activity bits, and appends its active pairs to the global worklist.
+// DENSE streams the u record of every pair (PLAN_DENSE_STATE).
+//
+// Early out (gated state): agent i's segment lies in the disk of centre m_i
+// (its midpoint) and radius h_i (half its length), so the relative segment of
+// a pair stays at distance >= |m_j - m_i| - h_i - h_j from the origin.  Rows
+// where every pair has |m_j - m_i| > (h_i + h_j + r_i + r_j)(1 + 1e-5) cannot
+// collide and skip the exact test; the margin keeps the outcome identical to
+// running the exact test everywhere.
+// TROWS rows per warp, TILE / TROWS warps per block (the launch shape the
+// batched autotuner varies).
+template <bool DENSE, int TROWS>
+__device__ __forceinline__ void test_block(const Dev& P, int blk) {
+  constexpr int TEST_ROWS = TROWS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int E1 = P.eta + 1;
+  float res = 0.f;
+  if (blk == 0 && threadIdx.x == 0) *P.res_cur = 0u;
+  const int s = blk / P.ntp;
+  const int2 IJ = P.tiles[blk - s * P.ntp];
+  const int I = IJ.x, J = IJ.y;
+  const bool diag = (I == J);
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  const int r0 = warp * TEST_ROWS;
+  const int nrows = min(TEST_ROWS, P.p - I * TILE - r0);
+  if (nrows > 0) {  // warp-uniform
+    // column agent of this lane
+    const int j = J * TILE + lane;
+    const bool vj = j < P.p;
+    float2 zjl = mk(0.f, 0.f), zjh = zjl;
+    float rj = 0.f;
+    if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
+    // row agents r0 .. r0 + 7, held by lanes 0 .. 7
+    float2 ill = mk(0.f, 0.f), ilh = ill;
+    float rl = 0.f;
+    uint32_t wordl = 0u;
+    if (lane < nrows) {
+      const int il = I * TILE + r0 + lane;
+      ill = P.z[(size_t)il * E1 + s]; ilh = P.z[(size_t)il * E1 + s + 1]; rl = P.radius[il];
+      wordl = P.bits[(size_t)blk * TILE + r0 + lane];
+    }
+    float2 mj = mk(0.f, 0.f), ml = mj;
+    float bj = 0.f, bl = 0.f;
+    if (!DENSE) {
+      mj = 0.5f * (zjl + zjh);
+      bj = 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj;
+      ml = 0.5f * (ill + ilh);
+      bl = 0.5f * sqrtf(dot(ilh - ill, ilh - ill)) + rl;
+    }
+#pragma unroll 2
+    for (int q = 0; q < nrows; ++q) {
+      const int r = r0 + q;
+      const uint32_t word = __shfl_sync(FULL, wordl, q);
+      const bool valid = vj && (!diag || r < lane);
+      const float ri = __shfl_sync(FULL, rl, q);
+      bool act = false;
+      float2 uil = mk(0.f, 0.f), ujl = uil, uih = uil, ujh = uil;
+      const size_t row = (size_t)blk * TILE + r;
+      const size_t fid = row * TILE + lane;
+      if (!DENSE && word == 0u) {
+        // no pair of this row was active: every u is 0 by the reset rule, n = z
+        const float2 mi = mk(__shfl_sync(FULL, ml.x, q), __shfl_sync(FULL, ml.y, q));
+        const float br = __shfl_sync(FULL, bl, q) + bj;
+        const float2 dm = mj - mi;
+        const bool near = valid && dot(dm, dm) <= br * br * 1.00002f;
+        if (__any_sync(FULL, near)) {
+          const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
+          const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
+          act = near && collides(zjl - zil, zjh - zih, ri + rj);
+        }
+      } else {
+        const float2 zil = mk(__shfl_sync(FULL, ill.x, q), __shfl_sync(FULL, ill.y, q));
+        const float2 zih = mk(__shfl_sync(FULL, ilh.x, q), __shfl_sync(FULL, ilh.y, q));
+        const bool bprev = (word >> lane) & 1u;  // set only for valid pairs
+        if (DENSE && valid) {
+          const float4 a = P.ulo[fid], b = P.uhi[fid];
+          uil = lo2(a); ujl = hi2(a); uih = lo2(b); ujh = hi2(b);
+        }
+        if (bprev) {
+          // finish step 7 of the previous iteration for this pair
+          const float4 xa = P.xlo[fid], xb = P.xhi[fid];
+          float4 a, b;
+          if (DENSE) { a = pack(uil, ujl); b = pack(uih, ujh); }
+          else { a = P.ulo[fid]; b = P.uhi[fid]; }
+          uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zil, P.alpha, res);
+          ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), zjl, P.alpha, res);
+          uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
+          ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), zjh, P.alpha, res);
+        } else if (DENSE && P.admm && valid) {
+          // standard ADMM: the pair was feasible, so x^k = z^{k-1} - u^{k-1}
+          const float2 pil = P.z_next[(size_t)(I * TILE + r) * E1 + s];
+          const float2 pih = P.z_next[(size_t)(I * TILE + r) * E1 + s + 1];
+          const float2 pjl = P.z_next[(size_t)j * E1 + s], pjh = P.z_next[(size_t)j * E1 + s + 1];
+          uil = finish_u_feasible(pin_lo, uil, pil, zil, P.alpha, res);
+          ujl = finish_u_feasible(pin_lo, ujl, pjl, zjl, P.alpha, res);
+          uih = finish_u_feasible(pin_hi, uih, pih, zih, P.alpha, res);
+          ujh = finish_u_feasible(pin_hi, ujh, pjh, zjh, P.alpha, res);
+        } else if (DENSE && !P.keep) {
+          uil = ujl = uih = ujh = mk(0.f, 0.f);  // reset rule: inactive edges carry u = 0
+        }
+        if (pin_lo) { uil = mk(0.f, 0.f); ujl = uil; }
+        if (pin_hi) { uih = mk(0.f, 0.f); ujh = uih; }
+        act = valid && collides((zjl - ujl) - (zil - uil), (zjh - ujh) - (zih - uih), ri + rj);
+        if (DENSE && valid) {
+          P.ulo[fid] = pack(uil, ujl);
+          P.uhi[fid] = pack(uih, ujh);
+        }
+      }
+      const uint32_t nword = __ballot_sync(FULL, act);
+      if (nword != word && lane == 0) P.bits[row] = nword;
+      if (nword) {
+        if (!DENSE && act) {
+          P.ulo[fid] = pack(uil, ujl);
+          P.uhi[fid] = pack(uih, ujh);
+        }
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(P.work_count, (unsigned)__popc(nword));
+        base = __shfl_sync(FULL, base, 0);
+        if (act) P.work[base + __popc(nword & ((1u << lane) - 1u))] = (uint32_t)fid;
+      }
+    }
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
+// Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
+// s and one agent tile: warp f < 1 + n_walls takes factor kind f (0 =
+// kinetic, else wall f - 1), lane = agent.
+__device__ __forceinline__ void segment_block(const Dev& P, int blk) {
+  const int s = blk / P.nt;
+  const int I = blk - s * P.nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = I * TILE + lane;
+  const bool vi = i < P.p;
+  const int E1 = P.eta + 1;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  float2 zl = mk(0.f, 0.f), zh = zl;
+  float r = 0.f;
+  if (vi) { zl = P.z[(size_t)i * E1 + s]; zh = P.z[(size_t)i * E1 + s + 1]; r = P.radius[i]; }
+  float res = 0.f;
+  for (int f = warp; f < 1 + P.nw; f += blockDim.x >> 5) {
+    if (f == 0) {
+      if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
+    } else {
+      wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
+    }
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
+// Pass 2: the collision minimizer (Eq. coll_minimizer_problem through
+// App. C/D/I) of every active pair in the worklist, one thread per pair.
+__device__ __forceinline__ void prox_item(const Dev& P, uint32_t fid) {
+  const int E1 = P.eta + 1;
+  const uint32_t row = fid >> 5, c = fid & 31;
+  const uint32_t blk = row >> 5, r = row & 31;
+  const int s = (int)(blk / P.ntp);
+  const int2 IJ = P.tiles[blk - (uint32_t)s * P.ntp];
+  const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
+  const float4 a = P.ulo[fid], b = P.uhi[fid];
+  const float2 nil = P.z[(size_t)i * E1 + s] - lo2(a), nih = P.z[(size_t)i * E1 + s + 1] - lo2(b);
+  const float2 njl = P.z[(size_t)j * E1 + s] - hi2(a), njh = P.z[(size_t)j * E1 + s + 1] - hi2(b);
+  float2 xil, xih, xjl, xjh;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, P.radius[i] + P.radius[j], P.rho,
+                 xil, xih, xjl, xjh);
+  P.xlo[fid] = pack(xil, xjl);
+  P.xhi[fid] = pack(xih, xjh);
+  if (!pin_lo) {
+    contribute(P, i, s, xil + lo2(a));
+    contribute(P, j, s, xjl + hi2(a));
+  }
+  if (!pin_hi) {
+    contribute(P, i, s + 1, xih + lo2(b));
+    contribute(P, j, s + 1, xjh + hi2(b));
+  }
+}
+
+// Pass 3 (steps 5-6): z = sum(rho m) / sum(rho) per free break-point from the
+// fixed-point sums (every weight is rho0, so z is the mean of the incoming m;
+// no incoming weight means z is unchanged).  Clears the sums for the next
+// iteration.
+__device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, bool& bad) {
+  const int sp = 1 + t / P.p;
+  const int i = t - (sp - 1) * P.p;
+  const size_t node = (size_t)i * (P.eta + 1) + sp;
+  const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
+  const unsigned cnt = P.accc[node];
+  P.accx[node] = 0ull;
+  P.accy[node] = 0ull;
+  P.accc[node] = 0u;
+  const float2 zo = P.z[node];
+  float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
+  if (P.admm) {
+    // every edge is weighted; each feasible collision or wall factor sent
+    // m = n + u = z^k, added here in the same exact fixed point
+    const unsigned deg = 2u * (unsigned)(P.p - 1) + 2u + 2u * (unsigned)P.nw;
+    const long long rest = (long long)(deg - cnt);
+    const long long qx = __float2ll_rn(zo.x * P.fix[0]), qy = __float2ll_rn(zo.y * P.fix[0]);
+    const double den = (double)P.fix[0] * (double)deg;
+    zn = mk((float)((double)(sx + rest * qx) / den), (float)((double)(sy + rest * qy) / den));
+  } else if (cnt > 0u) {
+    const double den = (double)P.fix[0] * (double)cnt;
+    zn = mk((float)((double)sx / den), (float)((double)sy / den));
+  }
+  P.z_next[node] = zn;
+  bad = (*P.status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
+  dz = bad ? 0.f : maxabs2(zn - zo);
+}
+
+// Warp-level end of the consensus pass: a NaN or overflow anywhere makes the
+// residual NaN (reported as PLAN_ENUMERIC).  All 32 lanes must call it.
+__device__ __forceinline__ void consensus_reduce(const Dev& P, float dz, bool bad) {
+  dz = warp_max(dz);
+  const bool anybad = __any_sync(FULL, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (anybad) atomicMax(P.res_cur, 0x7fc00000u);
+    else if (dz > 0.f) atomic_max_nonneg(P.res_cur, dz);
+  }
+}
+
+}  // namespace
