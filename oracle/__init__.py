@@ -15,9 +15,13 @@ Contents:
 * ``oracle.twa`` -- the seven-step TWA iteration of Appendix B over the factor
   graph of Section 3.3, plus the stopping rule, total cost and feasibility
   measures used by the tests.
+* ``oracle.adjoint`` -- the reference gradient of a loss on z^K after K
+  unrolled iterations with respect to starts, goals, radii and cost weights,
+  branch choices frozen; per-factor Jacobians by central differences of
+  ``oracle.prox``, pinned by central differences of the whole K-iteration map.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (closed forms, brute force on tiny inputs, invariants); see ``tests/``.
 """
 
-from . import prox, twa  # noqa: F401
+from . import adjoint, prox, twa  # noqa: F401
