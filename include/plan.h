@@ -213,8 +213,37 @@ plan_status plan_batch_set_shape(plan_batch_t batch, int rows_per_warp, int prox
                                  int iterations_per_graph);
 void plan_batch_destroy(plan_batch_t batch);
 
-/* Gradient of a trajectory loss through unrolled iterations (not built yet:
- * returns PLAN_EUNSUPPORTED). */
+/* Replace the radii (host, p) and/or the kinetic cost weights (host, laid
+ * out as cost_w of plan_create) and keep the current iterate; either pointer
+ * may be NULL.  New radii are checked against the endpoints like in
+ * plan_create.  Returns once the host buffers may be reused. */
+plan_status plan_set_params(plan_t plan, const float* radius, const float* cost_w);
+/*
+ * Differentiation through K unrolled iterations (the paper differentiates
+ * nothing; this serves callers that fit starts, goals, radii or cost weights
+ * to a loss on the planned trajectory).
+ *
+ * plan_unroll resets the plan to the initial state of Section 4 for its
+ * current inputs and runs K iterations of Appendix B, keeping a copy of the
+ * device state every checkpoint_every iterations (0 = ceil(sqrt(K))) and at
+ * iteration K; afterwards the trajectory is z^K (plan_get_trajectory).  The
+ * copies live in device memory that the library allocates on first use and
+ * frees in plan_destroy: about ceil(K / C) + 1 copies of the iteration state
+ * plus C recorded iterations, C = checkpoint_every.
+ *
+ * plan_backward returns the gradient of a loss L(z^K) given dL_dz = dL/dz^K
+ * (DEVICE, p x (eta+1) x 2), with every branch choice of the forward run held
+ * fixed: which collision factors were active in each iteration and which
+ * candidate direction each minimizer took (Appendix C).  It replays the
+ * iterations segment by segment from the checkpoints and runs the adjoint of
+ * each iteration in reverse.  Outputs are DEVICE arrays: d_start, d_goal
+ * (p x 2), d_radius (p), d_cost_w (laid out as cost_w).  K must be the K of
+ * the last plan_unroll, with no state change in between (else PLAN_EINVAL);
+ * the plan is left at iteration K, and plan_backward may be called again
+ * with another dL_dz.  Wall factors, PLAN_ADMM, PLAN_U_KEEP and a rho
+ * warm-up give PLAN_EUNSUPPORTED.  Enqueued on the plan's stream.
+ */
+plan_status plan_unroll(plan_t plan, int K, int checkpoint_every);
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,
                           float* d_radius, float* d_cost_w);
 

@@ -20,8 +20,9 @@ import numpy as np
 
 from .build import LIB, build  # noqa: F401
 
-__all__ = ["Planner", "PlanError", "load_library", "PLAN_U_KEEP", "PLAN_COST_UNNORM",
-           "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE", "PLAN_ADMM", "EXPORTED_SYMBOLS"]
+__all__ = ["Planner", "PlannerBatch", "PlanError", "load_library", "unrolled_trajectory",
+           "PLAN_U_KEEP", "PLAN_COST_UNNORM", "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE",
+           "PLAN_ADMM", "EXPORTED_SYMBOLS"]
 
 PLAN_U_KEEP = 1 << 0
 PLAN_COST_UNNORM = 1 << 1
@@ -38,7 +39,8 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_last_error", "plan_iterate_static", "plan_profile",
                     "plan_batch_workspace_size", "plan_batch_create", "plan_batch_iterate",
                     "plan_batch_solve", "plan_batch_get_trajectory", "plan_batch_autotune",
-                    "plan_batch_set_shape", "plan_batch_destroy"]
+                    "plan_batch_set_shape", "plan_batch_destroy", "plan_set_params",
+                    "plan_unroll"]
 
 
 class PlanError(RuntimeError):
@@ -87,7 +89,9 @@ def load_library(path: str | None = None):
                                       c_void_p, POINTER(c_int)]
     lib.plan_import_state.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]
     lib.plan_get_info.argtypes = [c_void_p, POINTER(plan_info)]
-    lib.plan_backward.argtypes = [c_void_p, c_int, fp, fp, fp, fp, fp]
+    lib.plan_backward.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.plan_set_params.argtypes = [c_void_p, fp, fp]
+    lib.plan_unroll.argtypes = [c_void_p, c_int, c_int]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
     pp = POINTER(c_void_p)
@@ -228,6 +232,41 @@ class Planner:
         st, st_p = _f32(start, (self.p, 2))
         gl, gl_p = _f32(goal, (self.p, 2))
         _check(_lib.plan_set_endpoints(self._h, st_p, gl_p))
+
+    def set_params(self, radius=None, cost_w=None):
+        """Replace the radii and/or cost weights (same layout as at creation)."""
+        rd = _f32(radius, (self.p,)) if radius is not None else (None, None)
+        cw = None, None
+        if cost_w is not None:
+            shape = (self.p, self.eta) if self.flags & PLAN_COST_PER_SEGMENT else (self.p,)
+            cw = _f32(cost_w, shape)
+        _check(_lib.plan_set_params(self._h, rd[1], cw[1]))
+
+    # -- differentiation ---------------------------------------------------
+    def unroll(self, K: int, checkpoint_every: int = 0):
+        """Reset to the initial state and run K iterations, keeping
+        checkpoints for ``backward`` (0 = every ceil(sqrt(K)) iterations)."""
+        _check(_lib.plan_unroll(self._h, int(K), int(checkpoint_every)))
+        self._unrolled = int(K)
+
+    def backward(self, dL_dz):
+        """Gradient of L(z^K) after ``unroll(K)``: dL_dz is a (p, eta+1, 2)
+        tensor.  Returns (d_start, d_goal, d_radius, d_cost_w) float32 device
+        tensors, d_cost_w laid out like the cost weights."""
+        import torch
+        dev = self.device
+        g = torch.as_tensor(dL_dz, dtype=torch.float32).to(dev).contiguous()
+        if tuple(g.shape) != (self.p, self.eta + 1, 2):
+            raise ValueError(f"dL_dz must have shape {(self.p, self.eta + 1, 2)}")
+        d_start = torch.empty((self.p, 2), dtype=torch.float32, device=dev)
+        d_goal = torch.empty((self.p, 2), dtype=torch.float32, device=dev)
+        d_radius = torch.empty((self.p,), dtype=torch.float32, device=dev)
+        shape = (self.p, self.eta) if self.flags & PLAN_COST_PER_SEGMENT else (self.p,)
+        d_cost = torch.empty(shape, dtype=torch.float32, device=dev)
+        ptr = lambda t: c_void_p(t.data_ptr())
+        _check(_lib.plan_backward(self._h, getattr(self, "_unrolled", -1), ptr(g), ptr(d_start),
+                                  ptr(d_goal), ptr(d_radius), ptr(d_cost)))
+        return d_start, d_goal, d_radius, d_cost
 
     # -- state ------------------------------------------------------------
     def trajectory(self):
@@ -378,3 +417,46 @@ class PlannerBatch:
         z = torch.empty((inst.p, inst.eta + 1, 2), dtype=torch.float32, device=self.device)
         _check(_lib.plan_batch_get_trajectory(self._h, int(member), c_void_p(z.data_ptr()), 1))
         return z
+
+
+def _unrolled_function():
+    import torch
+
+    class UnrolledTrajectory(torch.autograd.Function):
+        """z^K of K unrolled TWA iterations as a differentiable function of
+        (start, goal, radius, cost_w); backward runs the planner's adjoint
+        kernels (plan_backward) with the forward run's branches frozen."""
+
+        @staticmethod
+        def forward(ctx, start, goal, radius, cost_w, planner, K, checkpoint_every):
+            host = lambda t: t.detach().to("cpu", torch.float32).numpy()
+            planner.set_endpoints(host(start), host(goal))
+            planner.set_params(host(radius), host(cost_w))
+            planner.unroll(K, checkpoint_every)
+            ctx.planner = planner
+            ctx.shapes = (start.shape, goal.shape, radius.shape, cost_w.shape)
+            ctx.devices = (start.device, goal.device, radius.device, cost_w.device)
+            return planner.trajectory().to(start.device)
+
+        @staticmethod
+        def backward(ctx, gz):
+            grads = ctx.planner.backward(gz.detach().to(ctx.planner.device, torch.float32))
+            out = tuple(g.reshape(sh).to(dv) for g, sh, dv in zip(grads, ctx.shapes, ctx.devices))
+            return out + (None, None, None)
+
+    return UnrolledTrajectory
+
+
+_UNROLLED = None
+
+
+def unrolled_trajectory(planner: "Planner", start, goal, radius, cost_w, K: int,
+                        checkpoint_every: int = 0):
+    """Differentiable z^K (p, eta+1, 2) after K iterations from the initial
+    state, for torch tensors start, goal (p, 2), radius (p,) and cost_w
+    (laid out as the planner's cost weights).  The planner's inputs are
+    replaced by these values."""
+    global _UNROLLED
+    if _UNROLLED is None:
+        _UNROLLED = _unrolled_function()
+    return _UNROLLED.apply(start, goal, radius, cost_w, planner, int(K), int(checkpoint_every))

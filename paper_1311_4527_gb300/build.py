@@ -17,8 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libplan.so")
 SOURCES = [os.path.join(CSRC, "plan.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "twa_math.cuh"), os.path.join(CSRC, "twa_iter.cuh"),
-                  os.path.join(INCLUDE, "plan.h")]
+DEPS = SOURCES + [os.path.join(CSRC, n) for n in ("twa_math.cuh", "twa_iter.cuh", "twa_adjoint.cuh",
+                                                  "twa_backward.cuh")] + [os.path.join(INCLUDE, "plan.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

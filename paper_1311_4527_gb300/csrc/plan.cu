@@ -26,6 +26,7 @@
 
 #include "plan.h"
 #include "twa_iter.cuh"
+#include "twa_backward.cuh"
 
 namespace {
 
@@ -525,6 +526,13 @@ struct plan_s {
   unsigned* h_res;  // pinned host word for residual readback
   std::vector<float> h_radius;
   std::vector<float> h_walls;
+  std::vector<float> h_start, h_goal;
+  // differentiation (plan_unroll / plan_backward)
+  char* adj = nullptr;           // checkpoints, tape and adjoint state
+  size_t adj_bytes = 0;
+  int adj_K = -1, adj_C = 0;     // the last unroll
+  bool adj_valid = false;        // state unchanged since that unroll
+  std::vector<int> ck_cur;       // z buffer holding z at each checkpoint
 
   template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
 
@@ -724,6 +732,7 @@ plan_status plan_workspace_size(const plan_config* cfg, size_t* bytes) {
 
 plan_status plan_reset(plan_t h) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
+  h->adj_valid = false;
   h->k = 0;
   h->cur = 0;
   Dev P = h->dev(0);
@@ -793,6 +802,8 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
   h->stream = (cudaStream_t)cuda_stream;
   h->L = L;
   h->h_radius.assign(radius, radius + p);
+  h->h_start.assign(start, start + 2 * p);
+  h->h_goal.assign(goal, goal + 2 * p);
   if (h->nw) h->h_walls.assign(walls, walls + 4 * (size_t)h->nw);
   if (workspace) {
     if (workspace_bytes < L.total) {
@@ -866,6 +877,7 @@ void plan_destroy(plan_t h) {
   if (h->pend) cudaEventDestroy(h->pend);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->adj) cudaFree(h->adj);
   delete h;
 }
 
@@ -875,6 +887,9 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
     return fail(PLAN_EINVAL, "non-finite input");
   plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data());
   if (st != PLAN_OK) return st;
+  h->adj_valid = false;
+  h->h_start.assign(start, start + 2 * (size_t)h->p);
+  h->h_goal.assign(goal, goal + 2 * (size_t)h->p);
   CK(cudaMemcpyAsync(h->at<void>(h->L.start), start, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->at<void>(h->L.goal), goal, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
   endpoints_kernel<<<(h->p + 255) / 256, 256, 0, h->stream>>>(
@@ -890,6 +905,7 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
 plan_status plan_iterate(plan_t h, int k_iters, float* max_residual) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
   if (k_iters < 0) return fail(PLAN_EINVAL, "k_iters must be >= 0");
+  if (k_iters > 0) h->adj_valid = false;
   for (int it = 0; it < k_iters; ++it) {
     plan_status st = run_iteration(h);
     if (st != PLAN_OK) return st;
@@ -950,6 +966,7 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   if (!h || !z || !u_kin || (h->p > 1 && !u_coll) || (h->nw && !u_wall))
     return fail(PLAN_EINVAL, "null argument");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
+  h->adj_valid = false;
   const size_t zbytes = (size_t)h->p * (h->eta + 1) * 8;
   CK(cudaMemcpyAsync(h->at<void>(h->L.z0), z, zbytes, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemcpyAsync(h->at<void>(h->L.z1), z, zbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1014,11 +1031,324 @@ plan_status plan_profile(plan_t h, int enable, float* ms, int* iterations) {
   return PLAN_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Differentiation: K unrolled iterations, checkpoints, and the adjoint pass
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void record_kernel(Dev P, const float2* zk, float2* tz, float4* tukin, uint32_t* tfid,
+                              float4* tucl, float4* tuch, unsigned* tcount) {
+  const unsigned cnt = *P.work_count;
+  const unsigned nz = (unsigned)P.p * (P.eta + 1), nk = (unsigned)P.eta * P.p;
+  const unsigned n = max(max(nz, nk), cnt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *tcount = cnt;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    if (t < nz) tz[t] = zk[t];
+    if (t < nk) tukin[t] = P.ukin[t];
+    if (t < cnt) {
+      const uint32_t f = P.work[t];
+      tfid[t] = f;
+      tucl[t] = P.ulo[f];
+      tuch[t] = P.uhi[f];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) bw_scatter_kernel(AdjDev A) {
+  const unsigned n = (unsigned)(A.eta * A.p) + *A.count;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    bw_scatter_item(A, t);
+}
+
+__global__ void bw_node_kernel(AdjDev A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < A.p * (A.eta + 1)) bw_node(A, t);
+}
+
+__global__ void __launch_bounds__(256) bw_factor_kernel(AdjDev A) {
+  const unsigned n = (unsigned)(A.eta * A.p) + *A.count;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    bw_factor_item(A, t);
+}
+
+__global__ void bw_init_kernel(int n, const float2* dz, double2* zb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) zb[t] = make_double2((double)dz[t].x, (double)dz[t].y);
+}
+
+// z^0 is the start at every break-point but the goal node (Section 4); then
+// the FP32 outputs.  d_cost: dL/dC_{i,s} = norm dL/dc_{i,s}, summed over s
+// when one C_i serves every segment.
+__global__ void bw_final_kernel(AdjDev A, const double2* zb0, double norm, int per_segment,
+                                float2* d_start, float2* d_goal, float* d_radius, float* d_cost) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.p) return;
+  const int E1 = A.eta + 1;
+  double2 gs = A.g_start[i];
+  for (int s = 0; s < A.eta; ++s) { gs.x += zb0[(size_t)i * E1 + s].x; gs.y += zb0[(size_t)i * E1 + s].y; }
+  const double2 zg = zb0[(size_t)i * E1 + A.eta];
+  const double2 gg = make_double2(A.g_goal[i].x + zg.x, A.g_goal[i].y + zg.y);
+  d_start[i] = mk((float)gs.x, (float)gs.y);
+  d_goal[i] = mk((float)gg.x, (float)gg.y);
+  d_radius[i] = (float)A.g_r[i];
+  if (per_segment) {
+    for (int s = 0; s < A.eta; ++s) d_cost[(size_t)i * A.eta + s] = (float)(norm * A.g_c[(size_t)i * A.eta + s]);
+  } else {
+    double c = 0.0;
+    for (int s = 0; s < A.eta; ++s) c += A.g_c[(size_t)i * A.eta + s];
+    d_cost[i] = (float)(norm * c);
+  }
+}
+
+// Device state copied into a checkpoint: everything an iteration reads.
+struct Region { size_t off, bytes; };
+
+std::vector<Region> ck_regions(plan_t h) {
+  const size_t zb = (size_t)h->p * (h->eta + 1) * 8, kin = (size_t)h->eta * h->p * 16;
+  return {{h->L.z0, zb}, {h->L.z1, zb}, {h->L.bits, (size_t)h->eta * h->ntp * TILE * 4},
+          {h->L.ulo, h->slots * 16}, {h->L.uhi, h->slots * 16}, {h->L.xlo, h->slots * 16},
+          {h->L.xhi, h->slots * 16}, {h->L.ukin, kin}, {h->L.xkin, kin}, {h->L.wcount, 8},
+          {h->L.res, 16}, {h->L.status, 4}};
+}
+
+// Offsets inside the plan's differentiation block.
+struct AdjLayout {
+  size_t ck_bytes, ck0;
+  int nck;
+  size_t cap, slot_bytes, tape0;
+  size_t t_z, t_ukin, t_count, t_fid, t_ucl, t_uch;  // within one tape slot
+  size_t ubk, ubl, ubh, stamp, zbA, zbB, S, cnt, mbar, gs, gg, gr, gc;
+  size_t total;
+};
+
+AdjLayout adj_layout(plan_t h, int K, int C) {
+  AdjLayout A{};
+  const size_t p = h->p, E1 = h->eta + 1, eta = h->eta;
+  A.ck_bytes = 0;
+  for (const Region& r : ck_regions(h)) A.ck_bytes += a256(r.bytes);
+  A.nck = (K + C - 1) / C + 1;  // segment starts and the final state
+  A.cap = std::max<size_t>(1, eta * (p * (p - 1) / 2));
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = a256(o + std::max<size_t>(bytes, 1)); return at; };
+  A.t_z = take(p * E1 * 8);
+  A.t_ukin = take(eta * p * 16);
+  A.t_count = take(4);
+  A.t_fid = take(A.cap * 4);
+  A.t_ucl = take(A.cap * 16);
+  A.t_uch = take(A.cap * 16);
+  A.slot_bytes = o;
+  o = 0;
+  A.ck0 = take(A.ck_bytes * A.nck);
+  A.tape0 = take(A.slot_bytes * C);
+  A.ubk = take(eta * p * 16);
+  A.ubl = take(h->slots * 16);
+  A.ubh = take(h->slots * 16);
+  A.stamp = take(h->slots * 4);
+  A.zbA = take(p * E1 * 16);
+  A.zbB = take(p * E1 * 16);
+  A.S = take(p * E1 * 16);
+  A.cnt = take(p * E1 * 4);
+  A.mbar = take(p * E1 * 8);
+  A.gs = take(p * 16);
+  A.gg = take(p * 16);
+  A.gr = take(p * 8);
+  A.gc = take(p * eta * 8);
+  A.total = o;
+  return A;
+}
+
+plan_status snapshot(plan_t h, const AdjLayout& A, int idx, bool save) {
+  char* ck = h->adj + A.ck0 + (size_t)idx * A.ck_bytes;
+  for (const Region& r : ck_regions(h)) {
+    char* ws = h->ws + r.off;
+    CK(cudaMemcpyAsync(save ? ck : ws, save ? ws : ck, r.bytes, cudaMemcpyDeviceToDevice, h->stream));
+    ck += a256(r.bytes);
+  }
+  return PLAN_OK;
+}
+
+AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char* zb_out) {
+  AdjDev D{};
+  D.p = h->p; D.eta = h->eta; D.ntp = h->ntp; D.k = k;
+  D.rho = h->cfg.rho0; D.alpha = h->cfg.alpha;
+  D.tiles = h->at<int2>(h->L.tiles);
+  D.radius = h->at<float>(h->L.radius);
+  D.cost = h->at<float>(h->L.cost);
+  char* t = h->adj + A.tape0 + (size_t)slot * A.slot_bytes;
+  D.z = reinterpret_cast<const float2*>(t + A.t_z);
+  D.ukin = reinterpret_cast<const float4*>(t + A.t_ukin);
+  D.count = reinterpret_cast<const unsigned*>(t + A.t_count);
+  D.fid = reinterpret_cast<const uint32_t*>(t + A.t_fid);
+  D.ucl = reinterpret_cast<const float4*>(t + A.t_ucl);
+  D.uch = reinterpret_cast<const float4*>(t + A.t_uch);
+  D.ubk = reinterpret_cast<float4*>(h->adj + A.ubk);
+  D.ubl = reinterpret_cast<float4*>(h->adj + A.ubl);
+  D.ubh = reinterpret_cast<float4*>(h->adj + A.ubh);
+  D.stamp = reinterpret_cast<int*>(h->adj + A.stamp);
+  D.zb_in = reinterpret_cast<const double2*>(zb_in);
+  D.zb_out = reinterpret_cast<double2*>(zb_out);
+  D.S = reinterpret_cast<double2*>(h->adj + A.S);
+  D.cnt = reinterpret_cast<unsigned*>(h->adj + A.cnt);
+  D.mbar = reinterpret_cast<float2*>(h->adj + A.mbar);
+  D.g_start = reinterpret_cast<double2*>(h->adj + A.gs);
+  D.g_goal = reinterpret_cast<double2*>(h->adj + A.gg);
+  D.g_r = reinterpret_cast<double*>(h->adj + A.gr);
+  D.g_c = reinterpret_cast<double*>(h->adj + A.gc);
+  return D;
+}
+
+plan_status adj_supported(plan_t h) {
+  if (h->nw) return fail(PLAN_EUNSUPPORTED, "the adjoint does not cover wall factors yet");
+  if (h->cfg.flags & (PLAN_ADMM | PLAN_U_KEEP))
+    return fail(PLAN_EUNSUPPORTED, "the adjoint covers TWA with the reset rule only");
+  if (h->cfg.warm_iters > 0) return fail(PLAN_EUNSUPPORTED, "the adjoint needs a constant rho0");
+  return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  const size_t p = h->p, eta = h->eta;
+  const size_t ncost = (h->cfg.flags & PLAN_COST_PER_SEGMENT) ? p * eta : p;
+  if (radius) {
+    if (!finite_all(radius, p)) return fail(PLAN_EINVAL, "non-finite radius");
+    for (size_t i = 0; i < p; ++i)
+      if (!(radius[i] > 0.f)) return fail(PLAN_EINVAL, "radius[%zu] must be positive", i);
+    plan_status st = check_endpoints(h->p, h->h_start.data(), h->h_goal.data(), radius, h->nw,
+                                     h->h_walls.data());
+    if (st != PLAN_OK) return st;
+  }
+  std::vector<float> cost;
+  if (cost_w) {
+    if (!finite_all(cost_w, ncost)) return fail(PLAN_EINVAL, "non-finite cost_w");
+    for (size_t i = 0; i < ncost; ++i)
+      if (cost_w[i] < 0.f) return fail(PLAN_EINVAL, "cost_w[%zu] must be >= 0", i);
+    const double norm = (h->cfg.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * eta);
+    cost.resize(p * eta);
+    for (size_t i = 0; i < p; ++i)
+      for (size_t s = 0; s < eta; ++s)
+        cost[i * eta + s] = (float)(norm * ((h->cfg.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i]));
+  }
+  h->adj_valid = false;
+  if (radius) {
+    h->h_radius.assign(radius, radius + p);
+    CK(cudaMemcpyAsync(h->at<void>(h->L.radius), radius, p * 4, cudaMemcpyHostToDevice, h->stream));
+  }
+  if (cost_w)
+    CK(cudaMemcpyAsync(h->at<void>(h->L.cost), cost.data(), p * eta * 4, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_unroll(plan_t h, int K, int checkpoint_every) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  if (K < 0 || checkpoint_every < 0) return fail(PLAN_EINVAL, "K and checkpoint_every must be >= 0");
+  plan_status st = adj_supported(h);
+  if (st != PLAN_OK) return st;
+  int C = checkpoint_every ? checkpoint_every : (int)std::ceil(std::sqrt((double)std::max(K, 1)));
+  C = std::max(1, std::min(C, std::max(K, 1)));
+  const AdjLayout A = adj_layout(h, K, C);
+  if (h->adj_bytes < A.total) {
+    if (h->adj) {
+      CK(cudaStreamSynchronize(h->stream));
+      cudaFree(h->adj);
+      h->adj = nullptr;
+      h->adj_bytes = 0;
+    }
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, A.total);
+    if (e != cudaSuccess)
+      return fail(PLAN_ENOMEM, "cudaMalloc(%zu) for the adjoint failed: %s", A.total, cudaGetErrorString(e));
+    h->adj = static_cast<char*>(mem);
+    h->adj_bytes = A.total;
+  }
+  st = plan_reset(h);
+  if (st != PLAN_OK) return st;
+  h->ck_cur.assign(A.nck, 0);
+  for (int k = 0; k < K; ++k) {
+    if (k % C == 0) {
+      h->ck_cur[k / C] = h->cur;
+      if ((st = snapshot(h, A, k / C, true)) != PLAN_OK) return st;
+    }
+    if ((st = run_iteration(h)) != PLAN_OK) return st;
+  }
+  h->ck_cur[A.nck - 1] = h->cur;
+  if ((st = snapshot(h, A, A.nck - 1, true)) != PLAN_OK) return st;
+  h->adj_K = K;
+  h->adj_C = C;
+  h->adj_valid = true;
+  return PLAN_OK;
+}
+
 plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, float* d_goal,
                           float* d_radius, float* d_cost_w) {
-  (void)h; (void)K; (void)dL_dz; (void)d_start; (void)d_goal; (void)d_radius; (void)d_cost_w;
-  return fail(PLAN_EUNSUPPORTED, "plan_backward is not built yet");
+  if (!h || !dL_dz || !d_start || !d_goal || !d_radius || !d_cost_w)
+    return fail(PLAN_EINVAL, "null argument");
+  plan_status st = adj_supported(h);
+  if (st != PLAN_OK) return st;
+  if (!h->adj_valid || K != h->adj_K)
+    return fail(PLAN_EINVAL, "plan_backward(K = %d) needs the state left by plan_unroll(K)", K);
+  if ((st = ensure_prox_grid(h)) != PLAN_OK) return st;
+  const int C = h->adj_C;
+  const AdjLayout A = adj_layout(h, K, C);
+  const size_t p = h->p, E1 = h->eta + 1, nodes = p * E1;
+  // adjoint state: u adjoints 0, no stamps, gradients 0, zbar = dL/dz^K
+  CK(cudaMemsetAsync(h->adj + A.ubk, 0, (size_t)h->eta * p * 16, h->stream));
+  CK(cudaMemsetAsync(h->adj + A.stamp, 0xff, h->slots * 4, h->stream));
+  CK(cudaMemsetAsync(h->adj + A.S, 0, nodes * 16, h->stream));
+  CK(cudaMemsetAsync(h->adj + A.cnt, 0, nodes * 4, h->stream));
+  CK(cudaMemsetAsync(h->adj + A.gs, 0, A.gc + p * h->eta * 8 - A.gs, h->stream));
+  bw_init_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, h->stream>>>(
+      (int)nodes, reinterpret_cast<const float2*>(dL_dz), reinterpret_cast<double2*>(h->adj + A.zbA));
+  CK(cudaGetLastError());
+  char* zb_in = h->adj + A.zbA;
+  char* zb_out = h->adj + A.zbB;
+  const int nseg = A.nck - 1;
+  const unsigned node_grid = (unsigned)((nodes + 255) / 256);
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int c0 = seg * C, c1 = std::min(K, c0 + C);
+    // recompute the segment from its checkpoint, recording each iteration
+    if ((st = snapshot(h, A, seg, false)) != PLAN_OK) return st;
+    h->k = c0;
+    h->cur = h->ck_cur[seg];
+    for (int k = c0; k < c1; ++k) {
+      const float2* zk = h->cur ? h->at<float2>(h->L.z1) : h->at<float2>(h->L.z0);
+      if ((st = run_iteration(h)) != PLAN_OK) return st;
+      char* t = h->adj + A.tape0 + (size_t)(k - c0) * A.slot_bytes;
+      record_kernel<<<h->prox_grid, 256, 0, h->stream>>>(
+          h->dev(k), zk, reinterpret_cast<float2*>(t + A.t_z), reinterpret_cast<float4*>(t + A.t_ukin),
+          reinterpret_cast<uint32_t*>(t + A.t_fid), reinterpret_cast<float4*>(t + A.t_ucl),
+          reinterpret_cast<float4*>(t + A.t_uch), reinterpret_cast<unsigned*>(t + A.t_count));
+      CK(cudaGetLastError());
+    }
+    // the adjoint steps of the segment, last iteration first
+    for (int k = c1 - 1; k >= c0; --k) {
+      const AdjDev D = adj_dev(h, A, k - c0, k, zb_in, zb_out);
+      bw_scatter_kernel<<<h->prox_grid, 256, 0, h->stream>>>(D);
+      bw_node_kernel<<<node_grid, 256, 0, h->stream>>>(D);
+      bw_factor_kernel<<<h->prox_grid, 256, 0, h->stream>>>(D);
+      CK(cudaGetLastError());
+      std::swap(zb_in, zb_out);
+    }
+  }
+  const AdjDev D = adj_dev(h, A, 0, 0, zb_in, zb_out);
+  const double norm = (h->cfg.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * h->eta);
+  bw_final_kernel<<<(unsigned)((p + 127) / 128), 128, 0, h->stream>>>(
+      D, reinterpret_cast<const double2*>(zb_in), norm, (h->cfg.flags & PLAN_COST_PER_SEGMENT) ? 1 : 0,
+      reinterpret_cast<float2*>(d_start), reinterpret_cast<float2*>(d_goal), d_radius, d_cost_w);
+  CK(cudaGetLastError());
+  // leave the plan at iteration K, as plan_unroll did
+  if ((st = snapshot(h, A, nseg, false)) != PLAN_OK) return st;
+  h->k = K;
+  h->cur = h->ck_cur[nseg];
+  return PLAN_OK;
 }
+
 
 
 // ---------------------------------------------------------------------------

@@ -115,13 +115,15 @@ TWA_DEV float dist2_segment_segment(float2 a0, float2 a1, float2 b0, float2 b1) 
   return fminf(m, fminf(dist2_point_segment(b0, a0, a1), dist2_point_segment(b1, a0, a1)));
 }
 
-// Keep the best (lowest E, then smallest angle) candidate direction.
+// Keep the best (lowest E, then smallest angle) candidate direction.  tag
+// records which kind of candidate won (read by the adjoint; dead otherwise).
 struct Best {
   float2 n;
   float E;
-  TWA_DEV void init() { n = mk(1.f, 0.f); E = INFINITY; }
-  TWA_DEV void offer(float2 c, float e) {
-    if (e < E || (e == E && angle_of(c) < angle_of(n))) { n = c; E = e; }
+  int tag;
+  TWA_DEV void init() { n = mk(1.f, 0.f); E = INFINITY; tag = 0; }
+  TWA_DEV void offer(float2 c, float e, int t = 0) {
+    if (e < E || (e == E && angle_of(c) < angle_of(n))) { n = c; E = e; tag = t; }
   }
 };
 
@@ -307,35 +309,62 @@ TWA_DEV void tangent_normals(float2 q, float R, float2& t0, float2& t1) {
 }
 
 // Direction in the arc {n : <q,n> >= R} (|q| >= R) maximising <w, n>.
-TWA_DEV float2 arc_argmax(float2 q, float R, float2 w) {
+// tangent: the answer is an end of the arc (<q,n> = R) rather than w / |w|.
+TWA_DEV float2 arc_argmax(float2 q, float R, float2 w, bool& tangent) {
   float nw = hypotf(w.x, w.y);
+  tangent = false;
   if (nw > 0.f && dot(q, w) >= R * nw) return mk(w.x / nw, w.y / nw);
+  tangent = true;
   float2 t0, t1;
   tangent_normals(q, R, t0, t1);
   float d0 = dot(w, t0), d1 = dot(w, t1);
   if (d0 > d1 || (d0 == d1 && angle_of(t0) <= angle_of(t1))) return normalized(t0);
   return normalized(t1);
 }
+TWA_DEV float2 arc_argmax(float2 q, float R, float2 w) {
+  bool tangent;
+  return arc_argmax(q, R, w, tangent);
+}
+
+// Kinds of winning direction of the free disk minimizer (Best::tag).
+enum DiskTag {
+  DISK_DEFAULT = 0,  // the (1, 0) fallback
+  DISK_GLOBAL = 1,   // global minimiser n_f of the both-stretched piece f
+  DISK_A_INNER = 2,  // a / |a| on the arc where b's hinge is zero
+  DISK_A_TANGENT = 3,  // an end of that arc, <b, n> = R
+  DISK_B_INNER = 4,  // b / |b| on the arc where a's hinge is zero
+  DISK_B_TANGENT = 5   // an end of that arc, <a, n> = R
+};
+
+// Separating direction of the free disk minimizer and the kind of candidate
+// it came from.
+TWA_DEV float2 disk_dir_free(float2 a, float2 b, float wl, float wh, float R, int& tag) {
+  Best best;
+  best.init();
+  best.offer(mk(1.f, 0.f), hinge_E(a, b, wl, wh, R, mk(1.f, 0.f)), DISK_DEFAULT);
+  float2 c[2];
+  int nc = trs_global(a, b, wl, wh, R, c);
+  for (int k = 0; k < nc; ++k) best.offer(c[k], hinge_E(a, b, wl, wh, R, c[k]), DISK_GLOBAL);
+  if (dot(b, b) >= R * R) {  // b's hinge can be zero: best a-term on that arc
+    bool tg;
+    float2 n = arc_argmax(b, R, a, tg);
+    best.offer(n, hinge_E(a, b, wl, wh, R, n), tg ? DISK_A_TANGENT : DISK_A_INNER);
+  }
+  if (dot(a, a) >= R * R) {
+    bool tg;
+    float2 n = arc_argmax(a, R, b, tg);
+    best.offer(n, hinge_E(a, b, wl, wh, R, n), tg ? DISK_B_TANGENT : DISK_B_INNER);
+  }
+  tag = best.tag;
+  return best.n;
+}
 
 // Collision minimizer core: disk of radius R at the origin, finite equal or
 // unequal weights, neither end pinned.  (a, b): targets; (vl, vh): result.
 TWA_NOINLINE void disk_prox_free(float2 a, float2 b, float wl, float wh, float R,
                                             float2& vl, float2& vh) {
-  Best best;
-  best.init();
-  best.offer(mk(1.f, 0.f), hinge_E(a, b, wl, wh, R, mk(1.f, 0.f)));
-  float2 c[2];
-  int nc = trs_global(a, b, wl, wh, R, c);
-  for (int k = 0; k < nc; ++k) best.offer(c[k], hinge_E(a, b, wl, wh, R, c[k]));
-  if (dot(b, b) >= R * R) {  // b's hinge can be zero: best a-term on that arc
-    float2 n = arc_argmax(b, R, a);
-    best.offer(n, hinge_E(a, b, wl, wh, R, n));
-  }
-  if (dot(a, a) >= R * R) {
-    float2 n = arc_argmax(a, R, b);
-    best.offer(n, hinge_E(a, b, wl, wh, R, n));
-  }
-  float2 n = best.n;
+  int tag;
+  float2 n = disk_dir_free(a, b, wl, wh, R, tag);
   vl = a + fmaxf(R - dot(a, n), 0.f) * n;
   vh = b + fmaxf(R - dot(b, n), 0.f) * n;
 }

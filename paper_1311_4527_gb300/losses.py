@@ -1,0 +1,49 @@
+"""Trajectory losses for the differentiable planner (plain PyTorch ops on
+the break-points z, shape (p, eta+1, 2); autograd gives dL/dz, which
+``Planner.backward`` / ``unrolled_trajectory`` carry back to the inputs).
+
+The paper has no loss of its own: these are the quantities it reports on a
+plan, the kinetic energy of Section 1 and the collision clearance, written
+as functions of z.
+"""
+from __future__ import annotations
+
+
+def kinetic_energy(z, cost_w):
+    """sum over agents and segments of C_{i,s} |z_{i,s+1} - z_{i,s}|^2
+    (the objective of Section 1 with the planner's default normalisation
+    1 / (p eta)); cost_w is (p,) or (p, eta)."""
+    import torch
+    p, E1, _ = z.shape
+    eta = E1 - 1
+    d = z[:, 1:] - z[:, :-1]
+    c = cost_w if cost_w.dim() == 2 else cost_w[:, None].expand(p, eta)
+    return (c * (d * d).sum(-1)).sum() / (p * eta)
+
+
+def collision_slack(z, radius, chunk: int = 1 << 16):
+    """sum over pairs i < j and segments s of [R_ij - d_ij,s]_+^2, d the
+    closest distance of the two agents while both move linearly along
+    segment s (the relative position sweeps the segment from
+    z_j,s - z_i,s to z_j,s+1 - z_i,s+1), R_ij = r_i + r_j."""
+    import torch
+    p = z.shape[0]
+    iu, ju = torch.triu_indices(p, p, 1, device=z.device)
+    total = z.new_zeros(())
+    for a in range(0, iu.numel(), chunk):
+        i, j = iu[a:a + chunk], ju[a:a + chunk]
+        c0 = z[j, :-1] - z[i, :-1]
+        c1 = z[j, 1:] - z[i, 1:]
+        d = c1 - c0
+        dd = (d * d).sum(-1)
+        t = (-(c0 * d).sum(-1) / dd.clamp_min(1e-30)).clamp(0.0, 1.0)
+        q = c0 + t[..., None] * d
+        dist = torch.sqrt((q * q).sum(-1) + 1e-30)
+        R = (radius[i] + radius[j])[:, None]
+        total = total + (torch.relu(R - dist) ** 2).sum()
+    return total
+
+
+def plan_loss(z, radius, cost_w, weight: float = 10.0):
+    """Final kinetic energy + weight x the squared collision slack."""
+    return kinetic_energy(z, cost_w) + weight * collision_slack(z, radius)

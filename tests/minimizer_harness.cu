@@ -12,6 +12,7 @@ __host__ __device__ inline void count_iter(int kind) {
 }
 #define TWA_ITER_HOOK(kind) count_iter(kind)
 #include "twa_math.cuh"
+#include "twa_adjoint.cuh"
 
 using namespace twa;
 
@@ -55,6 +56,36 @@ void h_energy_prox(const float* nl, const float* nh, float rho, int pin_lo, int 
   float2 xl, xh;
   energy_prox(mk(nl[0], nl[1]), mk(nh[0], nh[1]), rho, pin_lo != 0, pin_hi != 0, c, xl, xh);
   out[0] = xl.x; out[1] = xl.y; out[2] = xh.x; out[3] = xh.y;
+}
+
+// Adjoints (twa_adjoint.cuh).  n: 8 floats (i lo, i hi, j lo, j hi); xbar
+// likewise; out: nbar (8 floats) then the adjoint of R.
+void h_coll_vjp(const float* n, int pin_lo, int pin_hi, float R, float rho, const float* xb,
+                float* out) {
+  float2 nb[4];
+  float Rb;
+  coll_vjp(mk(n[0], n[1]), mk(n[2], n[3]), mk(n[4], n[5]), mk(n[6], n[7]), pin_lo != 0,
+           pin_hi != 0, R, rho, mk(xb[0], xb[1]), mk(xb[2], xb[3]), mk(xb[4], xb[5]),
+           mk(xb[6], xb[7]), nb[0], nb[1], nb[2], nb[3], Rb);
+  for (int k = 0; k < 4; ++k) { out[2 * k] = nb[k].x; out[2 * k + 1] = nb[k].y; }
+  out[8] = Rb;
+}
+
+// out: nbar (4 floats) then the adjoint of c.
+void h_energy_vjp(const float* nl, const float* nh, float rho, int pin_lo, int pin_hi, float c,
+                  const float* xb, float* out) {
+  float2 bl, bh;
+  float cb;
+  energy_vjp(mk(nl[0], nl[1]), mk(nh[0], nh[1]), rho, pin_lo != 0, pin_hi != 0, c,
+             mk(xb[0], xb[1]), mk(xb[2], xb[3]), bl, bh, cb);
+  out[0] = bl.x; out[1] = bl.y; out[2] = bh.x; out[3] = bh.y; out[4] = cb;
+}
+
+// Winning candidate kind of the free disk minimizer (DiskTag).
+int h_disk_tag(const float* a, const float* b, float wl, float wh, float R) {
+  int tag;
+  disk_dir_free(mk(a[0], a[1]), mk(b[0], b[1]), wl, wh, R, tag);
+  return tag;
 }
 
 }  // extern "C"

@@ -106,8 +106,10 @@ def test_bad_parameters_are_rejected(lib):
     assert code == 1
 
 
-def test_backward_reports_unsupported(lib):
-    assert lib.plan_backward(None, 1, None, None, None, None, None) == 7
+def test_differentiation_entry_points_reject_null_plans(lib):
+    assert lib.plan_backward(None, 1, None, None, None, None, None) == 1
+    assert lib.plan_unroll(None, 10, 0) == 1
+    assert lib.plan_set_params(None, None, None) == 1
 
 
 def test_static_entry_point_rejects_a_problem_that_does_not_fit(lib):

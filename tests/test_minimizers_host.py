@@ -173,3 +173,92 @@ def test_secular_iterations_stay_few(H):
         worst = max(worst, k)
         calls += 1
     assert iters / calls < 5 and worst <= 12
+
+
+def _jt(f, v, xb, h):
+    """J(v)^T xb by central differences of f in FP64."""
+    out = np.zeros_like(v)
+    for q in range(v.shape[0]):
+        e = np.zeros_like(v)
+        e[q] = h
+        out[q] = float(xb @ ((f(v + e) - f(v - e)) / (2 * h)))
+    return out
+
+
+def _coll_fd(n, R, wl, wh):
+    nn = n.reshape(4, 2)
+    return np.concatenate(prox.coll_prox(nn[0], nn[1], nn[2], nn[3], wl, wh, wl, wh, R)[:4])
+
+
+def test_collision_adjoint_matches_oracle_differences(H):
+    """The FP32 adjoint of the pair collision minimizer (twa_adjoint.cuh)
+    against J^T xbar of the FP64 oracle minimizer by central differences, on
+    random active pairs, free and with either end fixed.  Pairs whose oracle
+    minimum is a near-tie, or whose differences at two step sizes disagree
+    (a branch boundary within the step), are skipped."""
+    rng = np.random.default_rng(31)
+    errs = {0: [], 1: [], 2: []}
+    tags = set()
+    for trial in range(3000):
+        pin = trial % 3  # 0 free, 1 lower end fixed, 2 upper end fixed
+        R = float(np.float32(rng.uniform(0.2, 0.8)))
+        n = _f32(rng.normal(size=8) * 0.6)
+        if not prox.segments_collide(n[0:2], n[2:4], n[4:6], n[6:8], R):
+            continue
+        if pin == 1 and np.linalg.norm(n[4:6] - n[0:2]) < R * 1.01:
+            continue
+        if pin == 2 and np.linalg.norm(n[6:8] - n[2:4]) < R * 1.01:
+            continue
+        wl = math.inf if pin == 1 else 1.0
+        wh = math.inf if pin == 2 else 1.0
+        if prox.coll_prox(n[0:2], n[2:4], n[4:6], n[6:8], wl, wh, wl, wh, R, want_gap=True)[5] < 1e-3:
+            continue
+        xb = rng.normal(size=8)
+        if pin == 1:
+            xb[0:2] = xb[4:6] = 0.0
+        if pin == 2:
+            xb[2:4] = xb[6:8] = 0.0
+        f = lambda v: _coll_fd(v, R, wl, wh)
+        r1, r2 = _jt(f, n, xb, 1e-6), _jt(f, n, xb, 1e-5)
+        if np.abs(r1 - r2).max() > 1e-5 * (1 + np.abs(r1).max()):
+            continue
+        dR = float(xb @ (_coll_fd(n, R + 1e-6, wl, wh) - _coll_fd(n, R - 1e-6, wl, wh))) / 2e-6
+        ref = np.concatenate([r1, [dR]])
+        N, pn = _a(n)
+        X, px = _a(xb)
+        out = np.zeros(9, np.float32)
+        H.h_coll_vjp(pn, int(pin == 1), int(pin == 2), ctypes.c_float(R), ctypes.c_float(1.0), px,
+                     out.ctypes.data_as(FP))
+        errs[pin].append(np.abs(out - ref).max() / (1 + np.abs(ref).max()))
+        if pin == 0:
+            c = n[4:6] - n[0:2], n[6:8] - n[2:4]
+            A, pa = _a(c[0])
+            B, pb = _a(c[1])
+            tags.add(H.h_disk_tag(pa, pb, ctypes.c_float(0.5), ctypes.c_float(0.5), ctypes.c_float(R)))
+    for pin, e in errs.items():
+        e = np.asarray(e)
+        assert e.size > 200, (pin, e.size)
+        assert np.median(e) < 1e-6 and e.max() < 5e-4, (pin, np.median(e), e.max())
+    assert {1, 2, 4} <= tags  # global, and both single-hinge directions
+
+
+def test_energy_adjoint_matches_oracle_differences(H):
+    rng = np.random.default_rng(32)
+    for _ in range(200):
+        nl, nh = _f32(rng.normal(size=(2, 2)) * 3)
+        rho, c = float(np.float32(rng.uniform(0.1, 3))), float(np.float32(rng.uniform(0, 2)))
+        xb = rng.normal(size=4)
+        for pl, ph in ((0, 0), (1, 0), (0, 1)):
+            wl, wh = (math.inf if pl else rho), (math.inf if ph else rho)
+            v = np.concatenate([nl, nh])
+            f = lambda u: np.concatenate(prox.energy_prox(u[:2], u[2:], wl, wh, c))
+            ref_n = _jt(f, v, xb, 1e-4)
+            fc = lambda cc: np.concatenate(prox.energy_prox(nl, nh, wl, wh, cc))
+            ref_c = float(xb @ (fc(c + 1e-6) - fc(c - 1e-6))) / 2e-6
+            N1, p1 = _a(nl)
+            N2, p2 = _a(nh)
+            X, px = _a(xb)
+            out = np.zeros(5, np.float32)
+            H.h_energy_vjp(p1, p2, ctypes.c_float(rho), pl, ph, ctypes.c_float(c), px, out.ctypes.data_as(FP))
+            ref = np.concatenate([ref_n, [ref_c]])
+            assert np.abs(out - ref).max() <= 1e-5 * (1 + np.abs(ref).max()), (pl, ph, out, ref)
