@@ -16,6 +16,7 @@ Under torchrun (N > 1) every rank plans its own replica of the workload
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -290,6 +291,56 @@ def batching(pk, n=512, max_iter=2000, check_every=50):
             "autotuned": choice, "autotune_s": t_tune}
 
 
+def differentiation(pk, K=2000, reps=3):
+    """Row f2: gradient of loss(z^K) = final kinetic energy + 10 x squared
+    collision slack with respect to starts, goals, radii and cost weights
+    through K unrolled iterations on the p = 256 circle swap (eta = 8,
+    r = 0.02), against the plain solver running the same K iterations.  The
+    forward keeps ceil(sqrt(K)) checkpoints; the backward replays each
+    segment and runs the adjoint kernels.  Times are CUDA events on the
+    planner's stream, best of reps."""
+    import torch
+    from paper_1311_4527_gb300 import losses
+    inst = workloads.circle256()
+    dev = torch.device("cuda")
+    radius = torch.tensor(inst.radius, dtype=torch.float32, device=dev)
+    cost = torch.tensor(inst.cost_w, dtype=torch.float32, device=dev)
+    pl = pk.Planner.from_instance(inst)
+
+    def timed(f):
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    t_plain = timed(lambda: (pl.reset(), pl.iterate(K)))
+    t_unroll = timed(lambda: pl.unroll(K))
+    z = pl.trajectory().requires_grad_(True)
+    loss = losses.plan_loss(z, radius, cost)
+    dz, = torch.autograd.grad(loss, z)
+    t_back = timed(lambda: pl.backward(dz))
+    gs, gg, gr, gc = pl.backward(dz)
+    torch.cuda.synchronize()
+    # translation equivariance: the position gradients sum to sum(dL/dz)
+    resid = (gs.double().sum(0) + gg.double().sum(0) - dz.double().reshape(-1, 2).sum(0)).abs().max()
+    pl.close()
+    return {"workload": f"circle256_eta8: p=256 circle swap, r=0.02, eta=8, K={K} unrolled FP32 "
+                        "iterations, loss = kinetic energy + 10 x squared collision slack",
+            "checkpoint_every": int(math.ceil(math.sqrt(K))), "loss": float(loss.detach()),
+            "plain_forward_ms": t_plain, "unroll_ms": t_unroll, "backward_ms": t_back,
+            "forward_plus_backward_ms": t_unroll + t_back,
+            "cost_vs_plain_forward": (t_unroll + t_back) / t_plain,
+            "grad_norms": {"start": float(gs.norm()), "goal": float(gg.norm()),
+                           "radius": float(gr.norm()), "cost": float(gc.norm())},
+            "translation_identity_residual": float(resid) / max(float(dz.abs().sum()), 1e-30)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,6 +493,7 @@ def main():
                                "plan_get_trajectory(host), pinned buffers"}
     if rank == 0 and world == 1 and not args.quick:
         line["batching"] = batching(pk)
+        line["differentiation"] = differentiation(pk)
         line["time_to_converge"] = time_to_converge(
             pk, ["circle4_eta4", "circle100_eta8", "square1024_eta16"], ["circle4_eta4"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

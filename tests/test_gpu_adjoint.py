@@ -3,7 +3,8 @@ FP64 oracle adjoint on small instances, and against the identities that hold
 at any size on the p = 256 circle swap with K = 2000 unrolled iterations.
 
 Error bound of the FP32 adjoint: every entry of each gradient group within
-2e-3 of that group's largest magnitude (the FP32 forward drifts from the FP64
+2e-4 of that group's largest magnitude (measured: 3e-5 on the p = 4 circle,
+3e-7 on the fixed-end case; the FP32 forward drifts from the FP64
 one by ~1e-6 relative per iteration, and the minimizer Jacobians are
 evaluated in FP32 at that drifted point)."""
 import numpy as np
@@ -14,7 +15,7 @@ from oracle import adjoint, twa
 
 pytestmark = pytest.mark.gpu
 GROUPS = ("start", "goal", "radius", "cost")
-TOL = 2e-3
+TOL = 2e-4
 
 
 def _planner(prob, **kw):
