@@ -127,6 +127,54 @@ def energy_prox(n_lo, n_hi, rho_lo, rho_hi, c):
 
 
 # --------------------------------------------------------------------------
+# maximum and minimum velocity minimizers (Appendices F and G)
+# --------------------------------------------------------------------------
+
+def velocity_prox(n_lo, n_hi, rho_lo, rho_hi, C, kind):
+    """Minimizer of rho_lo/2 |x_lo - n_lo|^2 + rho_hi/2 |x_hi - n_hi|^2 subject
+    to |x_lo - x_hi| <= C (kind "max", Appendix F) or >= C (kind "min",
+    Appendix G).  Returns (x_lo, x_hi, active): inactive (the n's already
+    satisfy the limit) gives x = n and outgoing weights 0 (Section 3.3).
+
+    Active finite weights follow the appendix: with
+    lambda = (|n_lo - n_hi| / C - 1) / (1/rho_lo + 1/rho_hi),
+    x_lo = (rho_lo (rho_hi + lambda) n_lo + lambda rho_hi n_hi) /
+           (rho_lo rho_hi + lambda (rho_lo + rho_hi)) and symmetrically x_hi,
+    which scales x_lo - x_hi to length C along n_lo - n_hi.  An infinite
+    weight keeps that end; a zero weight against a positive one moves only
+    the zero-weight end (the limit rho -> 0+); both zero are equal weights
+    (as the appendices prescribe).  For "min" with n_lo = n_hi the direction
+    is undefined; x_hi - x_lo is then taken along (1, 0) (reading R19).
+    """
+    n_lo = np.asarray(n_lo, dtype=np.float64)
+    n_hi = np.asarray(n_hi, dtype=np.float64)
+    C = float(C)
+    d = n_lo - n_hi
+    L = math.hypot(d[0], d[1])
+    active = (L > C) if kind == "max" else (L < C)
+    if not active:
+        return n_lo.copy(), n_hi.copy(), False
+    if rho_lo == INF and rho_hi == INF:
+        return n_lo.copy(), n_hi.copy(), True
+    if rho_lo == 0.0 and rho_hi == 0.0:
+        rho_lo = rho_hi = 1.0
+    u = d / L if L > 0.0 else np.array([-1.0, 0.0])   # unit x_lo - x_hi
+    if rho_lo == INF or rho_hi == 0.0:
+        return n_lo.copy(), n_lo - C * u, True
+    if rho_hi == INF or rho_lo == 0.0:
+        return n_hi + C * u, n_hi.copy(), True
+    if L == 0.0:
+        mean = (rho_lo * n_lo + rho_hi * n_hi) / (rho_lo + rho_hi)
+        return (mean + (rho_hi / (rho_lo + rho_hi)) * C * u,
+                mean - (rho_lo / (rho_lo + rho_hi)) * C * u, True)
+    lam = (L / C - 1.0) / (1.0 / rho_lo + 1.0 / rho_hi)
+    den = rho_lo * rho_hi + lam * (rho_lo + rho_hi)
+    x_lo = (rho_lo * (rho_hi + lam) * n_lo + lam * rho_hi * n_hi) / den
+    x_hi = (rho_hi * (rho_lo + lam) * n_hi + lam * rho_lo * n_lo) / den
+    return x_lo, x_hi, True
+
+
+# --------------------------------------------------------------------------
 # agent-obstacle minimizer on a disk or capsule (Appendices D and I)
 # --------------------------------------------------------------------------
 
@@ -212,7 +260,7 @@ def _tangent_normals(q, c, r):
     external point q to the circle of radius r at c)."""
     d = np.asarray(q, dtype=np.float64) - np.asarray(c, dtype=np.float64)
     L2 = float(np.dot(d, d))
-    if L2 < r * r:
+    if L2 < r * r * (1.0 - 1e-12):  # a point on the circle up to rounding has one tangent
         return []
     s = math.sqrt(max(L2 - r * r, 0.0))
     perp = np.array([-d[1], d[0]])
@@ -245,6 +293,31 @@ def _pick(cands, energies):
     return best
 
 
+def project_out(q, c0, c1, r):
+    """Closest point to q outside the open capsule of radius r around
+    [c0, c1] (q itself when it is outside).  A point on the axis goes out
+    along the normal of smallest angle in [0, 2pi) (along (1, 0) for a
+    disk)."""
+    q = np.asarray(q, dtype=np.float64)
+    c0 = np.asarray(c0, dtype=np.float64)
+    c1 = np.asarray(c1, dtype=np.float64)
+    e = c1 - c0
+    ee = float(np.dot(e, e))
+    t = 0.0 if ee == 0.0 else min(1.0, max(0.0, float(np.dot(q - c0, e)) / ee))
+    c = c0 + t * e
+    d = q - c
+    L = math.hypot(d[0], d[1])
+    if L >= r:
+        return q.copy()
+    if L > 0.0:
+        return c + (r / L) * d
+    if ee == 0.0:
+        return c + np.array([r, 0.0])
+    n1 = np.array([-e[1], e[0]]) / math.sqrt(ee)
+    n = n1 if _angle(n1) < _angle(-n1) else -n1
+    return c + r * n
+
+
 def region_prox(a, b, w_lo, w_hi, c0, c1, r, want_gap=False):
     """Minimizer of w_lo/2 |v_lo - a|^2 + w_hi/2 |v_hi - b|^2 subject to the
     segment [v_lo, v_hi] staying out of the open capsule of radius r around
@@ -253,7 +326,10 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r, want_gap=False):
 
     Returns (v_lo, v_hi, theta) with theta the separating direction (None when
     [a, b] is already feasible or both ends are pinned).  w = inf pins that
-    end; both weights zero is the equal-weight limit of Appendix D.  With
+    end; both weights zero is the equal-weight limit of Appendix D; one weight
+    zero and the other finite is the limit of that weight -> 0+ (reading R18:
+    the other end moves out of the region, then this end solves the
+    fixed-end problem).  With
     want_gap a fourth value is returned: the relative energy gap to the
     runner-up direction (see ``_gap``).
     """
@@ -267,8 +343,18 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r, want_gap=False):
         return (a.copy(), b.copy(), None) + ((INF,) if want_gap else ())
     if w_lo == 0.0 and w_hi == 0.0:
         w_lo = w_hi = 1.0  # equal weights: the argmin does not depend on their value
-    if (w_lo == 0.0) != (w_hi == 0.0):
-        raise NotImplementedError("a zero weight on one end only (no kinetic cost term)")
+    if w_lo == 0.0 and w_hi != INF or w_hi == 0.0 and w_lo != INF:
+        # One weight -> 0+ with the other finite: the limit of the argmin is
+        # lexicographic.  The weighted end moves the least any feasible
+        # segment allows, which is out of the region (a segment shrunk to that
+        # point is feasible); the free end then solves the fixed-end problem.
+        if w_lo == 0.0:
+            v_hi = project_out(b, c0, c1, r)
+            out = region_prox(a, v_hi, 1.0, INF, c0, c1, r, want_gap=want_gap)
+            return (out[0], v_hi) + tuple(out[2:])
+        v_lo = project_out(a, c0, c1, r)
+        out = region_prox(v_lo, b, INF, 1.0, c0, c1, r, want_gap=want_gap)
+        return (v_lo, out[1]) + tuple(out[2:])
 
     centres = [c0] if np.array_equal(c0, c1) else [c0, c1]
     kinks = []
@@ -280,6 +366,8 @@ def region_prox(a, b, w_lo, w_hi, c0, c1, r, want_gap=False):
         # One end pinned: v at that end is fixed; theta ranges over the arc of
         # directions that separate the pinned point from the region.
         pin, free, w_free = (a, b, w_hi) if w_lo == INF else (b, a, w_lo)
+        if w_free == 0.0:
+            w_free = 1.0  # the free end's argmin does not depend on its weight
         cands = list(kinks)
         for c in centres:
             cands += [_angle(n) for n in _tangent_normals(pin, c, r)]

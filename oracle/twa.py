@@ -10,7 +10,14 @@ and goal; each carries a position factor that always sends weight infinity
   c_{i,s} = C_{i,s} / (p eta) (Eq. velo_cost_pair_wise); weight rho0 always;
 * collision factor (s, i < j): f^coll_{r_i, r_j} on the four nodes
   (i,s), (i,s+1), (j,s), (j,s+1) (Eq. f_coll_def); weight 0 or rho0;
-* wall factor (w, i, s): f^wall for wall w (Eq. wall_minimizer); 0 or rho0.
+* wall factor (w, i, s): f^wall for wall w (Eq. wall_minimizer); 0 or rho0;
+* optional maximum / minimum velocity factors (i, s): |x_i(s) - x_i(s+1)|
+  <= vmax_{i,s} or >= vmin_{i,s} (Eq. max_vel_min and the reversed
+  inequality, Appendices F and G); 0 or rho0.
+
+``energy=False`` drops the kinetic factors: the feasibility problem of
+Eq. basic_opt_prob (Section 4 compares it with the energy problem), where
+break-points can receive only zero weights.
 
 One iteration is the seven steps of Appendix B, in order.  Readings where the
 text is silent or its figure is missing (the special u and back-weight rules of
@@ -60,6 +67,9 @@ class Problem:
     u_keep: bool = False
     cost_unnorm: bool = False
     admm: bool = False          # standard ADMM: every factor always sends rho0
+    energy: bool = True         # kinetic-energy factors present
+    vmax: np.ndarray | None = None   # (p, eta) limits of |x(s+1) - x(s)|, or None
+    vmin: np.ndarray | None = None
     warm_iters: int = 0
     warm_rho: float = 0.0
 
@@ -97,10 +107,11 @@ class State:
     u_wall: np.ndarray         # (n_walls, eta, p, 2, 2)
     wback: np.ndarray          # (p, eta+1) back-weight class
     k: int = 0
+    u_vel: dict = field(default_factory=dict)   # "max" / "min" -> (eta, p, 2, 2)
 
     def copy(self):
         return State(self.z.copy(), self.u_coll.copy(), self.u_kin.copy(), self.u_wall.copy(),
-                     self.wback.copy(), self.k)
+                     self.wback.copy(), self.k, {k: v.copy() for k, v in self.u_vel.items()})
 
 
 @dataclass
@@ -128,8 +139,10 @@ def initial_state(prob: Problem) -> State:
     wback = np.full((p, eta + 1), WR, dtype=np.int8)
     wback[:, 0] = WI
     wback[:, eta] = WI
+    u_vel = {kind: np.zeros((eta, p, 2, 2)) for kind, lim in (("max", prob.vmax), ("min", prob.vmin))
+             if lim is not None}
     return State(z=z, u_coll=np.zeros((eta, P, 4, 2)), u_kin=np.zeros((eta, p, 2, 2)),
-                 u_wall=np.zeros((prob.n_walls, eta, p, 2, 2)), wback=wback, k=0)
+                 u_wall=np.zeros((prob.n_walls, eta, p, 2, 2)), wback=wback, k=0, u_vel=u_vel)
 
 
 def _wnum(cls, rho0):
@@ -145,6 +158,8 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     inactive): the two places where a lower-precision solver may take the
     other branch."""
     p, eta = prob.p, prob.eta
+    assert not (prob.admm and (not prob.energy or prob.vmax is not None or prob.vmin is not None)), \
+        "standard-ADMM mode is defined here with the kinetic factors only"
     rho0 = prob.rho_at(st.k)
     z = st.z
     wb = st.wback
@@ -162,7 +177,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     # --- kinetic factors: steps 1-4 -------------------------------------
     x_kin = np.empty_like(st.u_kin)
     n_kin = np.empty_like(st.u_kin)
-    for s in range(eta):
+    for s in range(eta if prob.energy else 0):
         n_kin[s, :, 0] = z[:, s] - st.u_kin[s, :, 0]
         n_kin[s, :, 1] = z[:, s + 1] - st.u_kin[s, :, 1]
         for i in range(p):
@@ -170,7 +185,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
                 n_kin[s, i, 0], n_kin[s, i, 1], _wnum(wb[i, s], rho0),
                 _wnum(wb[i, s + 1], rho0), cc[i, s])
     m_kin = x_kin + st.u_kin
-    for s in range(eta):
+    for s in range(eta if prob.energy else 0):
         for e, ss in ((0, s), (1, s + 1)):
             num[:, ss] += rho0 * m_kin[s, :, e]
             den[:, ss] += rho0
@@ -262,15 +277,41 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
                         edges.append((i, ss, mv.copy(), rho0))
             active_wall[w, s] = act
 
+    # --- velocity factors (Appendices F, G) --------------------------------
+    vel_x = {}
+    active_vel = {}
+    for kind, lim in (("max", prob.vmax), ("min", prob.vmin)):
+        if lim is None:
+            continue
+        u = st.u_vel[kind]
+        act = np.zeros((eta, p), dtype=bool)
+        for s in range(eta):
+            for i in range(p):
+                n_lo = z[i, s] - u[s, i, 0]
+                n_hi = z[i, s + 1] - u[s, i, 1]
+                x_lo, x_hi, a = prox.velocity_prox(n_lo, n_hi, _wnum(wb[i, s], rho0),
+                                                   _wnum(wb[i, s + 1], rho0), lim[i, s], kind)
+                act[s, i] = a
+                if not a:
+                    continue
+                vel_x[(kind, s, i)] = (x_lo, x_hi)
+                for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):
+                    mv = xv + u[s, i, e]
+                    num[i, ss] += rho0 * mv
+                    den[i, ss] += rho0
+                    if record_edges:
+                        edges.append((i, ss, mv.copy(), rho0))
+        active_vel[kind] = act
+
     # --- step 5: consensus z ----------------------------------------------
     z_new = np.empty_like(z)
     pos = den > 0
     z_new[pos] = num[pos] / den[pos][:, None]
     # all incoming weights zero: treat them as 1, i.e. the plain mean of every
-    # incoming m.  An inactive factor returns x = n, so its m = n + u = z^k.
+    # incoming m.  Every factor at such a node is inactive and returns x = n,
+    # so each of its messages is m = n + u = z^k: the mean is z^k.
     zero_nodes = (~pos) & (~pinned)
-    if np.any(zero_nodes):
-        z_new[zero_nodes] = _plain_mean_all_edges(prob, st, zero_nodes, m_kin, coll_x, wall_x)
+    z_new[zero_nodes] = z[zero_nodes]
     z_new[:, 0] = prob.start
     z_new[:, eta] = prob.goal
 
@@ -295,7 +336,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         return np.where(ok[..., None], step, reset)
 
     # kinetic: forward weight always rho0
-    for s in range(eta):
+    for s in range(eta if prob.energy else 0):
         allp = np.arange(p)
         for e, ss in ((0, s), (1, s + 1)):
             new.u_kin[s, :, e] = upd(st.u_kin[s, :, e], x_kin[s, :, e], allp, np.full(p, ss),
@@ -314,6 +355,17 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
                 new.u_coll[s][idx, e] = upd(u[idx, e], xa[:, e], nodes_i[e], si,
                                             np.ones(idx.shape[0], dtype=bool))
                 primal = max(primal, float(np.max(np.abs(xa[:, e] - z_new[nodes_i[e], nodes_s[e]]))))
+    # velocity factors: inactive ones reset u (or keep it)
+    for kind, act in active_vel.items():
+        u_old = st.u_vel[kind]
+        new.u_vel[kind] = u_old.copy() if prob.u_keep else np.zeros_like(u_old)
+        for (kd, s, i), (x_lo, x_hi) in vel_x.items():
+            if kd != kind:
+                continue
+            for e, ss, xv in ((0, s, x_lo), (1, s + 1, x_hi)):
+                new.u_vel[kind][s, i, e] = upd(u_old[s, i, e][None], xv[None], np.array([i]),
+                                               np.array([ss]), np.array([True]))[0]
+                primal = max(primal, float(np.max(np.abs(xv - z_new[i, ss]))))
     # walls
     for w in range(nw):
         for s in range(eta):
@@ -330,6 +382,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     dz = float(np.max(np.abs(z_new - z)))
     info = Info(active_coll=active_coll, active_wall=active_wall, residual=max(primal, dz),
                 primal=primal, dz=dz)
+    info.extra["active_vel"] = active_vel
     if record_branches:
         info.extra.update(coll_margin=coll_margin, coll_gap=coll_gap, wall_margin=wall_margin,
                           wall_gap=wall_gap)
@@ -338,37 +391,6 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         info.extra["x_kin"] = x_kin
         info.extra["coll_x"] = coll_x
     return new, info
-
-
-def _plain_mean_all_edges(prob, st, mask, m_kin, coll_x, wall_x):
-    """Step 5's all-zero rule for the nodes in ``mask``: the plain mean of
-    every incoming m.  Only reachable without a kinetic cost term."""
-    p, eta = prob.p, prob.eta
-    iu, ju = pairs(p)
-    tot = np.zeros((p, eta + 1, 2))
-    cnt = np.zeros((p, eta + 1))
-    for s in range(eta):
-        for e, ss in ((0, s), (1, s + 1)):
-            tot[:, ss] += m_kin[s, :, e]
-            cnt[:, ss] += 1
-        # collision factors: m = x + u, with x = n for the inactive ones
-        u = st.u_coll[s]
-        m = np.stack([st.z[iu, s], st.z[iu, s + 1], st.z[ju, s], st.z[ju, s + 1]], axis=1)
-        idx, xa = coll_x[s]
-        if idx.shape[0]:
-            m[idx] = xa + u[idx]
-        for e, (ni, ss) in enumerate(((iu, s), (iu, s + 1), (ju, s), (ju, s + 1))):
-            np.add.at(tot, (ni, ss), m[:, e])
-            np.add.at(cnt, (ni, ss), 1)
-    for w in range(prob.n_walls):
-        for s in range(eta):
-            for i in range(p):
-                for e, ss in ((0, s), (1, s + 1)):
-                    xv = wall_x.get((w, s, i), (None, None))[e]
-                    mv = st.z[i, ss] if xv is None else xv + st.u_wall[w, s, i, e]
-                    tot[i, ss] += mv
-                    cnt[i, ss] += 1
-    return tot[mask] / cnt[mask][:, None]
 
 
 def solve(prob: Problem, tol: float, max_iter: int, st: State | None = None):

@@ -109,3 +109,13 @@ def test_standard_admm_mode_parity():
     _run(prob, [0, 4, 40])
     prob = _prob(workloads.small_square(40, 5, seed=9), cost_unnorm=True, admm=True)
     _run(prob, [0, 6])
+
+
+def test_interior_wall_segments_parity():
+    """Static obstacles beyond the bounding box (Section 3.2): five interior
+    axis-aligned wall segments plus the four sides; p = 48 (two tiles, the
+    second ragged)."""
+    inst = workloads.obstacle_square(48, 6, 10.0, 5, 7)
+    prob = _prob(inst, cost_unnorm=True)
+    stats = _run(prob, [0, 3, 30, 150])
+    assert sum(s.get("wall_active", 0) for s in stats) > 0, stats

@@ -147,6 +147,67 @@ def random_square(p: int, eta: int, side: float, r_lo: float, r_hi: float, seed:
                 f"{w.shape[0]} walls, eta={eta}, seed={seed}"))
 
 
+def _clear_of_walls(pos: np.ndarray, r: float, walls: np.ndarray) -> bool:
+    """pos at distance >= r from every axis-aligned wall segment."""
+    for x0, y0, x1, y1 in walls:
+        cx = min(max(pos[0], min(x0, x1)), max(x0, x1))
+        cy = min(max(pos[1], min(y0, y1)), max(y0, y1))
+        if math.hypot(pos[0] - cx, pos[1] - cy) < r:
+            return False
+    return True
+
+
+def obstacle_square(p: int, eta: int, side: float, n_obstacles: int, seed: int, *,
+                    r_lo: float = 0.2, r_hi: float = 0.4, rho0: float = 1.0,
+                    alpha: float = 0.1, max_iter: int = 20000, name=None) -> Instance:
+    """CONF2 with static obstacles: the random square's four sides plus
+    n_obstacles interior wall segments (Section 3.2), each axis-aligned,
+    horizontal or vertical with equal odds, of length U[side/8, side/4],
+    centred uniformly in the middle 80% of the square.  Starts and goals are
+    rejection-sampled without overlap and at least r_i from every wall.
+
+    Draw order: radii, walls, then starts, then goals (each position drawn
+    until it clears the walls and the disks placed before it).
+    """
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(r_lo, r_hi, size=p)
+    L = float(side)
+    walls = [[0, 0, L, 0], [L, 0, L, L], [L, L, 0, L], [0, L, 0, 0]]
+    for _ in range(n_obstacles):
+        half = 0.5 * rng.uniform(L / 8, L / 4)
+        cx, cy = rng.uniform(0.1 * L, 0.9 * L, size=2)
+        if rng.uniform() < 0.5:
+            walls.append([cx - half, cy, cx + half, cy])
+        else:
+            walls.append([cx, cy - half, cx, cy + half])
+    w = np.asarray(walls, dtype=np.float64)
+
+    def place():
+        pos = np.zeros((p, 2))
+        for i in range(p):
+            for _ in range(100000):
+                cand = rng.uniform(r[i], L - r[i], size=2)
+                if not _clear_of_walls(cand, r[i], w[4:]):
+                    continue
+                d = np.hypot(pos[:i, 0] - cand[0], pos[:i, 1] - cand[1])
+                if np.all(d >= r[:i] + r[i]):
+                    break
+            else:
+                raise RuntimeError("rejection sampling did not place every agent")
+            pos[i] = cand
+        return pos
+
+    start = place()
+    goal = place()
+    return Instance(
+        name=name or f"obstacles{p}_eta{eta}_s{seed}", p=p, eta=eta, T=1.0, start=start,
+        goal=goal, radius=r, cost_w=np.ones(p), walls=w, rho0=rho0, alpha=alpha,
+        tol=1e-6 * max(1.0, L), max_iter=max_iter,
+        recipe=(f"random square with obstacles: p={p}, side {side}, radii U[{r_lo},{r_hi}], "
+                f"4 sides + {n_obstacles} axis-aligned interior walls of length U[side/8, side/4], "
+                f"starts and goals clear of walls and of each other, eta={eta}, seed={seed}"))
+
+
 # --- the named workloads -----------------------------------------------------
 
 def circle4() -> Instance:
