@@ -57,6 +57,14 @@ typedef enum {
                                             iteration, zeros included (else only active ones) */
 #define PLAN_ADMM              (1u << 4) /* standard ADMM (App. B): every factor always sends
                                             rho0; implies the dense state */
+#define PLAN_NO_ENERGY         (1u << 5) /* no kinetic factors: the feasibility problem of
+                                            Eq. basic_opt_prob (Section 4); break-points
+                                            can then receive only zero weights */
+#define PLAN_VMAX              (1u << 6) /* a maximum-velocity factor per agent segment,
+                                            |x(s+1) - x(s)| <= vmax (Eq. max_vel_min, App. F) */
+#define PLAN_VMIN              (1u << 7) /* a minimum-velocity factor per agent segment,
+                                            |x(s+1) - x(s)| >= vmin (the reversed Eq.
+                                            max_vel_min, App. G) */
 
 typedef struct {
   int p;              /* agents, >= 1 */
@@ -213,6 +221,44 @@ plan_status plan_batch_set_shape(plan_batch_t batch, int rows_per_warp, int prox
                                  int iterations_per_graph);
 void plan_batch_destroy(plan_batch_t batch);
 
+/*
+ * Velocity limits and the feasibility problem (Section 3.3 "minimum energy
+ * and maximum (minimum) velocity minimizer", Appendices F and G, Section 4).
+ *
+ * plan_set_velocity_limits: host arrays p x eta of the per-segment limits on
+ * |x_i(s+1) - x_i(s)| (distance per segment); vmax needs PLAN_VMAX (values
+ * > 0, +inf allowed), vmin needs PLAN_VMIN (finite, >= 0); either may be NULL
+ * to keep the current values.  Until set, maxima are +inf and minima 0 (no
+ * factor ever activates).  Each factor sends rho0 while the n-messages
+ * violate its limit and 0 otherwise.
+ *
+ * plan_export_velocity_state / plan_import_velocity_state: the velocity
+ * factors' u (DEVICE, eta x p x 2 x 2, edges (i,s), (i,s+1)) and activity
+ * (eta x p bytes, export only); any pointer may be NULL.  plan_import_state
+ * resets these to 0, so import them after it.
+ *
+ * plan_set_energy(plan, 0) switches the kinetic factors off from the next
+ * iteration (the feasibility problem from the current state: the paper's
+ * recovery of collision-free paths from a solve stopped early); 1 switches
+ * them back on with their u restarted at 0.  Without kinetic factors a
+ * break-point whose factors all sent 0 gets back weight 0 (App. B step 6),
+ * and the minimizers take the limit of that weight -> 0+.
+ *
+ * Not combined with PLAN_ADMM; batches, plan_iterate_static and the adjoint
+ * return PLAN_EUNSUPPORTED for these modes.
+ */
+plan_status plan_set_velocity_limits(plan_t plan, const float* vmax, const float* vmin);
+plan_status plan_export_velocity_state(plan_t plan, float* u_vmax, float* u_vmin,
+                                       uint8_t* act_vmax, uint8_t* act_vmin);
+plan_status plan_import_velocity_state(plan_t plan, const float* u_vmax, const float* u_vmin);
+plan_status plan_set_energy(plan_t plan, int on);
+/* Back-weight class of every break-point (App. B step 6), DEVICE p x (eta+1)
+ * bytes: 0 zero, 1 rho0, 2 infinite (the fixed ends).  Export works in every
+ * mode; import (feasibility problem only; fixed ends ignored) replaces the
+ * classes that plan_import_state / plan_import_velocity_state otherwise infer
+ * from which imported u are nonzero. */
+plan_status plan_export_back_weights(plan_t plan, uint8_t* classes);
+plan_status plan_import_back_weights(plan_t plan, const uint8_t* classes);
 /* Replace the radii (host, p) and/or the kinetic cost weights (host, laid
  * out as cost_w of plan_create) and keep the current iterate; either pointer
  * may be NULL.  New radii are checked against the endpoints like in

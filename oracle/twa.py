@@ -280,15 +280,19 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     # --- velocity factors (Appendices F, G) --------------------------------
     vel_x = {}
     active_vel = {}
+    vel_margin = {}
     for kind, lim in (("max", prob.vmax), ("min", prob.vmin)):
         if lim is None:
             continue
         u = st.u_vel[kind]
         act = np.zeros((eta, p), dtype=bool)
+        vel_margin[kind] = np.full((eta, p), INF)
         for s in range(eta):
             for i in range(p):
                 n_lo = z[i, s] - u[s, i, 0]
                 n_hi = z[i, s + 1] - u[s, i, 1]
+                if lim[i, s] > 0.0 and math.isfinite(lim[i, s]):
+                    vel_margin[kind][s, i] = (float(np.linalg.norm(n_lo - n_hi)) - lim[i, s]) / lim[i, s]
                 x_lo, x_hi, a = prox.velocity_prox(n_lo, n_hi, _wnum(wb[i, s], rho0),
                                                    _wnum(wb[i, s + 1], rho0), lim[i, s], kind)
                 act[s, i] = a
@@ -383,6 +387,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     info = Info(active_coll=active_coll, active_wall=active_wall, residual=max(primal, dz),
                 primal=primal, dz=dz)
     info.extra["active_vel"] = active_vel
+    info.extra["vel_margin"] = vel_margin
     if record_branches:
         info.extra.update(coll_margin=coll_margin, coll_gap=coll_gap, wall_margin=wall_margin,
                           wall_gap=wall_gap)

@@ -22,13 +22,16 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["Planner", "PlannerBatch", "PlanError", "load_library", "unrolled_trajectory",
            "PLAN_U_KEEP", "PLAN_COST_UNNORM", "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE",
-           "PLAN_ADMM", "EXPORTED_SYMBOLS"]
+           "PLAN_ADMM", "PLAN_NO_ENERGY", "PLAN_VMAX", "PLAN_VMIN", "EXPORTED_SYMBOLS"]
 
 PLAN_U_KEEP = 1 << 0
 PLAN_COST_UNNORM = 1 << 1
 PLAN_COST_PER_SEGMENT = 1 << 2
 PLAN_DENSE_STATE = 1 << 3
 PLAN_ADMM = 1 << 4
+PLAN_NO_ENERGY = 1 << 5
+PLAN_VMAX = 1 << 6
+PLAN_VMIN = 1 << 7
 
 STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: "PLAN_ENOTCONV",
           5: "PLAN_ENUMERIC", 6: "PLAN_EINFEASIBLE_INPUT", 7: "PLAN_EUNSUPPORTED"}
@@ -40,7 +43,9 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_batch_workspace_size", "plan_batch_create", "plan_batch_iterate",
                     "plan_batch_solve", "plan_batch_get_trajectory", "plan_batch_autotune",
                     "plan_batch_set_shape", "plan_batch_destroy", "plan_set_params",
-                    "plan_unroll"]
+                    "plan_unroll", "plan_set_velocity_limits", "plan_export_velocity_state",
+                    "plan_import_velocity_state", "plan_set_energy", "plan_export_back_weights",
+                    "plan_import_back_weights"]
 
 
 class PlanError(RuntimeError):
@@ -92,6 +97,12 @@ def load_library(path: str | None = None):
     lib.plan_backward.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.plan_set_params.argtypes = [c_void_p, fp, fp]
     lib.plan_unroll.argtypes = [c_void_p, c_int, c_int]
+    lib.plan_set_velocity_limits.argtypes = [c_void_p, fp, fp]
+    lib.plan_export_velocity_state.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.plan_import_velocity_state.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.plan_set_energy.argtypes = [c_void_p, c_int]
+    lib.plan_export_back_weights.argtypes = [c_void_p, c_void_p]
+    lib.plan_import_back_weights.argtypes = [c_void_p, c_void_p]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
     pp = POINTER(c_void_p)
@@ -145,7 +156,7 @@ class Planner:
 
     def __init__(self, start, goal, radius, eta, cost_w=None, walls=None, rho0=1.0, alpha=0.1,
                  tol=1e-6, max_iter=20000, flags=0, check_every=50, warm_iters=0, warm_rho=0.0,
-                 T=1.0, device=None, stream=None):
+                 T=1.0, device=None, stream=None, energy=True, vmax=None, vmin=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Planner needs a CUDA device (there is no CPU fallback)")
@@ -157,6 +168,12 @@ class Planner:
         cost_w = np.asarray(cost_w, dtype=np.float64)
         if cost_w.ndim == 2:
             flags |= PLAN_COST_PER_SEGMENT
+        if not energy:
+            flags |= PLAN_NO_ENERGY
+        if vmax is not None:
+            flags |= PLAN_VMAX
+        if vmin is not None:
+            flags |= PLAN_VMIN
         walls = np.zeros((0, 4)) if walls is None else np.asarray(walls, dtype=np.float64).reshape(-1, 4)
         self.p, self.eta, self.n_walls = p, int(eta), int(walls.shape[0])
         self.flags = flags
@@ -179,6 +196,8 @@ class Planner:
                                    c_void_p(self.workspace.data_ptr()), nbytes.value,
                                    c_void_p(self.stream.cuda_stream), byref(h)))
         self._h = h
+        if vmax is not None or vmin is not None:
+            self.set_velocity_limits(vmax, vmin)
 
     @classmethod
     def from_instance(cls, inst, **kw):
@@ -241,6 +260,60 @@ class Planner:
             shape = (self.p, self.eta) if self.flags & PLAN_COST_PER_SEGMENT else (self.p,)
             cw = _f32(cost_w, shape)
         _check(_lib.plan_set_params(self._h, rd[1], cw[1]))
+
+    # -- velocity limits and the feasibility problem -------------------------
+    def set_velocity_limits(self, vmax=None, vmin=None):
+        """Per-segment limits (p, eta) on |x(s+1) - x(s)|; scalars broadcast."""
+        full = lambda v: np.broadcast_to(np.asarray(v, dtype=np.float64), (self.p, self.eta))
+        mx = _f32(full(vmax), (self.p, self.eta)) if vmax is not None else (None, None)
+        mn = _f32(full(vmin), (self.p, self.eta)) if vmin is not None else (None, None)
+        _check(_lib.plan_set_velocity_limits(self._h, mx[1], mn[1]))
+
+    def set_energy(self, on: bool):
+        """Switch the kinetic factors on or off (off: the feasibility problem
+        from the current state)."""
+        _check(_lib.plan_set_energy(self._h, 1 if on else 0))
+
+    def export_velocity_state(self):
+        import torch
+        dev = self.device
+        out = {}
+        ptr = lambda t: c_void_p(t.data_ptr()) if t is not None else None
+        u = {k: torch.empty((self.eta, self.p, 2, 2), dtype=torch.float32, device=dev)
+             if self.flags & f else None for k, f in (("max", PLAN_VMAX), ("min", PLAN_VMIN))}
+        a = {k: torch.empty((self.eta, self.p), dtype=torch.uint8, device=dev)
+             if self.flags & f else None for k, f in (("max", PLAN_VMAX), ("min", PLAN_VMIN))}
+        _check(_lib.plan_export_velocity_state(self._h, ptr(u["max"]), ptr(u["min"]),
+                                               ptr(a["max"]), ptr(a["min"])))
+        torch.cuda.current_stream(dev).synchronize()
+        for k in ("max", "min"):
+            if u[k] is not None:
+                out[k] = (u[k], a[k])
+        return out
+
+    def import_velocity_state(self, u_vmax=None, u_vmin=None):
+        import torch
+        dev = self.device
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(dev) if a is not None else None
+        um, un = t(u_vmax), t(u_vmin)
+        self._keep_vel = [um, un]
+        ptr = lambda x: c_void_p(x.data_ptr()) if x is not None else None
+        _check(_lib.plan_import_velocity_state(self._h, ptr(um), ptr(un)))
+        torch.cuda.current_stream(dev).synchronize()
+
+    def export_back_weights(self):
+        """(p, eta+1) uint8 classes: 0 zero, 1 rho0, 2 infinite."""
+        import torch
+        out = torch.empty((self.p, self.eta + 1), dtype=torch.uint8, device=self.device)
+        _check(_lib.plan_export_back_weights(self._h, c_void_p(out.data_ptr())))
+        torch.cuda.current_stream(self.device).synchronize()
+        return out
+
+    def import_back_weights(self, classes):
+        import torch
+        t = torch.as_tensor(np.ascontiguousarray(classes, dtype=np.uint8)).to(self.device)
+        _check(_lib.plan_import_back_weights(self._h, c_void_p(t.data_ptr())))
+        torch.cuda.current_stream(self.device).synchronize()
 
     # -- differentiation ---------------------------------------------------
     def unroll(self, K: int, checkpoint_every: int = 0):

@@ -76,7 +76,7 @@ __global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * P.nw;
+    const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * (P.nw + P.nv);
     const double bound = 8.0 * ((double)red[0] + 1.0);
     int e = (int)floor(log2(4.611686018427388e18 / (bound * edges)));
     e = e < 8 ? 8 : (e > 60 ? 60 : e);
@@ -136,13 +136,13 @@ __global__ void residual_kernel(Dev P) {
   }
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  for (int t = gt; t < P.eta * P.p; t += nth) {
+  for (int t = gt; t < (P.noenergy ? 0 : P.eta * P.p); t += nth) {
     const int s = t / P.p, i = t - s * P.p;
     float4 x = P.xkin[t];
     if (s != 0) res = fmaxf(res, maxabs2(lo2(x) - P.z[(size_t)i * E1 + s]));
     if (s != P.eta - 1) res = fmaxf(res, maxabs2(hi2(x) - P.z[(size_t)i * E1 + s + 1]));
   }
-  for (int t = gt; t < P.nw * P.eta * P.p; t += nth) {
+  for (int t = gt; t < (P.nw + P.nv) * P.eta * P.p; t += nth) {
     const int i = t % P.p;
     const int ws = t / P.p;
     const int s = ws % P.eta;
@@ -251,6 +251,7 @@ __global__ void export_seg_kernel(Dev P, float* u_kin, float* u_wall, uint8_t* a
     float4 u4 = P.ukin[t], x4 = P.xkin[t];
     float2 ul = finish_u(true, s == 0, false, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
     float2 uh = finish_u(true, s == P.eta - 1, false, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+    if (P.noenergy) { ul = mk(0.f, 0.f); uh = ul; }  // no kinetic factors
     if (u_kin) {
       float* o = u_kin + (size_t)t * 4;
       o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
@@ -333,7 +334,7 @@ __global__ void import_seg_kernel(Dev P, const float* u_kin, const float* u_wall
 __global__ void import_wbits_kernel(Dev P) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (w, s, tile, lane)
   const int lane = threadIdx.x & 31;
-  const int words = P.nw * P.eta * P.nt;
+  const int words = (P.nw + P.nv) * P.eta * P.nt;
   const int w = t >> 5;
   bool nz = false;
   if (w < words) {
@@ -346,6 +347,106 @@ __global__ void import_wbits_kernel(Dev P) {
   }
   uint32_t word = __ballot_sync(FULL, nz);
   if (lane == 0 && w < words) P.wbits[w] = word;
+}
+
+// Velocity kinds (gated segment factors nw .. nw + nv - 1): export u and
+// activity; import u (pending x = z^k) and set bits where u != 0.
+__global__ void export_vel_kernel(Dev P, int v, float* u_vel, uint8_t* act) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nk = P.eta * P.p, E1 = P.eta + 1;
+  if (t >= nk) return;
+  const int i = t % P.p, s = t / P.p;
+  const size_t g = (size_t)(P.nw + v) * nk + t;
+  const size_t ws = (size_t)(P.nw + v) * P.eta + s;
+  const bool bprev = (P.wbits[ws * P.nt + i / TILE] >> (i % TILE)) & 1u;
+  float4 u4 = P.uwall[g], x4 = P.xwall[g];
+  if (!P.dense && !bprev) u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float dummy = 0.f;
+  const float2 ul = finish_u(bprev, s == 0, P.keep, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
+  const float2 uh = finish_u(bprev, s == P.eta - 1, P.keep, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
+  if (u_vel) {
+    float* o = u_vel + (size_t)t * 4;
+    o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
+  }
+  if (act) act[t] = bprev ? 1 : 0;
+}
+
+__global__ void import_vel_kernel(Dev P, int v, const float* u_vel) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nk = P.eta * P.p, E1 = P.eta + 1;
+  if (t >= nk) return;
+  const int i = t % P.p, s = t / P.p;
+  const size_t g = (size_t)(P.nw + v) * nk + t;
+  float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (u_vel) u = make_float4(u_vel[4 * (size_t)t], u_vel[4 * (size_t)t + 1], u_vel[4 * (size_t)t + 2], u_vel[4 * (size_t)t + 3]);
+  P.uwall[g] = u;
+  P.xwall[g] = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s + 1]);
+}
+
+// Back-weight classes of the feasibility problem after an import: rho0 at
+// every node some factor sent rho0 to in the last iteration (a set activity
+// bit), else 0; every node at the initial state (k = 0, Section 4).
+__global__ void wnode_clear_kernel(Dev P, uint8_t value) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P.p * (P.eta + 1)) P.wnode[t] = value;
+}
+
+__global__ void wnode_from_bits_kernel(Dev P) {
+  const int E1 = P.eta + 1;
+  const size_t nslots = (size_t)P.eta * P.ntp * TILE * TILE;
+  const size_t nseg = (size_t)(P.nw + P.nv) * P.eta * P.p;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslots + nseg;
+       t += (size_t)gridDim.x * blockDim.x) {
+    if (t < nslots) {
+      const size_t row = t / TILE;
+      const int lane = (int)(t - row * TILE);
+      if (!((P.bits[row] >> lane) & 1u)) continue;
+      const size_t blk = row / TILE;
+      const int r = (int)(row - blk * TILE);
+      const int s = (int)(blk / P.ntp);
+      const int2 IJ = P.tiles[blk - (size_t)s * P.ntp];
+      const int i = IJ.x * TILE + r, j = IJ.y * TILE + lane;
+      P.wnode[(size_t)i * E1 + s] = 1; P.wnode[(size_t)i * E1 + s + 1] = 1;
+      P.wnode[(size_t)j * E1 + s] = 1; P.wnode[(size_t)j * E1 + s + 1] = 1;
+    } else {
+      const size_t g = t - nslots;
+      const int i = (int)(g % P.p);
+      const size_t ws = g / P.p;
+      const int s = (int)(ws % P.eta);
+      if ((P.wbits[ws * P.nt + i / TILE] >> (i % TILE)) & 1u) {
+        P.wnode[(size_t)i * E1 + s] = 1; P.wnode[(size_t)i * E1 + s + 1] = 1;
+      }
+    }
+  }
+}
+
+// Back-weight classes per node, out (export) or in (import): 2 at the fixed
+// ends, else the stored class (rho0 whenever the kinetic factors run).
+__global__ void back_weights_kernel(Dev P, uint8_t* out, const uint8_t* in) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int E1 = P.eta + 1;
+  if (t >= P.p * E1) return;
+  const int s = t % E1;
+  const bool fixed = (s == 0 || s == P.eta);
+  if (in) {
+    if (!fixed) P.wnode[t] = in[t] ? 1 : 0;
+  } else {
+    out[t] = fixed ? 2 : (P.noenergy ? P.wnode[t] : 1);
+  }
+}
+
+// New pending kinetic x = z, u = 0 (the kinetic factors switched back on).
+__global__ void kinetic_restart_kernel(Dev P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.eta * P.p) return;
+  const int s = t / P.p, i = t - s * P.p, E1 = P.eta + 1;
+  P.xkin[t] = pack(P.z[(size_t)i * E1 + s], P.z[(size_t)i * E1 + s + 1]);
+  P.ukin[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void fill_kernel(float* a, size_t n, float v) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = v;
 }
 
 __global__ void count_kernel(const uint32_t* words, size_t n, unsigned long long* out) {
@@ -382,7 +483,7 @@ plan_status fail(plan_status s, const char* fmt, ...) {
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t z0, z1, start, goal, radius, cost, walls, tiles;
+  size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
   size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wcount, accx, accy, accc, fix,
       res, status, count;
   size_t total;
@@ -396,6 +497,8 @@ bool sizes_ok(const plan_config* c) {
 
 Layout layout_for(const plan_config* c) {
   const size_t p = c->p, eta = c->eta, nw = c->n_walls;
+  const size_t nv = ((c->flags & PLAN_VMAX) ? 1 : 0) + ((c->flags & PLAN_VMIN) ? 1 : 0);
+  const size_t ng = nw + nv;  // gated segment-factor kinds: walls, then velocity limits
   const size_t nt = (p + TILE - 1) / TILE, ntp = nt * (nt + 1) / 2;
   const size_t slots = eta * ntp * TILE * TILE;
   Layout L{};
@@ -408,6 +511,8 @@ Layout layout_for(const plan_config* c) {
   L.radius = take(p * 4);
   L.cost = take(p * eta * 4);
   L.walls = take(nw * 16);
+  L.vlim = take(nv * p * eta * 4);
+  L.wnode = take(p * (eta + 1));
   L.tiles = take(ntp * 8);
   L.ulo = take(slots * 16);
   L.uhi = take(slots * 16);
@@ -416,9 +521,9 @@ Layout layout_for(const plan_config* c) {
   L.bits = take(eta * ntp * TILE * 4);
   L.ukin = take(eta * p * 16);
   L.xkin = take(eta * p * 16);
-  L.uwall = take(nw * eta * p * 16);
-  L.xwall = take(nw * eta * p * 16);
-  L.wbits = take(nw * eta * nt * 4);
+  L.uwall = take(ng * eta * p * 16);
+  L.xwall = take(ng * eta * p * 16);
+  L.wbits = take(ng * eta * nt * 4);
   L.work = take(slots * 4);
   L.wcount = take(2 * 4);
   L.accx = take(p * (eta + 1) * 8);
@@ -506,6 +611,9 @@ plan_status check_endpoints(int p, const float* start, const float* goal, const 
 struct plan_s {
   plan_config cfg;
   int p, eta, nw, nt, ntp;
+  int nv = 0;             // velocity-limit kinds (PLAN_VMAX, PLAN_VMIN)
+  unsigned vmin_mask = 0; // which of them are minima
+  bool noenergy = false;  // kinetic factors off (PLAN_NO_ENERGY or plan_set_energy)
   size_t slots;
   cudaStream_t stream;
   Layout L;
@@ -543,6 +651,11 @@ struct plan_s {
   Dev dev(int kk) const {
     Dev P{};
     P.p = p; P.eta = eta; P.nw = nw; P.nt = nt; P.ntp = ntp;
+    P.nv = nv;
+    P.vmin_mask = vmin_mask;
+    P.noenergy = noenergy ? 1 : 0;
+    P.vlim = at<float>(L.vlim);
+    P.wnode = at<uint8_t>(L.wnode);
     P.rho = rho_at(kk);
     P.alpha = cfg.alpha;
     // keeping u on inactive edges (or standard ADMM, which updates every u)
@@ -604,7 +717,7 @@ plan_status ensure_prox_grid(plan_t h) {
 plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   Dev P = h->dev(h->k);
   const unsigned grid = (unsigned)((size_t)h->eta * h->ntp);
-  const int seg_threads = 32 * std::min(1 + h->nw, WARPS);
+  const int seg_threads = 32 * std::min(1 + h->nw + h->nv, WARPS);
   const bool prof = h->profiling && h->side;
   if (h->side) {
     // kinetic and wall factors run beside the collision passes
@@ -717,6 +830,17 @@ plan_status upload_inputs(plan_t h, const float* start, const float* goal, const
   return PLAN_OK;
 }
 
+// Back-weight classes after an import (feasibility problem only).
+plan_status derive_wnode(plan_t h) {
+  if (!h->noenergy) return PLAN_OK;
+  Dev P = h->dev(h->k);
+  const int nodes = h->p * (h->eta + 1);
+  wnode_clear_kernel<<<(nodes + 255) / 256, 256, 0, h->stream>>>(P, h->k == 0 ? 1 : 0);
+  if (h->k > 0) wnode_from_bits_kernel<<<304, 256, 0, h->stream>>>(P);
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -739,11 +863,13 @@ plan_status plan_reset(plan_t h) {
   const size_t zbytes = (size_t)h->p * (h->eta + 1) * 8;
   (void)zbytes;
   CK(cudaMemsetAsync(h->at<void>(h->L.bits), 0, (size_t)h->eta * h->ntp * TILE * 4, h->stream));
-  if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.wbits), 0, (size_t)h->nw * h->eta * h->nt * 4, h->stream));
+  const size_t ng = (size_t)h->nw + h->nv;
+  if (ng) CK(cudaMemsetAsync(h->at<void>(h->L.wbits), 0, ng * h->eta * h->nt * 4, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.wnode), 1, (size_t)h->p * (h->eta + 1), h->stream));
   if (h->cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM)) {
     CK(cudaMemsetAsync(h->at<void>(h->L.ulo), 0, h->slots * 16, h->stream));
     CK(cudaMemsetAsync(h->at<void>(h->L.uhi), 0, h->slots * 16, h->stream));
-    if (h->nw) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, (size_t)h->nw * h->eta * h->p * 16, h->stream));
+    if (ng) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, ng * h->eta * h->p * 16, h->stream));
   }
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
@@ -777,8 +903,10 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
     return fail(PLAN_EINVAL, "warm_rho must be positive when warm_iters > 0");
   if (cfg->max_iter < 0) return fail(PLAN_EINVAL, "max_iter must be >= 0");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
-                         PLAN_DENSE_STATE | PLAN_ADMM;
+                         PLAN_DENSE_STATE | PLAN_ADMM | PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
+  if ((cfg->flags & PLAN_ADMM) && (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN)))
+    return fail(PLAN_EUNSUPPORTED, "standard-ADMM mode runs with the kinetic factors only");
   const size_t p = cfg->p, eta = cfg->eta;
   const size_t ncost = (cfg->flags & PLAN_COST_PER_SEGMENT) ? p * eta : p;
   if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p) || !finite_all(radius, p) ||
@@ -796,6 +924,9 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
   h->cfg = *cfg;
   if (h->cfg.check_every < 1) h->cfg.check_every = 1;
   h->p = cfg->p; h->eta = cfg->eta; h->nw = cfg->n_walls;
+  h->nv = ((cfg->flags & PLAN_VMAX) ? 1 : 0) + ((cfg->flags & PLAN_VMIN) ? 1 : 0);
+  h->vmin_mask = (cfg->flags & PLAN_VMIN) ? (1u << (h->nv - 1)) : 0u;
+  h->noenergy = (cfg->flags & PLAN_NO_ENERGY) != 0;
   h->nt = (h->p + TILE - 1) / TILE;
   h->ntp = h->nt * (h->nt + 1) / 2;
   h->slots = (size_t)h->eta * h->ntp * TILE * TILE;
@@ -842,6 +973,13 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
     }
   }
   st = upload_inputs(h, start, goal, radius, cost_w, walls);
+  // velocity limits start unbinding: maxima +inf, minima 0 (plan_set_velocity_limits)
+  for (int v = 0; v < h->nv && st == PLAN_OK; ++v) {
+    const size_t n = (size_t)h->p * h->eta;
+    fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        h->at<float>(h->L.vlim) + v * n, n, ((h->vmin_mask >> v) & 1u) ? 0.f : INFINITY);
+    if (cudaGetLastError() != cudaSuccess) st = fail(PLAN_ECUDA, "fill_kernel launch failed");
+  }
   if (st == PLAN_OK) st = plan_reset(h);
   if (st != PLAN_OK) {
     plan_destroy(h);
@@ -976,10 +1114,15 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   if (h->p > 1) import_coll_kernel<<<(unsigned)((h->slots + 255) / 256), 256, 0, h->stream>>>(P, u_coll);
   const int nseg = std::max(h->eta * h->p, h->nw * h->eta * h->p);
   import_seg_kernel<<<(nseg + 255) / 256, 256, 0, h->stream>>>(P, u_kin, u_wall);
-  if (h->nw) {
-    const int words = h->nw * h->eta * h->nt;
+  // velocity factors start from u = 0 (plan_import_velocity_state sets them)
+  for (int v = 0; v < h->nv; ++v)
+    import_vel_kernel<<<(h->eta * h->p + 255) / 256, 256, 0, h->stream>>>(P, v, nullptr);
+  if (h->nw + h->nv) {
+    const int words = (h->nw + h->nv) * h->eta * h->nt;
     import_wbits_kernel<<<(words * 32 + 255) / 256, 256, 0, h->stream>>>(P);
   }
+  plan_status wst = derive_wnode(h);
+  if (wst != PLAN_OK) return wst;
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
   CK(clear_sums(h));
@@ -1204,12 +1347,108 @@ plan_status adj_supported(plan_t h) {
   if (h->cfg.flags & (PLAN_ADMM | PLAN_U_KEEP))
     return fail(PLAN_EUNSUPPORTED, "the adjoint covers TWA with the reset rule only");
   if (h->cfg.warm_iters > 0) return fail(PLAN_EUNSUPPORTED, "the adjoint needs a constant rho0");
+  if (h->noenergy || h->nv)
+    return fail(PLAN_EUNSUPPORTED, "the adjoint covers the kinetic, collision factors only");
   return PLAN_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+plan_status plan_set_velocity_limits(plan_t h, const float* vmax, const float* vmin) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  const bool has_max = (h->cfg.flags & PLAN_VMAX) != 0, has_min = (h->cfg.flags & PLAN_VMIN) != 0;
+  if ((vmax && !has_max) || (vmin && !has_min))
+    return fail(PLAN_EINVAL, "velocity limits need PLAN_VMAX / PLAN_VMIN at plan_create");
+  const size_t n = (size_t)h->p * h->eta;
+  if (vmax) {
+    for (size_t t = 0; t < n; ++t)
+      if (!(vmax[t] > 0.f)) return fail(PLAN_EINVAL, "vmax[%zu] must be positive (or +inf)", t);
+  }
+  if (vmin) {
+    for (size_t t = 0; t < n; ++t)
+      if (!(vmin[t] >= 0.f) || !std::isfinite(vmin[t])) return fail(PLAN_EINVAL, "vmin[%zu] must be finite and >= 0", t);
+  }
+  h->adj_valid = false;
+  float* lim = h->at<float>(h->L.vlim);
+  if (vmax) CK(cudaMemcpyAsync(lim, vmax, n * 4, cudaMemcpyHostToDevice, h->stream));
+  if (vmin) CK(cudaMemcpyAsync(lim + (has_max ? n : 0), vmin, n * 4, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_export_velocity_state(plan_t h, float* u_vmax, float* u_vmin, uint8_t* act_vmax,
+                                       uint8_t* act_vmin) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  const bool has_max = (h->cfg.flags & PLAN_VMAX) != 0, has_min = (h->cfg.flags & PLAN_VMIN) != 0;
+  if (((u_vmax || act_vmax) && !has_max) || ((u_vmin || act_vmin) && !has_min))
+    return fail(PLAN_EINVAL, "the plan has no such velocity factors");
+  Dev P = h->dev(h->k);
+  const unsigned grid = (unsigned)((h->eta * h->p + 255) / 256);
+  if (has_max && (u_vmax || act_vmax)) export_vel_kernel<<<grid, 256, 0, h->stream>>>(P, 0, u_vmax, act_vmax);
+  if (has_min && (u_vmin || act_vmin))
+    export_vel_kernel<<<grid, 256, 0, h->stream>>>(P, has_max ? 1 : 0, u_vmin, act_vmin);
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+plan_status plan_import_velocity_state(plan_t h, const float* u_vmax, const float* u_vmin) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  const bool has_max = (h->cfg.flags & PLAN_VMAX) != 0, has_min = (h->cfg.flags & PLAN_VMIN) != 0;
+  if ((u_vmax && !has_max) || (u_vmin && !has_min))
+    return fail(PLAN_EINVAL, "the plan has no such velocity factors");
+  h->adj_valid = false;
+  Dev P = h->dev(h->k);
+  const unsigned grid = (unsigned)((h->eta * h->p + 255) / 256);
+  if (has_max) import_vel_kernel<<<grid, 256, 0, h->stream>>>(P, 0, u_vmax);
+  if (has_min) import_vel_kernel<<<grid, 256, 0, h->stream>>>(P, has_max ? 1 : 0, u_vmin);
+  const int words = (h->nw + h->nv) * h->eta * h->nt;
+  if (words) import_wbits_kernel<<<(words * 32 + 255) / 256, 256, 0, h->stream>>>(P);
+  CK(cudaGetLastError());
+  return derive_wnode(h);
+}
+
+plan_status plan_export_back_weights(plan_t h, uint8_t* classes) {
+  if (!h || !classes) return fail(PLAN_EINVAL, "null argument");
+  Dev P = h->dev(h->k);
+  const int nodes = h->p * (h->eta + 1);
+  back_weights_kernel<<<(nodes + 255) / 256, 256, 0, h->stream>>>(P, classes, nullptr);
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+plan_status plan_import_back_weights(plan_t h, const uint8_t* classes) {
+  if (!h || !classes) return fail(PLAN_EINVAL, "null argument");
+  if (!h->noenergy) return fail(PLAN_EINVAL, "back weights are rho0 inside while the kinetic factors run");
+  Dev P = h->dev(h->k);
+  const int nodes = h->p * (h->eta + 1);
+  back_weights_kernel<<<(nodes + 255) / 256, 256, 0, h->stream>>>(P, nullptr, classes);
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
+
+plan_status plan_set_energy(plan_t h, int on) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  if (h->cfg.flags & PLAN_ADMM) return fail(PLAN_EUNSUPPORTED, "standard-ADMM mode keeps the kinetic factors");
+  const bool off = (on == 0);
+  if (off == h->noenergy) return PLAN_OK;
+  h->adj_valid = false;
+  // the captured iterations hold the old mode
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec[q]) { cudaGraphExecDestroy(h->gexec[q]); h->gexec[q] = nullptr; }
+  h->noenergy = off;
+  Dev P = h->dev(h->k);
+  if (off) {
+    // every node had the kinetic factors' rho0 so far
+    const int nodes = h->p * (h->eta + 1);
+    wnode_clear_kernel<<<(nodes + 255) / 256, 256, 0, h->stream>>>(P, 1);
+  } else {
+    kinetic_restart_kernel<<<(h->eta * h->p + 255) / 256, 256, 0, h->stream>>>(P);
+  }
+  CK(cudaGetLastError());
+  return PLAN_OK;
+}
 
 plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
@@ -1416,6 +1655,8 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
   if (cfg->n_walls > 0 && (!walls || !u_wall_in || !u_wall_out)) return fail(PLAN_EINVAL, "null wall array");
   if (!(cfg->rho0 > 0.f) || !(cfg->alpha > 0.f)) return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
+  if (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN))
+    return fail(PLAN_EUNSUPPORTED, "plan_iterate_static runs the energy problem without velocity factors");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
                          PLAN_DENSE_STATE | PLAN_ADMM;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
@@ -1725,6 +1966,9 @@ plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const
     return fail(PLAN_EINVAL, "null argument or n < 1");
   *out = nullptr;
   const unsigned modes = PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM;
+  for (int b = 0; b < n; ++b)
+    if (cfgs[b].flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN))
+      return fail(PLAN_EUNSUPPORTED, "batch members run the energy problem without velocity factors");
   for (int b = 1; b < n; ++b)
     if ((cfgs[b].flags & modes) != (cfgs[0].flags & modes))
       return fail(PLAN_EINVAL, "batch members must share the state-mode flags");

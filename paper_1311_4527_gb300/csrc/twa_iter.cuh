@@ -47,11 +47,17 @@ struct Dev {
   int p, eta, nw, nt, ntp;
   float rho, alpha;
   int dense, keep, admm;
+  int nv;                // velocity-factor kinds after the walls (0..2)
+  unsigned vmin_mask;    // bit v: velocity kind v is a minimum (else maximum)
+  int noenergy;          // no kinetic factors (the feasibility problem)
+  const float* vlim;     // [nv][p][eta] velocity limits
+  uint8_t* wnode;        // [p][eta+1] back-weight class when noenergy: 0 or 1
   const float2* z;       // z^k, [p][eta+1]
   float2* z_next;        // z^{k+1}; until the consensus pass writes it, z^{k-1}
   const float* radius;   // [p]
   const float* cost;     // [p][eta], kinetic coefficients c_{i,s}
   const float4* walls;   // [nw] (xL.x, xL.y, xR.x, xR.y)
+  // uwall / xwall / wbits hold nw wall kinds followed by nv velocity kinds
   const int2* tiles;     // [ntp] (I, J), I <= J
   float4 *ulo, *uhi, *xlo, *xhi;
   uint32_t* bits;        // [eta * ntp * 32]
@@ -154,6 +160,34 @@ __device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 nj
   }
 }
 
+// The collision minimizer with per-agent weight classes at each end (the
+// feasibility problem; Appendix C's reduction with weights rho rho' / (rho +
+// rho')): both agents at rho0 give relative weight rho0 / 2, a zero class on
+// either gives relative weight 0 and the relative change goes to the
+// zero-weight agent (split evenly when both are zero), a fixed end stays.
+__device__ __forceinline__ void pair_end(float2 ni, float2 nj, int ci, int cj, float2 v, float2& xi,
+                                         float2& xj) {
+  if (ci == 2) { xi = ni; xj = nj; return; }
+  if (ci == 0 && cj == 1) { xj = nj; xi = nj - v; return; }
+  if (ci == 1 && cj == 0) { xi = ni; xj = ni + v; return; }
+  const float2 sm = ni + nj;
+  xi = 0.5f * (sm - v);
+  xj = 0.5f * (sm + v);
+}
+
+__device__ __forceinline__ void coll_minimizer_classes(float2 nil, float2 nih, float2 njl,
+                                                       float2 njh, int cil, int cih, int cjl,
+                                                       int cjh, float R, float rho, float2& xil,
+                                                       float2& xih, float2& xjl, float2& xjh) {
+  const float2 cl = njl - nil, ch = njh - nih;
+  const int rl = (cil == 2) ? 2 : ((cil == 1 && cjl == 1) ? 1 : 0);
+  const int rh = (cih == 2) ? 2 : ((cih == 1 && cjh == 1) ? 1 : 0);
+  float2 vl, vh;
+  disk_prox_classes(cl, ch, rl, rh, R, 0.5f * rho, vl, vh);
+  pair_end(nil, njl, cil, cjl, vl, xil, xjl);
+  pair_end(nih, njh, cih, cjh, vh, xih, xjh);
+}
+
 // Kinetic factor (i, s): always active (it always sends rho0).  Finishes its
 // pending dual update, runs the closed-form minimizer and stores x and u.
 __device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float2 zl, float2 zh,
@@ -170,7 +204,20 @@ __device__ __forceinline__ void kinetic_factor(const Dev& P, int i, int s, float
   if (!pin_hi) contribute(P, i, s + 1, xh + uh);
 }
 
-// Wall factor (w, i, s).  Called by a full warp (lane = agent of tile I).
+// Back-weight classes of agent i's break-points s and s + 1: 2 at a fixed
+// end, else rho0 (1) unless the feasibility problem left a node with only
+// zero incoming weights (0).
+__device__ __forceinline__ void end_classes(const Dev& P, int i, int s, bool pin_lo, bool pin_hi,
+                                            int& cl, int& ch) {
+  const size_t b = (size_t)i * (P.eta + 1) + s;
+  cl = pin_lo ? 2 : (P.noenergy ? (int)P.wnode[b] : 1);
+  ch = pin_hi ? 2 : (P.noenergy ? (int)P.wnode[b + 1] : 1);
+}
+
+// Gated segment factor w of (i, s): a wall (w < nw, Eq. wall_minimizer) or a
+// maximum / minimum velocity factor (w >= nw, Eq. max_vel_min).  Forward
+// weight rho0 when the n's violate it, else 0.  Called by a full warp (lane =
+// agent of tile I).
 __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
                                             float2 zl, float2 zh, float r, bool pin_lo,
                                             bool pin_hi, float& res) {
@@ -192,21 +239,33 @@ __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi,
     uh = finish_u(bprev, pin_hi, P.keep, hi2(u4), hi2(x4), zh, P.alpha, res);
   }
   const float2 nl = zl - ul, nh = zh - uh;
-  const float4 W = P.walls[w];
-  const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
-  const bool act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
+  const bool vel = w >= P.nw;
+  bool act;
+  float2 c0 = mk(0.f, 0.f), c1 = c0;
+  float C = 0.f;
+  bool vmin = false;
+  if (vel) {
+    const int v = w - P.nw;
+    vmin = (P.vmin_mask >> v) & 1u;
+    if (vi) C = P.vlim[((size_t)v * P.p + i) * P.eta + s];
+    const float2 d = nl - nh;
+    const float d2 = dot(d, d);
+    act = vi && (vmin ? d2 < C * C : d2 > C * C);
+  } else {
+    const float4 W = P.walls[w];
+    c0 = mk(W.x, W.y); c1 = mk(W.z, W.w);
+    act = vi && dist2_segment_segment(nl, nh, c0, c1) < r * r;
+  }
   const uint32_t nw = __ballot_sync(FULL, act);
   if (lane == 0 && nw != word) P.wbits[widx] = nw;
   if (act) {
     float2 xl = nl, xh = nh;
-    if (pin_lo && pin_hi) {
-    } else if (pin_lo) {
-      if (!capsule_prox_pinned(nl, nh, c0, c1, r, xh)) atomicOr(P.status, 1u);
-    } else if (pin_hi) {
-      if (!capsule_prox_pinned(nh, nl, c0, c1, r, xl)) atomicOr(P.status, 1u);
-    } else {
-      const float wgt = 0.5f * P.rho;
-      capsule_prox_free(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
+    int cl, ch;
+    end_classes(P, i, s, pin_lo, pin_hi, cl, ch);
+    if (vel) {
+      velocity_prox(nl, nh, cl, ch, C, xl, xh);
+    } else if (!capsule_prox_classes(nl, nh, cl, ch, c0, c1, r, 0.5f * P.rho, xl, xh)) {
+      atomicOr(P.status, 1u);
     }
     P.xwall[idx] = pack(xl, xh);
     P.uwall[idx] = pack(ul, uh);
@@ -382,9 +441,9 @@ __device__ __forceinline__ void segment_block(const Dev& P, int blk) {
   float r = 0.f;
   if (vi) { zl = P.z[(size_t)i * E1 + s]; zh = P.z[(size_t)i * E1 + s + 1]; r = P.radius[i]; }
   float res = 0.f;
-  for (int f = warp; f < 1 + P.nw; f += blockDim.x >> 5) {
+  for (int f = warp; f < 1 + P.nw + P.nv; f += blockDim.x >> 5) {
     if (f == 0) {
-      if (vi) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
+      if (vi && !P.noenergy) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
     } else {
       wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
     }
@@ -407,8 +466,16 @@ __device__ __forceinline__ void prox_item(const Dev& P, uint32_t fid) {
   const float2 njl = P.z[(size_t)j * E1 + s] - hi2(a), njh = P.z[(size_t)j * E1 + s + 1] - hi2(b);
   float2 xil, xih, xjl, xjh;
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-  coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, P.radius[i] + P.radius[j], P.rho,
-                 xil, xih, xjl, xjh);
+  if (P.noenergy) {
+    int cil, cih, cjl, cjh;
+    end_classes(P, i, s, pin_lo, pin_hi, cil, cih);
+    end_classes(P, j, s, pin_lo, pin_hi, cjl, cjh);
+    coll_minimizer_classes(nil, nih, njl, njh, cil, cih, cjl, cjh, P.radius[i] + P.radius[j],
+                           P.rho, xil, xih, xjl, xjh);
+  } else {
+    coll_minimizer(nil, nih, njl, njh, pin_lo, pin_hi, P.radius[i] + P.radius[j], P.rho,
+                   xil, xih, xjl, xjh);
+  }
   P.xlo[fid] = pack(xil, xjl);
   P.xhi[fid] = pack(xih, xjh);
   if (!pin_lo) {
@@ -448,6 +515,8 @@ __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, b
     const double den = (double)P.fix[0] * (double)cnt;
     zn = mk((float)((double)sx / den), (float)((double)sy / den));
   }
+  // step 6: the back weight is rho0 where some factor sent rho0, else 0
+  if (P.noenergy) P.wnode[node] = cnt > 0u ? 1 : 0;
   P.z_next[node] = zn;
   bad = (*P.status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
   dz = bad ? 0.f : maxabs2(zn - zo);

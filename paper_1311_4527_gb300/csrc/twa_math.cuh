@@ -470,4 +470,92 @@ TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, 
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Zero incoming weights (the feasibility problem, no kinetic factors)
+// ---------------------------------------------------------------------------
+// Weight classes of one end: 0 (zero), 1 (rho0), 2 (infinite: fixed end).
+// One end's weight -> 0+ with the other finite has a lexicographic limit:
+// the weighted end moves out of the region by the least amount (a segment
+// shrunk to that point is feasible), then the zero-weight end solves the
+// fixed-end problem against it.  Both zero are equal weights.
+
+// Closest point to q outside the open disk of radius R at the origin.
+TWA_DEV float2 disk_project_out(float2 q, float R) {
+  const float L = hypotf(q.x, q.y);
+  if (L >= R) return q;
+  if (L > 0.f) return (R / L) * q;
+  return mk(R, 0.f);
+}
+
+// Closest point to q outside the open capsule of radius r around [c0, c1]; a
+// point on the axis leaves along the normal of smallest angle.
+TWA_DEV float2 capsule_project_out(float2 q, float2 c0, float2 c1, float r) {
+  const float2 e = c1 - c0;
+  const float ee = dot(e, e);
+  float t = ee > 0.f ? dot(q - c0, e) / ee : 0.f;
+  t = fminf(1.f, fmaxf(0.f, t));
+  const float2 c = c0 + t * e;
+  const float2 d = q - c;
+  const float L = hypotf(d.x, d.y);
+  if (L >= r) return q;
+  if (L > 0.f) return c + (r / L) * d;
+  if (!(ee > 0.f)) return c + mk(r, 0.f);
+  const float2 n1 = normalized(perp(e));
+  return c + r * ((angle_of(n1) < angle_of(-n1)) ? n1 : -n1);
+}
+
+// Disk minimizer for weight classes (cl, ch) of the two ends of the relative
+// segment (equal finite weights where both are 1).
+TWA_DEV void disk_prox_classes(float2 a, float2 b, int cl, int ch, float R, float w, float2& vl,
+                               float2& vh) {
+  vl = a; vh = b;
+  if (cl == 2 && ch == 2) return;
+  if (cl == 2) { vh = disk_prox_pinned(a, b, R); return; }
+  if (ch == 2) { vl = disk_prox_pinned(b, a, R); return; }
+  if (cl == 0 && ch == 1) { vh = disk_project_out(b, R); vl = disk_prox_pinned(vh, a, R); return; }
+  if (cl == 1 && ch == 0) { vl = disk_project_out(a, R); vh = disk_prox_pinned(vl, b, R); return; }
+  disk_prox_free(a, b, w, w, R, vl, vh);
+}
+
+// Capsule minimizer for weight classes; false if a fixed end lies inside.
+TWA_DEV bool capsule_prox_classes(float2 a, float2 b, int cl, int ch, float2 c0, float2 c1, float r,
+                                  float w, float2& vl, float2& vh) {
+  vl = a; vh = b;
+  if (cl == 2 && ch == 2) return true;
+  if (cl == 2) return capsule_prox_pinned(a, b, c0, c1, r, vh);
+  if (ch == 2) return capsule_prox_pinned(b, a, c0, c1, r, vl);
+  if (cl == 0 && ch == 1) {
+    vh = capsule_project_out(b, c0, c1, r);
+    return capsule_prox_pinned(vh, a, c0, c1, r, vl);
+  }
+  if (cl == 1 && ch == 0) {
+    vl = capsule_project_out(a, c0, c1, r);
+    return capsule_prox_pinned(vl, b, c0, c1, r, vh);
+  }
+  capsule_prox_free(a, b, w, w, c0, c1, r, vl, vh);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Maximum / minimum velocity minimizers (Appendices F and G)
+// ---------------------------------------------------------------------------
+// |x_lo - x_hi| <= C (is_max) or >= C, from messages that violate it.  With
+// equal finite weights the appendix's closed form keeps the midpoint and
+// scales x_lo - x_hi to length C along n_lo - n_hi; an infinite weight (or a
+// zero weight against a finite one) keeps the other end; both zero are equal
+// weights.  Coincident ends (minimum velocity) separate along (1, 0).
+TWA_DEV void velocity_prox(float2 n_lo, float2 n_hi, int cl, int ch, float C, float2& x_lo,
+                           float2& x_hi) {
+  x_lo = n_lo; x_hi = n_hi;
+  if (cl == 2 && ch == 2) return;
+  const float2 d = n_lo - n_hi;
+  const float L = hypotf(d.x, d.y);
+  const float2 u = L > 0.f ? (1.f / L) * d : mk(-1.f, 0.f);
+  if (cl == 2 || (ch == 0 && cl != 0)) { x_hi = n_lo - C * u; return; }
+  if (ch == 2 || (cl == 0 && ch != 0)) { x_lo = n_hi + C * u; return; }
+  const float2 m = 0.5f * (n_lo + n_hi);
+  x_lo = m + (0.5f * C) * u;
+  x_hi = m - (0.5f * C) * u;
+}
+
 }  // namespace twa

@@ -44,16 +44,27 @@ def make_planner(prob, flags=0, **kw):
         flags |= pk.PLAN_ADMM
     return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=cost,
                       walls=prob.walls if prob.n_walls else None, rho0=prob.rho0,
-                      alpha=prob.alpha, flags=flags, **kw)
+                      alpha=prob.alpha, flags=flags, energy=prob.energy, vmax=prob.vmax,
+                      vmin=prob.vmin, **kw)
 
 
 def gpu_step(prob, st, flags=0, planner=None):
     """Import oracle state st, run one GPU iteration, export as numpy."""
     pl = planner or make_planner(prob, flags)
     pl.import_state(st.z, st.u_coll, st.u_kin, st.u_wall if prob.n_walls else None, st.k)
+    if st.u_vel:
+        pl.import_velocity_state(st.u_vel.get("max"), st.u_vel.get("min"))
+    if not prob.energy:
+        # a factor alone at a node leaves u = 0 there, so the classes cannot
+        # be read back from u: import the oracle's
+        pl.import_back_weights(st.wback)
     pl.iterate(1)
     ex = pl.export_state()
     out = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ex.items()}
+    if st.u_vel:
+        out["vel"] = {k: (u.cpu().numpy(), a.cpu().numpy().astype(bool))
+                      for k, (u, a) in pl.export_velocity_state().items()}
+    out["wback"] = pl.export_back_weights().cpu().numpy()
     if planner is None:
         pl.close()
     return out
@@ -101,7 +112,22 @@ def compare(prob, new, info, gpu, tol=TOL):
                 idx = np.nonzero(wex[w, s])[0]
                 bad_node[idx, s] = True
                 bad_node[idx, s + 1] = True
+    vex = {}
+    for kind, act_v in info.extra.get("active_vel", {}).items():
+        vm = info.extra["vel_margin"][kind]
+        vg = gpu["vel"][kind][1]
+        vdiff = act_v != vg
+        vbad = vdiff & ~(np.abs(vm) < MARGIN)
+        assert not vbad.any(), f"{int(vbad.sum())} {kind}-velocity factors disagree away from the limit"
+        vex[kind] = vdiff | (np.abs(vm) < MARGIN)
+        stats[f"v{kind}_active"] = int(act_v.sum())
+        for s_, i_ in zip(*np.nonzero(vex[kind])):
+            bad_node[i_, s_] = True
+            bad_node[i_, s_ + 1] = True
     stats["nodes_excluded"] = int(bad_node.sum())
+    # back weights of the new iterate (step 6), away from excluded factors
+    wdiff = (gpu["wback"] != new.wback) & ~bad_node
+    assert not wdiff.any(), f"{int(wdiff.sum())} break-points differ in back weight"
     # --- values --------------------------------------------------------------
     dz = np.abs(gpu["z"] - new.z)
     worst = float(np.max(dz[~bad_node])) if (~bad_node).any() else 0.0
@@ -117,6 +143,12 @@ def compare(prob, new, info, gpu, tol=TOL):
     stats["coll_compared_active"] = int((ok & act_o).sum())
     assert worst <= tol * L, f"u_coll error {worst} > {tol * L}"
     kin_ok = ~seg_bad.T                                     # (eta, p)
+    for kind, ex_v in vex.items():
+        okv = ~ex_v & kin_ok
+        dv = np.abs(gpu["vel"][kind][0] - new.u_vel[kind])
+        worst = float(np.max(dv[okv])) if okv.any() else 0.0
+        stats[f"u_v{kind}_maxerr"] = worst / L
+        assert worst <= tol * L, f"u_v{kind} error {worst} > {tol * L}"
     dk = np.abs(gpu["u_kin"] - new.u_kin)
     worst = float(np.max(dk[kin_ok])) if kin_ok.any() else 0.0
     stats["u_kin_maxerr"] = worst / L
