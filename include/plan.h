@@ -65,6 +65,11 @@ typedef enum {
 #define PLAN_VMIN              (1u << 7) /* a minimum-velocity factor per agent segment,
                                             |x(s+1) - x(s)| >= vmin (the reversed Eq.
                                             max_vel_min, App. G) */
+#define PLAN_VO                (1u << 8) /* one velocity-obstacle epoch (Section 5, App. H):
+                                            eta = 2, start = x(0), goal = x_ref; collision,
+                                            wall and velocity factors on segment 0 only, the
+                                            kinetic factor C'_i |x - x_ref|^2 (cost_w,
+                                            unnormalised) on segment 1 only */
 
 typedef struct {
   int p;              /* agents, >= 1 */
@@ -252,6 +257,19 @@ plan_status plan_export_velocity_state(plan_t plan, float* u_vmax, float* u_vmin
                                        uint8_t* act_vmax, uint8_t* act_vmin);
 plan_status plan_import_velocity_state(plan_t plan, const float* u_vmax, const float* u_vmin);
 plan_status plan_set_energy(plan_t plan, int on);
+/* Copy the current fixed positions (start, goal; host, p x 2 each, either may
+ * be NULL).  Synchronises. */
+plan_status plan_get_endpoints(plan_t plan, float* start, float* goal);
+/* One epoch of the velocity-obstacle local planner (Section 5) on a PLAN_VO
+ * plan: set x_ref = x(0) + (dest - x(0)) clipped to length step (the
+ * preferred velocity times the horizon), reset to the initial state, solve
+ * (cfg.tol / max_iter / check_every), then move x(0) a fraction advance in
+ * (0, 1] of the way to the planned x.  dest: DEVICE p x 2.  iters / residual
+ * (may be NULL): the solve's iterations and last residual; max_dist: the
+ * largest remaining distance to dest.  Returns PLAN_ENOTCONV when the solve
+ * hit max_iter (x(0) still advances), else as plan_solve.  Synchronises. */
+plan_status plan_vo_epoch(plan_t plan, const float* dest, float step, float advance, int* iters,
+                          float* residual, float* max_dist);
 /* Back-weight class of every break-point (App. B step 6), DEVICE p x (eta+1)
  * bytes: 0 zero, 1 rho0, 2 infinite (the fixed ends).  Export works in every
  * mode; import (feasibility problem only; fixed ends ignored) replaces the

@@ -19,6 +19,16 @@ and goal; each carries a position factor that always sends weight infinity
 Eq. basic_opt_prob (Section 4 compares it with the energy problem), where
 break-points can receive only zero weights.
 
+``vo=True`` is the local planner of Section 5 (Eq. unconst_opt_RVO through
+the minimizers of Appendix H) on eta = 2 break-point segments: s = 0 holds the
+current positions x_i(0) (fixed), s = 1 the positions x_i after one epoch
+(free), s = 2 the reference positions x_ref_i (fixed, in ``goal``).  The
+collision, wall and velocity factors exist on segment 0 only (Eqs.
+minimizer_rvo_coll and minimizer_rvo_wall: g^coll and g^wall with the x(0)
+end fixed), the kinetic factor on segment 1 only, where it is
+C'_i |x_i - x_ref_i|^2 (Eq. minimizer_rvo_cost: g^cost with the x_ref end
+fixed); C'_i comes from ``cost[:, 1]`` (with ``cost_unnorm``).
+
 One iteration is the seven steps of Appendix B, in order.  Readings where the
 text is silent or its figure is missing (the special u and back-weight rules of
 Fig. special_update_rules):
@@ -70,6 +80,7 @@ class Problem:
     energy: bool = True         # kinetic-energy factors present
     vmax: np.ndarray | None = None   # (p, eta) limits of |x(s+1) - x(s)|, or None
     vmin: np.ndarray | None = None
+    vo: bool = False            # one-epoch velocity-obstacle problem (Section 5), eta = 2
     warm_iters: int = 0
     warm_rho: float = 0.0
 
@@ -160,6 +171,9 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     p, eta = prob.p, prob.eta
     assert not (prob.admm and (not prob.energy or prob.vmax is not None or prob.vmin is not None)), \
         "standard-ADMM mode is defined here with the kinetic factors only"
+    assert not prob.vo or eta == 2, "the velocity-obstacle problem has eta = 2"
+    kin_segs = [s for s in range(eta) if prob.energy and not (prob.vo and s == 0)]
+    con_segs = {0} if prob.vo else set(range(eta))   # collision, wall, velocity factors
     rho0 = prob.rho_at(st.k)
     z = st.z
     wb = st.wback
@@ -177,7 +191,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     # --- kinetic factors: steps 1-4 -------------------------------------
     x_kin = np.empty_like(st.u_kin)
     n_kin = np.empty_like(st.u_kin)
-    for s in range(eta if prob.energy else 0):
+    for s in kin_segs:
         n_kin[s, :, 0] = z[:, s] - st.u_kin[s, :, 0]
         n_kin[s, :, 1] = z[:, s + 1] - st.u_kin[s, :, 1]
         for i in range(p):
@@ -185,7 +199,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
                 n_kin[s, i, 0], n_kin[s, i, 1], _wnum(wb[i, s], rho0),
                 _wnum(wb[i, s + 1], rho0), cc[i, s])
     m_kin = x_kin + st.u_kin
-    for s in range(eta if prob.energy else 0):
+    for s in kin_segs:
         for e, ss in ((0, s), (1, s + 1)):
             num[:, ss] += rho0 * m_kin[s, :, e]
             den[:, ss] += rho0
@@ -200,6 +214,11 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         coll_margin = np.empty((eta, iu.shape[0]))
         coll_gap = np.full((eta, iu.shape[0]), INF)
     for s in range(eta):
+        if s not in con_segs:
+            coll_x.append((np.zeros(0, dtype=np.int64), np.zeros((0, 4, 2))))
+            if record_branches:
+                coll_margin[s] = INF
+            continue
         u = st.u_coll[s]
         n = np.stack([z[iu, s], z[iu, s + 1], z[ju, s], z[ju, s + 1]], axis=1) - u
         c_lo = n[:, 2] - n[:, 0]
@@ -252,6 +271,10 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         xL = prob.walls[w, :2]
         xR = prob.walls[w, 2:]
         for s in range(eta):
+            if s not in con_segs:
+                if record_branches:
+                    wall_margin[w, s] = INF
+                continue
             u = st.u_wall[w, s]
             n_lo = z[:, s] - u[:, 0]
             n_hi = z[:, s + 1] - u[:, 1]
@@ -287,7 +310,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         u = st.u_vel[kind]
         act = np.zeros((eta, p), dtype=bool)
         vel_margin[kind] = np.full((eta, p), INF)
-        for s in range(eta):
+        for s in sorted(con_segs):
             for i in range(p):
                 n_lo = z[i, s] - u[s, i, 0]
                 n_hi = z[i, s + 1] - u[s, i, 1]
@@ -340,7 +363,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
         return np.where(ok[..., None], step, reset)
 
     # kinetic: forward weight always rho0
-    for s in range(eta if prob.energy else 0):
+    for s in kin_segs:
         allp = np.arange(p)
         for e, ss in ((0, s), (1, s + 1)):
             new.u_kin[s, :, e] = upd(st.u_kin[s, :, e], x_kin[s, :, e], allp, np.full(p, ss),

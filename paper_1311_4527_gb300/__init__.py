@@ -22,7 +22,7 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["Planner", "PlannerBatch", "PlanError", "load_library", "unrolled_trajectory",
            "PLAN_U_KEEP", "PLAN_COST_UNNORM", "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE",
-           "PLAN_ADMM", "PLAN_NO_ENERGY", "PLAN_VMAX", "PLAN_VMIN", "EXPORTED_SYMBOLS"]
+           "PLAN_ADMM", "PLAN_NO_ENERGY", "PLAN_VMAX", "PLAN_VMIN", "PLAN_VO", "EXPORTED_SYMBOLS"]
 
 PLAN_U_KEEP = 1 << 0
 PLAN_COST_UNNORM = 1 << 1
@@ -32,6 +32,7 @@ PLAN_ADMM = 1 << 4
 PLAN_NO_ENERGY = 1 << 5
 PLAN_VMAX = 1 << 6
 PLAN_VMIN = 1 << 7
+PLAN_VO = 1 << 8
 
 STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: "PLAN_ENOTCONV",
           5: "PLAN_ENUMERIC", 6: "PLAN_EINFEASIBLE_INPUT", 7: "PLAN_EUNSUPPORTED"}
@@ -45,7 +46,7 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_batch_set_shape", "plan_batch_destroy", "plan_set_params",
                     "plan_unroll", "plan_set_velocity_limits", "plan_export_velocity_state",
                     "plan_import_velocity_state", "plan_set_energy", "plan_export_back_weights",
-                    "plan_import_back_weights"]
+                    "plan_import_back_weights", "plan_vo_epoch", "plan_get_endpoints"]
 
 
 class PlanError(RuntimeError):
@@ -103,6 +104,8 @@ def load_library(path: str | None = None):
     lib.plan_set_energy.argtypes = [c_void_p, c_int]
     lib.plan_export_back_weights.argtypes = [c_void_p, c_void_p]
     lib.plan_import_back_weights.argtypes = [c_void_p, c_void_p]
+    lib.plan_vo_epoch.argtypes = [c_void_p, c_void_p, c_float, c_float, POINTER(c_int), fp, fp]
+    lib.plan_get_endpoints.argtypes = [c_void_p, fp, fp]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
     pp = POINTER(c_void_p)
@@ -156,7 +159,7 @@ class Planner:
 
     def __init__(self, start, goal, radius, eta, cost_w=None, walls=None, rho0=1.0, alpha=0.1,
                  tol=1e-6, max_iter=20000, flags=0, check_every=50, warm_iters=0, warm_rho=0.0,
-                 T=1.0, device=None, stream=None, energy=True, vmax=None, vmin=None):
+                 T=1.0, device=None, stream=None, energy=True, vmax=None, vmin=None, vo=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Planner needs a CUDA device (there is no CPU fallback)")
@@ -170,6 +173,8 @@ class Planner:
             flags |= PLAN_COST_PER_SEGMENT
         if not energy:
             flags |= PLAN_NO_ENERGY
+        if vo:
+            flags |= PLAN_VO
         if vmax is not None:
             flags |= PLAN_VMAX
         if vmin is not None:
@@ -300,6 +305,46 @@ class Planner:
         ptr = lambda x: c_void_p(x.data_ptr()) if x is not None else None
         _check(_lib.plan_import_velocity_state(self._h, ptr(um), ptr(un)))
         torch.cuda.current_stream(dev).synchronize()
+
+    @classmethod
+    def velocity_obstacle(cls, x0, dest, radius, c_prime, step, walls=None, rho0=10.0, **kw):
+        """A one-epoch velocity-obstacle planner (Section 5): current
+        positions x0, destinations dest, per-agent cost C'_i; step bounds
+        |x_ref - x0|.  Advance it with ``vo_epoch``."""
+        x0 = np.asarray(x0, dtype=np.float64).reshape(-1, 2)
+        dest = np.asarray(dest, dtype=np.float64).reshape(-1, 2)
+        d = dest - x0
+        L = np.linalg.norm(d, axis=1, keepdims=True)
+        x_ref = x0 + np.where(L > step, step / np.maximum(L, 1e-300), 1.0) * d
+        pl = cls(x0, x_ref, radius, 2, cost_w=c_prime, walls=walls, rho0=rho0, vo=True, **kw)
+        import torch
+        pl._dest = torch.as_tensor(np.ascontiguousarray(dest, dtype=np.float32)).to(pl.device)
+        pl._step = float(step)
+        return pl
+
+    def vo_epoch(self, advance: float = 0.5, dest=None, step=None):
+        """One epoch: re-target, solve, advance.  Returns (converged,
+        iterations, residual, largest remaining distance to dest)."""
+        import torch
+        if dest is not None:
+            self._dest = torch.as_tensor(np.ascontiguousarray(dest, dtype=np.float32)).to(self.device)
+        if step is not None:
+            self._step = float(step)
+        it, r, md = c_int(0), c_float(0.0), c_float(0.0)
+        code = _lib.plan_vo_epoch(self._h, c_void_p(self._dest.data_ptr()), c_float(self._step),
+                                  c_float(advance), byref(it), byref(r), byref(md))
+        if code not in (0, 4):
+            _check(code)
+        return code == 0, int(it.value), float(r.value), float(md.value)
+
+    def endpoints(self):
+        """Current (start, goal) as (p, 2) float32 host arrays (for a
+        velocity-obstacle planner: x(0) and x_ref)."""
+        st = np.empty((self.p, 2), dtype=np.float32)
+        gl = np.empty((self.p, 2), dtype=np.float32)
+        _check(_lib.plan_get_endpoints(self._h, st.ctypes.data_as(POINTER(c_float)),
+                                       gl.ctypes.data_as(POINTER(c_float))))
+        return st, gl
 
     def export_back_weights(self):
         """(p, eta+1) uint8 classes: 0 zero, 1 rho0, 2 infinite."""

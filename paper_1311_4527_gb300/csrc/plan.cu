@@ -138,6 +138,7 @@ __global__ void residual_kernel(Dev P) {
   const int nth = gridDim.x * blockDim.x;
   for (int t = gt; t < (P.noenergy ? 0 : P.eta * P.p); t += nth) {
     const int s = t / P.p, i = t - s * P.p;
+    if (P.vo && s == 0) continue;  // no kinetic factor on the epoch's motion
     float4 x = P.xkin[t];
     if (s != 0) res = fmaxf(res, maxabs2(lo2(x) - P.z[(size_t)i * E1 + s]));
     if (s != P.eta - 1) res = fmaxf(res, maxabs2(hi2(x) - P.z[(size_t)i * E1 + s + 1]));
@@ -251,7 +252,7 @@ __global__ void export_seg_kernel(Dev P, float* u_kin, float* u_wall, uint8_t* a
     float4 u4 = P.ukin[t], x4 = P.xkin[t];
     float2 ul = finish_u(true, s == 0, false, lo2(u4), lo2(x4), P.z[(size_t)i * E1 + s], P.alpha, dummy);
     float2 uh = finish_u(true, s == P.eta - 1, false, hi2(u4), hi2(x4), P.z[(size_t)i * E1 + s + 1], P.alpha, dummy);
-    if (P.noenergy) { ul = mk(0.f, 0.f); uh = ul; }  // no kinetic factors
+    if (P.noenergy || (P.vo && s == 0)) { ul = mk(0.f, 0.f); uh = ul; }  // no kinetic factor here
     if (u_kin) {
       float* o = u_kin + (size_t)t * 4;
       o[0] = ul.x; o[1] = ul.y; o[2] = uh.x; o[3] = uh.y;
@@ -420,6 +421,33 @@ __global__ void wnode_from_bits_kernel(Dev P) {
   }
 }
 
+// Velocity-obstacle epochs (Section 5): x_ref = x(0) + (dest - x(0)) clipped
+// to length step; after the solve, x(0) moves a fraction of the way to x.
+__global__ void vo_target_kernel(int p, const float2* start, const float2* dest, float step,
+                                 float2* goal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p) return;
+  const float2 d = dest[i] - start[i];
+  const float L = hypotf(d.x, d.y);
+  const float sc = (L > step) ? step / L : 1.f;
+  goal[i] = start[i] + sc * d;
+}
+
+__global__ void vo_advance_kernel(int p, int eta, const float2* z, const float2* dest, float frac,
+                                  float2* start, unsigned* max_dist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float dist = 0.f;
+  if (i < p) {
+    const float2 x0 = start[i], x1 = z[(size_t)i * (eta + 1) + 1];
+    const float2 xn = x0 + frac * (x1 - x0);
+    start[i] = xn;
+    const float2 d = dest[i] - xn;
+    dist = hypotf(d.x, d.y);
+  }
+  dist = warp_max(dist);
+  if ((threadIdx.x & 31) == 0 && dist > 0.f) atomicMax(max_dist, __float_as_uint(dist));
+}
+
 // Back-weight classes per node, out (export) or in (import): 2 at the fixed
 // ends, else the stored class (rho0 whenever the kinetic factors run).
 __global__ void back_weights_kernel(Dev P, uint8_t* out, const uint8_t* in) {
@@ -556,11 +584,13 @@ double seg_point_dist(double px, double py, double ax, double ay, double bx, dou
 // fixed-end minimizers infeasible).  Pairs are found with a uniform grid of
 // cell size max(r_i + r_j), so the check is linear in p.
 plan_status check_endpoints(int p, const float* start, const float* goal, const float* radius,
-                            int nw, const float* walls) {
+                            int nw, const float* walls, bool goals_fixed = true) {
   float rmax = 0.f;
   for (int i = 0; i < p; ++i) rmax = std::max(rmax, radius[i]);
   const double cell = std::max(2.0 * rmax, 1e-6);
-  for (int which = 0; which < 2; ++which) {
+  // a velocity-obstacle epoch's goal node holds reference points, which the
+  // factors never test against each other
+  for (int which = 0; which < (goals_fixed ? 2 : 1); ++which) {
     const float* X = which ? goal : start;
     double x0 = X[0], y0 = X[1], x1 = X[0], y1 = X[1];
     for (int i = 1; i < p; ++i) {
@@ -614,6 +644,7 @@ struct plan_s {
   int nv = 0;             // velocity-limit kinds (PLAN_VMAX, PLAN_VMIN)
   unsigned vmin_mask = 0; // which of them are minima
   bool noenergy = false;  // kinetic factors off (PLAN_NO_ENERGY or plan_set_energy)
+  bool vo = false;        // PLAN_VO: one velocity-obstacle epoch
   size_t slots;
   cudaStream_t stream;
   Layout L;
@@ -654,6 +685,7 @@ struct plan_s {
     P.nv = nv;
     P.vmin_mask = vmin_mask;
     P.noenergy = noenergy ? 1 : 0;
+    P.vo = vo ? 1 : 0;
     P.vlim = at<float>(L.vlim);
     P.wnode = at<uint8_t>(L.wnode);
     P.rho = rho_at(kk);
@@ -809,7 +841,7 @@ plan_status upload_inputs(plan_t h, const float* start, const float* goal, const
   const plan_config& c = h->cfg;
   const size_t p = c.p, eta = c.eta;
   std::vector<float> cost(p * eta);
-  const double norm = (c.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * eta);
+  const double norm = (c.flags & (PLAN_COST_UNNORM | PLAN_VO)) ? 1.0 : 1.0 / ((double)p * eta);
   for (size_t i = 0; i < p; ++i)
     for (size_t s = 0; s < eta; ++s) {
       double C = (c.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i];
@@ -903,8 +935,11 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
     return fail(PLAN_EINVAL, "warm_rho must be positive when warm_iters > 0");
   if (cfg->max_iter < 0) return fail(PLAN_EINVAL, "max_iter must be >= 0");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
-                         PLAN_DENSE_STATE | PLAN_ADMM | PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN;
+                         PLAN_DENSE_STATE | PLAN_ADMM | PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN |
+                         PLAN_VO;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
+  if ((cfg->flags & PLAN_VO) && (cfg->eta != 2 || (cfg->flags & (PLAN_ADMM | PLAN_NO_ENERGY))))
+    return fail(PLAN_EINVAL, "PLAN_VO needs eta = 2 and the kinetic factors, without PLAN_ADMM");
   if ((cfg->flags & PLAN_ADMM) && (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN)))
     return fail(PLAN_EUNSUPPORTED, "standard-ADMM mode runs with the kinetic factors only");
   const size_t p = cfg->p, eta = cfg->eta;
@@ -916,7 +951,8 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
     if (!(radius[i] > 0.f)) return fail(PLAN_EINVAL, "radius[%zu] must be positive", i);
   for (size_t i = 0; i < ncost; ++i)
     if (cost_w[i] < 0.f) return fail(PLAN_EINVAL, "cost_w[%zu] must be >= 0", i);
-  plan_status st = check_endpoints(cfg->p, start, goal, radius, cfg->n_walls, walls);
+  plan_status st = check_endpoints(cfg->p, start, goal, radius, cfg->n_walls, walls,
+                                   !(cfg->flags & PLAN_VO));
   if (st != PLAN_OK) return st;
 
   Layout L = layout_for(cfg);
@@ -927,6 +963,7 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
   h->nv = ((cfg->flags & PLAN_VMAX) ? 1 : 0) + ((cfg->flags & PLAN_VMIN) ? 1 : 0);
   h->vmin_mask = (cfg->flags & PLAN_VMIN) ? (1u << (h->nv - 1)) : 0u;
   h->noenergy = (cfg->flags & PLAN_NO_ENERGY) != 0;
+  h->vo = (cfg->flags & PLAN_VO) != 0;
   h->nt = (h->p + TILE - 1) / TILE;
   h->ntp = h->nt * (h->nt + 1) / 2;
   h->slots = (size_t)h->eta * h->ntp * TILE * TILE;
@@ -1023,7 +1060,8 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
   if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
   if (!finite_all(start, 2 * (size_t)h->p) || !finite_all(goal, 2 * (size_t)h->p))
     return fail(PLAN_EINVAL, "non-finite input");
-  plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data());
+  plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(),
+                                   !h->vo);
   if (st != PLAN_OK) return st;
   h->adj_valid = false;
   h->h_start.assign(start, start + 2 * (size_t)h->p);
@@ -1347,7 +1385,7 @@ plan_status adj_supported(plan_t h) {
   if (h->cfg.flags & (PLAN_ADMM | PLAN_U_KEEP))
     return fail(PLAN_EUNSUPPORTED, "the adjoint covers TWA with the reset rule only");
   if (h->cfg.warm_iters > 0) return fail(PLAN_EUNSUPPORTED, "the adjoint needs a constant rho0");
-  if (h->noenergy || h->nv)
+  if (h->noenergy || h->nv || h->vo)
     return fail(PLAN_EUNSUPPORTED, "the adjoint covers the kinetic, collision factors only");
   return PLAN_OK;
 }
@@ -1428,6 +1466,50 @@ plan_status plan_import_back_weights(plan_t h, const uint8_t* classes) {
   return PLAN_OK;
 }
 
+plan_status plan_get_endpoints(plan_t h, float* start, float* goal) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  if (start) CK(cudaMemcpyAsync(start, h->at<void>(h->L.start), (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (goal) CK(cudaMemcpyAsync(goal, h->at<void>(h->L.goal), (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_vo_epoch(plan_t h, const float* dest, float step, float advance, int* iters,
+                          float* residual, float* max_dist) {
+  if (!h || !dest) return fail(PLAN_EINVAL, "null argument");
+  if (!h->vo) return fail(PLAN_EINVAL, "plan_vo_epoch needs a PLAN_VO plan");
+  if (!(step > 0.f) || !(advance > 0.f && advance <= 1.f))
+    return fail(PLAN_EINVAL, "step must be > 0 and advance in (0, 1]");
+  const unsigned g = (unsigned)((h->p + 255) / 256);
+  float2* start = h->at<float2>(h->L.start);
+  float2* goal = h->at<float2>(h->L.goal);
+  vo_target_kernel<<<g, 256, 0, h->stream>>>(h->p, start, reinterpret_cast<const float2*>(dest), step, goal);
+  CK(cudaGetLastError());
+  plan_status st = plan_reset(h);  // the initial state of Section 4 for this epoch
+  if (st != PLAN_OK) return st;
+  int it = 0;
+  float res = INFINITY;
+  const plan_status sst = plan_solve(h, &it, &res);
+  if (sst != PLAN_OK && sst != PLAN_ENOTCONV) return sst;
+  unsigned* md = h->at<unsigned>(h->L.count);
+  CK(cudaMemsetAsync(md, 0, 4, h->stream));
+  const float2* z = h->cur ? h->at<float2>(h->L.z1) : h->at<float2>(h->L.z0);
+  vo_advance_kernel<<<g, 256, 0, h->stream>>>(h->p, h->eta, z, reinterpret_cast<const float2*>(dest),
+                                              advance, start, md);
+  CK(cudaGetLastError());
+  unsigned mdh = 0;
+  CK(cudaMemcpyAsync(h->h_start.data(), start, (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_goal.data(), goal, (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_res, md, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  mdh = *h->h_res;
+  if (iters) *iters = it;
+  if (residual) *residual = res;
+  if (max_dist) std::memcpy(max_dist, &mdh, 4);
+  h->adj_valid = false;
+  return sst;
+}
+
 plan_status plan_set_energy(plan_t h, int on) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
   if (h->cfg.flags & PLAN_ADMM) return fail(PLAN_EUNSUPPORTED, "standard-ADMM mode keeps the kinetic factors");
@@ -1459,7 +1541,7 @@ plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) 
     for (size_t i = 0; i < p; ++i)
       if (!(radius[i] > 0.f)) return fail(PLAN_EINVAL, "radius[%zu] must be positive", i);
     plan_status st = check_endpoints(h->p, h->h_start.data(), h->h_goal.data(), radius, h->nw,
-                                     h->h_walls.data());
+                                     h->h_walls.data(), !h->vo);
     if (st != PLAN_OK) return st;
   }
   std::vector<float> cost;
@@ -1467,7 +1549,7 @@ plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) 
     if (!finite_all(cost_w, ncost)) return fail(PLAN_EINVAL, "non-finite cost_w");
     for (size_t i = 0; i < ncost; ++i)
       if (cost_w[i] < 0.f) return fail(PLAN_EINVAL, "cost_w[%zu] must be >= 0", i);
-    const double norm = (h->cfg.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * eta);
+    const double norm = (h->cfg.flags & (PLAN_COST_UNNORM | PLAN_VO)) ? 1.0 : 1.0 / ((double)p * eta);
     cost.resize(p * eta);
     for (size_t i = 0; i < p; ++i)
       for (size_t s = 0; s < eta; ++s)
@@ -1655,7 +1737,7 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
   if (cfg->n_walls > 0 && (!walls || !u_wall_in || !u_wall_out)) return fail(PLAN_EINVAL, "null wall array");
   if (!(cfg->rho0 > 0.f) || !(cfg->alpha > 0.f)) return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
-  if (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN))
+  if (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN | PLAN_VO))
     return fail(PLAN_EUNSUPPORTED, "plan_iterate_static runs the energy problem without velocity factors");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
                          PLAN_DENSE_STATE | PLAN_ADMM;
@@ -1967,7 +2049,7 @@ plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const
   *out = nullptr;
   const unsigned modes = PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM;
   for (int b = 0; b < n; ++b)
-    if (cfgs[b].flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN))
+    if (cfgs[b].flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN | PLAN_VO))
       return fail(PLAN_EUNSUPPORTED, "batch members run the energy problem without velocity factors");
   for (int b = 1; b < n; ++b)
     if ((cfgs[b].flags & modes) != (cfgs[0].flags & modes))

@@ -50,6 +50,8 @@ struct Dev {
   int nv;                // velocity-factor kinds after the walls (0..2)
   unsigned vmin_mask;    // bit v: velocity kind v is a minimum (else maximum)
   int noenergy;          // no kinetic factors (the feasibility problem)
+  int vo;                // velocity-obstacle epoch (eta = 2): collision, wall and velocity
+                         // factors on segment 0 only, the kinetic factor on segment 1 only
   const float* vlim;     // [nv][p][eta] velocity limits
   uint8_t* wnode;        // [p][eta+1] back-weight class when noenergy: 0 or 1
   const float2* z;       // z^k, [p][eta+1]
@@ -319,6 +321,7 @@ __device__ __forceinline__ void test_block(const Dev& P, int blk) {
   float res = 0.f;
   if (blk == 0 && threadIdx.x == 0) *P.res_cur = 0u;
   const int s = blk / P.ntp;
+  if (P.vo && s != 0) return;  // no collision factors between x and x_ref
   const int2 IJ = P.tiles[blk - s * P.ntp];
   const int I = IJ.x, J = IJ.y;
   const bool diag = (I == J);
@@ -443,8 +446,8 @@ __device__ __forceinline__ void segment_block(const Dev& P, int blk) {
   float res = 0.f;
   for (int f = warp; f < 1 + P.nw + P.nv; f += blockDim.x >> 5) {
     if (f == 0) {
-      if (vi && !P.noenergy) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
-    } else {
+      if (vi && !P.noenergy && !(P.vo && s == 0)) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
+    } else if (!(P.vo && s != 0)) {
       wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
     }
   }
