@@ -148,9 +148,16 @@ def cpu_baseline(inst, budget_s=20.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": total * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full oracle iteration(s) of {inst.name} (iterations 2..{n + 1}), "
-                      f"{dt:.1f} s, numpy FP64 single thread"}
+    out = {"value": total * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} full oracle iteration(s) of {inst.name} (iterations 2..{n + 1}), "
+                     f"{dt:.1f} s, numpy FP64 single thread"}
+    # the oracle's own solve of the CPU-sized circle swap (time to converge)
+    small = workloads.circle4()
+    t0 = time.perf_counter()
+    _, it, _ = twa.solve(twa.Problem.from_instance(small), small.tol, small.max_iter)
+    out["time_to_converge_circle4_eta4"] = {"oracle_ms": 1e3 * (time.perf_counter() - t0),
+                                            "iterations": it}
+    return out
 
 
 def run_reference(args, inst):
@@ -184,7 +191,7 @@ def run_reference(args, inst):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_finite(line), allow_nan=False), flush=True)
 
 
 def timed_iterations(pl, stream, steps, flush):
@@ -214,33 +221,111 @@ def kernel_times(pl, stream, steps, flush):
     return pl.profile_stop()
 
 
-def time_to_converge(pk, names, oracle_names):
-    """plan_solve to the workload's tolerance (or its iteration cap) on the
-    GPU; the FP64 oracle's own solve time for the small workloads."""
+def _plan_quality(pk, inst, pl):
+    """Total kinetic cost (Eq. velo_cost_pair_wise) and clearances of the
+    planner's current trajectory, measured on the GPU with torch ops."""
     import torch
-    from oracle import twa
+    from paper_1311_4527_gb300 import losses
+    z = pl.trajectory().double()
+    dev = z.device
+    radius = torch.tensor(inst.radius, dtype=torch.float64, device=dev)
+    cost = torch.tensor(inst.cost_w, dtype=torch.float64, device=dev)
+    coll, wall = losses.min_clearance(z, radius, inst.walls if inst.n_walls else None)
+    return float(losses.kinetic_energy(z, cost)), coll, wall
+
+
+def _solve_timed(pl):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv, it, res = pl.solve()
+    torch.cuda.synchronize()
+    return conv, it, res, 1e3 * (time.perf_counter() - t0)
+
+
+def time_to_converge(pk, names):
+    """plan_solve to the workload's tolerance (or its iteration cap) on the
+    GPU, with the plan's cost and clearance."""
     out = {}
     for name in names:
         inst = workloads.by_name(name)
-        prob = twa.Problem.from_instance(inst)
         with pk.Planner.from_instance(inst, check_every=10) as pl:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            conv, it, res = pl.solve()
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            z = pl.trajectory().cpu().numpy().astype(np.float64)
-        coll, wall = twa.min_clearance(prob, z)
-        rec = {"converged": conv, "iterations": it, "residual": res, "tol": inst.tol,
-               "gpu_ms": 1e3 * dt, "total_cost": twa.total_cost(prob, z),
-               "min_clearance_ratio": coll}
-        if name in oracle_names:
-            t0 = time.perf_counter()
-            _, oit, ores = twa.solve(prob, inst.tol, inst.max_iter)
-            rec.update(oracle_ms=1e3 * (time.perf_counter() - t0), oracle_iterations=oit,
-                       oracle_cores=1)
-        out[name] = rec
+            conv, it, res, ms = _solve_timed(pl)
+            cost, coll, wall = _plan_quality(pk, inst, pl)
+        out[name] = {"converged": conv, "iterations": it, "residual": res, "tol": inst.tol,
+                     "gpu_ms": ms, "total_cost": cost, "min_clearance_ratio": coll,
+                     "min_wall_clearance_ratio": wall}
     return out
+
+
+def modes(pk):
+    """Rows f3 / f4 beside the plain solver on the same GPU: standard ADMM
+    against TWA (Fig. 2-left's comparison), the feasibility problem against
+    the energy problem (Section 4), a maximum-velocity limit, and recovery of
+    a collision-free plan from an energy solve stopped early."""
+    out = {}
+    for name in ("circle4_eta4", "circle100_eta8"):
+        inst = workloads.by_name(name)
+        rec = {}
+        for label, kw in (("twa", {}), ("admm", {"flags": pk.PLAN_ADMM}),
+                          ("feasibility", {"energy": False})):
+            with pk.Planner.from_instance(inst, check_every=10, **kw) as pl:
+                conv, it, res, ms = _solve_timed(pl)
+                cost, coll, _ = _plan_quality(pk, inst, pl)
+            rec[label] = {"converged": conv, "iterations": it, "gpu_ms": ms, "total_cost": cost,
+                          "min_clearance_ratio": coll}
+        if rec["twa"]["converged"] and rec["admm"]["converged"]:
+            rec["admm_over_twa_iterations"] = rec["admm"]["iterations"] / rec["twa"]["iterations"]
+        out[name] = rec
+    inst = workloads.circle4()
+    with pk.Planner.from_instance(inst, check_every=10, vmax=0.56) as pl:
+        conv, it, res, ms = _solve_timed(pl)
+        z = pl.trajectory().double()
+        vmax_seen = float((z[:, 1:] - z[:, :-1]).norm(dim=-1).max())
+        cost, coll, _ = _plan_quality(pk, inst, pl)
+    out["circle4_vmax0.56"] = {"converged": conv, "iterations": it, "gpu_ms": ms,
+                               "longest_segment": vmax_seen, "total_cost": cost,
+                               "min_clearance_ratio": coll}
+    inst = workloads.small_square(48, 8, 2)
+    with pk.Planner.from_instance(inst, check_every=1) as pl:
+        pl.iterate(300)
+        _, before, _ = _plan_quality(pk, inst, pl)
+        pl.set_energy(False)
+        conv, it, res, ms = _solve_timed(pl)
+        _, after, wall = _plan_quality(pk, inst, pl)
+    out["recovery_square48"] = {"energy_iterations": 300, "clearance_before": before,
+                                "feasibility_iterations": it - 300, "converged": conv,
+                                "gpu_ms": ms, "clearance_after": after,
+                                "wall_clearance_after": wall}
+    return out
+
+
+def local_planner(pk, p=32, epochs=150, step=0.1, advance=0.5):
+    """Section 5's velocity-obstacle planner on a circle swap (CONF1) with
+    the paper's symmetry breaking C_i = 1 + 0.001 i: per-epoch solve time and
+    iterations until every agent is within 1e-3 of its destination."""
+    import torch
+    inst = workloads.circle_swap(p, 2, 0.05, 0.005, workloads.SEED_BASE + 5, name=f"vo_circle{p}")
+    c = 1 + 0.001 * np.arange(p)
+    pl = pk.Planner.velocity_obstacle(inst.start, inst.goal, inst.radius, c, step, rho0=10.0,
+                                      tol=1e-6, max_iter=8000, check_every=5)
+    ms, its, conv_all = [], [], True
+    md = float("inf")
+    for e in range(epochs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, it, r, md = pl.vo_epoch(advance)
+        ms.append(1e3 * (time.perf_counter() - t0))
+        its.append(it)
+        conv_all &= conv
+        if md < 1e-3:
+            break
+    pl.close()
+    q = lambda a, f: float(np.percentile(a, f))
+    return {"workload": f"{inst.name}: p={p} circle swap, r=0.05, step {step}, advance {advance}",
+            "epochs": len(ms), "arrived": md < 1e-3, "all_epochs_converged": conv_all,
+            "epoch_ms": {"median": q(ms, 50), "p90": q(ms, 90), "max": max(ms)},
+            "epoch_iterations": {"median": q(its, 50), "p90": q(its, 90), "max": max(its)}}
 
 
 def batching(pk, n=512, max_iter=2000, check_every=50):
@@ -339,6 +424,18 @@ def differentiation(pk, K=2000, reps=3):
             "grad_norms": {"start": float(gs.norm()), "goal": float(gg.norm()),
                            "radius": float(gr.norm()), "cost": float(gc.norm())},
             "translation_identity_residual": float(resid) / max(float(dz.abs().sum()), 1e-30)}
+
+
+def _finite(obj):
+    """Non-finite floats (an unmeasured clearance, a residual that never
+    came) as null, so that the line is strict JSON."""
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: _finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_finite(v) for v in obj]
+    return obj
 
 
 def main():
@@ -495,11 +592,13 @@ def main():
         line["batching"] = batching(pk)
         line["differentiation"] = differentiation(pk)
         line["time_to_converge"] = time_to_converge(
-            pk, ["circle4_eta4", "circle100_eta8", "square1024_eta16"], ["circle4_eta4"])
+            pk, ["circle4_eta4", "circle100_eta8", "square1024_eta16"])
+        line["modes"] = modes(pk)
+        line["local_planner"] = local_planner(pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_finite(line), allow_nan=False), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

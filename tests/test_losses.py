@@ -31,3 +31,14 @@ def test_collision_slack_by_brute_force():
                 want += max(r[i] + r[j] - float(d), 0.0) ** 2
     got = float(losses.collision_slack(torch.tensor(z), torch.tensor(r), chunk=5))
     assert want > 0 and abs(got - want) <= 1e-9 * want
+
+
+def test_min_clearance_matches_the_oracle():
+    inst = workloads.small_square(30, 4, seed=8)
+    prob = twa.Problem.from_instance(inst)
+    rng = np.random.default_rng(3)
+    z = rng.uniform(0, inst.walls.max(), size=(30, 5, 2))
+    z[:, 0] = inst.start
+    want = twa.min_clearance(prob, z)
+    got = losses.min_clearance(torch.tensor(z), torch.tensor(inst.radius), inst.walls)
+    assert abs(got[0] - want[0]) <= 1e-9 * max(1.0, want[0]) and abs(got[1] - want[1]) <= 1e-9 * max(1.0, want[1])
