@@ -39,6 +39,18 @@ __global__ void __launch_bounds__(32 * TEST_WARPS) test_kernel(Dev P) {
   test_block<DENSE, TEST_ROWS>(P, blockIdx.x);
 }
 
+// Gated state: one warp per tile, lane = row agent (test_tile_rows).
+constexpr int TILES_PER_CTA = 4;
+__global__ void __launch_bounds__(32 * TILES_PER_CTA) test_rows_kernel(Dev P) {
+  __shared__ float4 col[TILES_PER_CTA][64];
+  const int warp = threadIdx.x >> 5;
+  const int blk = blockIdx.x * TILES_PER_CTA + warp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
+  if (blk >= P.eta * P.ntp) return;  // warp-uniform
+  if (P.vo && blk >= P.ntp) return;  // no collision factors on the second segment
+  test_tile_rows(P, blk, col[warp]);
+}
+
 __global__ void __launch_bounds__(THREADS) segment_kernel(Dev P) { segment_block(P, blockIdx.x); }
 
 __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
@@ -764,7 +776,7 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   }
   if (prof) CK(cudaEventRecord(h->pev[0], ms));
   if (P.dense) test_kernel<true><<<grid, 32 * TEST_WARPS, 0, ms>>>(P);
-  else test_kernel<false><<<grid, 32 * TEST_WARPS, 0, ms>>>(P);
+  else test_rows_kernel<<<(grid + TILES_PER_CTA - 1) / TILES_PER_CTA, 32 * TILES_PER_CTA, 0, ms>>>(P);
   if (prof) CK(cudaEventRecord(h->pev[1], ms));
   prox_kernel<<<h->prox_grid, 256, 0, ms>>>(P);
   if (prof) CK(cudaEventRecord(h->pev[2], ms));

@@ -429,6 +429,111 @@ __device__ __forceinline__ void test_block(const Dev& P, int blk) {
   if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
 }
 
+// Pass 1 of an iteration, gated state, one warp per (segment s, agent tiles
+// I <= J) block with lane = ROW agent i: each lane keeps its row agent in
+// registers and walks the 32 column agents, whose data the warp stages in
+// shared memory (one broadcast 16-byte load per column).  A lane accumulates
+// its row's activity word itself, so a row costs no shuffles, ballots or
+// per-row bookkeeping; the pairs of the row that were active in the last
+// iteration (set bits) are finished first (deferred step 7, exact test on
+// n = z - u), every other valid pair has u = 0 by the reset rule and takes the
+// bounding-circle early out before the exact test.  Same decisions and
+// stores as test_block<false>; only the worklist order differs.
+// col: 64 float4 of shared memory per warp.
+__device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col) {
+  const int lane = threadIdx.x & 31;
+  const int E1 = P.eta + 1;
+  float res = 0.f;
+  const int s = blk / P.ntp;
+  const int2 IJ = P.tiles[blk - s * P.ntp];
+  const int I = IJ.x, J = IJ.y;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  // column agents: (midpoint, bounding radius, r_j) and (z lo, z hi)
+  const int j = J * TILE + lane;
+  const bool vj = j < P.p;
+  float2 zjl = mk(0.f, 0.f), zjh = zjl;
+  float rj = 0.f;
+  if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
+  {
+    const float2 m = 0.5f * (zjl + zjh);
+    col[lane] = make_float4(m.x, m.y, 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj, rj);
+    col[32 + lane] = pack(zjl, zjh);
+  }
+  const uint32_t vmask = __ballot_sync(FULL, vj);
+  __syncwarp();
+  // the row agent of this lane
+  const int i = I * TILE + lane;
+  const bool vi = i < P.p;
+  const size_t row = (size_t)blk * TILE + lane;
+  float2 zil = mk(0.f, 0.f), zih = zil;
+  float ri = 0.f;
+  uint32_t word = 0u;
+  if (vi) {
+    zil = P.z[(size_t)i * E1 + s]; zih = P.z[(size_t)i * E1 + s + 1]; ri = P.radius[i];
+    word = P.bits[row];
+  }
+  uint32_t valid = vi ? vmask : 0u;
+  if (I == J) valid &= (lane == 31) ? 0u : (~0u << (lane + 1));  // pairs i < j
+  uint32_t nword = 0u;
+  // pairs active in the last iteration: finish step 7, test n = z - u exactly
+  for (uint32_t pend = word; pend; pend &= pend - 1u) {
+    const int c = __ffs(pend) - 1;
+    const size_t fid = row * TILE + c;
+    const float4 cb = col[32 + c];
+    const float rjc = col[c].w;
+    const float4 a = P.ulo[fid], b = P.uhi[fid], xa = P.xlo[fid], xb = P.xhi[fid];
+    const float2 uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zil, P.alpha, res);
+    const float2 ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), lo2(cb), P.alpha, res);
+    const float2 uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
+    const float2 ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), hi2(cb), P.alpha, res);
+    if (collides((lo2(cb) - ujl) - (zil - uil), (hi2(cb) - ujh) - (zih - uih), ri + rjc)) {
+      P.ulo[fid] = pack(uil, ujl);
+      P.uhi[fid] = pack(uih, ujh);
+      nword |= 1u << c;
+    }
+  }
+  // every other valid pair: u = 0, n = z; bounding circles first
+  const uint32_t rest = valid & ~word;
+  if (__any_sync(FULL, rest != 0u)) {
+    const float2 mi = 0.5f * (zil + zih);
+    const float bi = 0.5f * sqrtf(dot(zih - zil, zih - zil)) + ri;
+#pragma unroll 8
+    for (int c = 0; c < TILE; ++c) {
+      const float4 A = col[c];
+      const float2 dm = mk(A.x, A.y) - mi;
+      const float br = bi + A.z;
+      if (((rest >> c) & 1u) && dot(dm, dm) <= br * br * 1.00002f) {
+        const float4 B = col[32 + c];
+        if (collides(lo2(B) - zil, hi2(B) - zih, ri + A.w)) {
+          // a newly active pair starts from u = 0 (the slot may hold an old u)
+          const size_t fid = row * TILE + c;
+          P.ulo[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          P.uhi[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          nword |= 1u << c;
+        }
+      }
+    }
+  }
+  if (vi && nword != word) P.bits[row] = nword;
+  // worklist: warp prefix sum of the rows' active counts, one atomic per warp
+  const unsigned cnt = __popc(nword);
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned total = __shfl_sync(FULL, incl, 31);
+  if (total) {
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(P.work_count, total);
+    base = __shfl_sync(FULL, base, 31) + (incl - cnt);
+    for (uint32_t w = nword; w; w &= w - 1u) P.work[base++] = (uint32_t)(row * TILE + (__ffs(w) - 1));
+  }
+  res = warp_max(res);
+  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
 // Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
 // s and one agent tile: warp f < 1 + n_walls takes factor kind f (0 =
 // kinetic, else wall f - 1), lane = agent.
