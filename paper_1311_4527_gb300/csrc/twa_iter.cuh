@@ -296,6 +296,18 @@ __device__ __forceinline__ int tile_pair(int nt, int I, int J) {  // I <= J
   return I * nt - I * (I - 1) / 2 + (J - I);
 }
 
+// Inverse of tile_pair: the tiles (I, J), I <= J, of pair index t, without
+// the table lookup (a square root, then an exact integer correction).
+__device__ __forceinline__ void tile_of(int nt, int t, int& I, int& J) {
+  const float b = 2.f * nt + 1.f;
+  int i = (int)((b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
+  i = max(0, min(i, nt - 1));
+  while (i > 0 && tile_pair(nt, i, i) > t) --i;
+  while (i + 1 < nt && tile_pair(nt, i + 1, i + 1) <= t) ++i;
+  I = i;
+  J = i + (t - tile_pair(nt, i, i));
+}
+
 // Pass 1 of an iteration.  One CTA of 4 warps per (segment s, agent tiles
 // I <= J) block of 32 x 32 collision factors; each warp takes 8 rows, lane =
 // column agent j, and the row agents' data is held one per lane and broadcast
@@ -445,8 +457,8 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   const int E1 = P.eta + 1;
   float res = 0.f;
   const int s = blk / P.ntp;
-  const int2 IJ = P.tiles[blk - s * P.ntp];
-  const int I = IJ.x, J = IJ.y;
+  int I, J;
+  tile_of(P.nt, blk - s * P.ntp, I, J);
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
   // column agents: (midpoint, bounding radius, r_j) and (z lo, z hi)
   const int j = J * TILE + lane;
@@ -492,25 +504,29 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
       nword |= 1u << c;
     }
   }
-  // every other valid pair: u = 0, n = z; bounding circles first
+  // every other valid pair: u = 0, n = z.  The bounding circles of all 32
+  // columns first (branch-free), then the exact test on the near ones.
   const uint32_t rest = valid & ~word;
   if (__any_sync(FULL, rest != 0u)) {
     const float2 mi = 0.5f * (zil + zih);
     const float bi = 0.5f * sqrtf(dot(zih - zil, zih - zil)) + ri;
-#pragma unroll 8
+    uint32_t near = 0u;
+#pragma unroll
     for (int c = 0; c < TILE; ++c) {
       const float4 A = col[c];
       const float2 dm = mk(A.x, A.y) - mi;
       const float br = bi + A.z;
-      if (((rest >> c) & 1u) && dot(dm, dm) <= br * br * 1.00002f) {
-        const float4 B = col[32 + c];
-        if (collides(lo2(B) - zil, hi2(B) - zih, ri + A.w)) {
-          // a newly active pair starts from u = 0 (the slot may hold an old u)
-          const size_t fid = row * TILE + c;
-          P.ulo[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
-          P.uhi[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
-          nword |= 1u << c;
-        }
+      near |= (dot(dm, dm) <= br * br * 1.00002f) ? (1u << c) : 0u;
+    }
+    for (near &= rest; near; near &= near - 1u) {
+      const int c = __ffs(near) - 1;
+      const float4 B = col[32 + c];
+      if (collides(lo2(B) - zil, hi2(B) - zih, ri + col[c].w)) {
+        // a newly active pair starts from u = 0 (the slot may hold an old u)
+        const size_t fid = row * TILE + c;
+        P.ulo[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.uhi[fid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        nword |= 1u << c;
       }
     }
   }
