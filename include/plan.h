@@ -214,13 +214,14 @@ plan_status plan_batch_solve(plan_batch_t batch, int* iters_done, float* residua
 /* Break-points of one member, as plan_get_trajectory. */
 plan_status plan_batch_get_trajectory(plan_batch_t batch, int member, float* z, int on_device);
 /* Time the launch-shape candidates (rows per warp of the collision test
- * {4, 8, 16}, minimizer CTAs per SM {1, 2, 4} x the base grid, iterations per
+ * {4, 8, 16}, or 32: one warp per tile with lane = row agent, gated state
+ * only; minimizer CTAs per SM {1, 2, 4} x the base grid; iterations per
  * graph {2, 8}) on this batch, iters_per_candidate iterations each (they are
  * real iterations: results do not depend on the shape), and keep the fastest.
  * choice: 3 host ints receiving the chosen values (may be NULL). */
 plan_status plan_batch_autotune(plan_batch_t batch, int iters_per_candidate, int* choice);
 /* Set the launch shape directly (for example one found by the autotuner on
- * another batch of the same instances): rows_per_warp in {4, 8, 16},
+ * another batch of the same instances): rows_per_warp in {4, 8, 16, 32},
  * prox_ctas_per_sm in 1..8, iterations_per_graph even and >= 2. */
 plan_status plan_batch_set_shape(plan_batch_t batch, int rows_per_warp, int prox_ctas_per_sm,
                                  int iterations_per_graph);

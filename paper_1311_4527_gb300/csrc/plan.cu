@@ -1844,6 +1844,28 @@ __global__ void __launch_bounds__(32 * (TILE / TROWS)) batch_test_kernel(const D
   test_block<DENSE, TROWS>(sP, sblk);
 }
 
+// Gated state, one warp per tile (lane = row agent): each warp finds its own
+// member, since the 4 tiles of a CTA may belong to different members.
+__global__ void __launch_bounds__(32 * TILES_PER_CTA) batch_test_rows_kernel(const Dev* tab, const int* pre,
+                                                                         int n, int ntiles,
+                                                                         const uint8_t* frozen) {
+  __shared__ Dev sP[TILES_PER_CTA];
+  __shared__ float4 col[TILES_PER_CTA][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * TILES_PER_CTA + warp;
+  if (t >= ntiles) return;  // warp-uniform
+  const int b = find_member(pre, n, t);
+  if (frozen[b]) return;
+  // the member's descriptor into this warp's shared slot
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(tab + b);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sP[warp]);
+  for (int w = lane; w < (int)(sizeof(Dev) / 4); w += 32) dst[w] = src[w];
+  __syncwarp();
+  const int blk = t - pre[b];
+  if (blk == 0 && lane == 0) *sP[warp].res_cur = 0u;
+  test_tile_rows(sP[warp], blk, col[warp]);
+}
+
 __global__ void batch_segment_kernel(const Dev* tab, const int* pre, int n, const uint8_t* frozen) {
   __shared__ Dev sP;
   __shared__ int sb, sblk;
@@ -1979,7 +2001,10 @@ void launch_batch_test(plan_batch_s* B, const Dev* tab, cudaStream_t s) {
 
 plan_status enqueue_batch_iteration(plan_batch_s* B, int parity, cudaStream_t s) {
   const Dev* tab = B->tab[parity];
-  if (B->trows == 4) launch_batch_test<4>(B, tab, s);
+  if (B->trows == 32 && !B->dense)
+    batch_test_rows_kernel<<<(B->ntest + TILES_PER_CTA - 1) / TILES_PER_CTA, 32 * TILES_PER_CTA, 0, s>>>(
+        tab, B->pre_test, B->n, B->ntest, B->frozen);
+  else if (B->trows == 4) launch_batch_test<4>(B, tab, s);
   else if (B->trows == 16) launch_batch_test<16>(B, tab, s);
   else launch_batch_test<8>(B, tab, s);
   batch_segment_kernel<<<B->nseg, THREADS, 0, s>>>(tab, B->pre_seg, B->n, B->frozen);
@@ -2199,11 +2224,11 @@ plan_status plan_batch_autotune(plan_batch_t B, int iters_per_candidate, int* ch
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int tr[3] = {4, 8, 16}, mu[3] = {1, 2, 4}, gl[2] = {2, 8};
+  const int tr[4] = {4, 8, 16, 32}, mu[3] = {1, 2, 4}, gl[2] = {2, 8};
   float best = INFINITY;
   int bt = B->trows, bm = B->prox_mult, bg = B->glen;
   if (B->k & 1) { plan_status st = batch_run(B, 1); if (st != PLAN_OK) return st; }
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < (B->dense ? 3 : 4); ++a)
     for (int c = 0; c < 3; ++c)
       for (int g = 0; g < 2; ++g) {
         B->trows = tr[a]; B->prox_mult = mu[c]; B->glen = gl[g];
@@ -2229,8 +2254,9 @@ plan_status plan_batch_autotune(plan_batch_t B, int iters_per_candidate, int* ch
 plan_status plan_batch_set_shape(plan_batch_t B, int rows_per_warp, int prox_ctas_per_sm,
                                  int iterations_per_graph) {
   if (!B) return fail(PLAN_EINVAL, "null batch");
-  if (rows_per_warp != 4 && rows_per_warp != 8 && rows_per_warp != 16)
-    return fail(PLAN_EINVAL, "rows_per_warp must be 4, 8 or 16");
+  if (rows_per_warp != 4 && rows_per_warp != 8 && rows_per_warp != 16 &&
+      !(rows_per_warp == 32 && !B->dense))
+    return fail(PLAN_EINVAL, "rows_per_warp must be 4, 8, 16 (or 32 with the gated state)");
   if (prox_ctas_per_sm < 1 || prox_ctas_per_sm > 8) return fail(PLAN_EINVAL, "prox_ctas_per_sm must be 1..8");
   if (iterations_per_graph < 2 || (iterations_per_graph & 1))
     return fail(PLAN_EINVAL, "iterations_per_graph must be even and >= 2");

@@ -33,11 +33,11 @@ def test_batch_members_match_single_planners_bit_for_bit():
         B.iterate(37)
         zb = [B.trajectory(b).cpu().numpy() for b in range(len(insts))]
         choice = B.autotune(4)          # real iterations under other shapes
-        assert choice["rows_per_warp"] in (4, 8, 16)
+        assert choice["rows_per_warp"] in (4, 8, 16, 32)
         # the autotuner first aligns to an even iteration (37 -> 38), then per
         # candidate runs one graph's worth (2 or 8) plus the timed iterations
-        # (4 rounded to whole graphs: 4 or 8): 9 x (2 + 4 + 8 + 8)
-        done = 38 + 9 * (2 + 4 + 8 + 8)
+        # (4 rounded to whole graphs: 4 or 8): 4 x 3 shapes x (2 + 4 + 8 + 8)
+        done = 38 + 12 * (2 + 4 + 8 + 8)
         B.iterate(11)
         zc = [B.trajectory(b).cpu().numpy() for b in range(len(insts))]
     for b, inst in enumerate(insts):
@@ -62,3 +62,17 @@ def test_batch_solve_stops_members_where_their_own_solves_stop():
             z = pl.trajectory().cpu().numpy()
         assert it == its[b], (b, it, its[b])
         assert np.array_equal(z, zb[b]), b
+
+
+@pytest.mark.parametrize("rows", [4, 32])
+def test_every_test_pass_shape_gives_the_same_iterates(rows):
+    """The row-per-lane collision test (rows_per_warp = 32) and the
+    rows-per-warp one take identical decisions and store identical state."""
+    import paper_1311_4527_gb300 as pk
+    insts = _members()
+    with pk.PlannerBatch(insts) as B:
+        B.set_shape(rows, 2, 2)
+        B.iterate(24)
+        zb = [B.trajectory(b).cpu().numpy() for b in range(len(insts))]
+    for b, inst in enumerate(insts):
+        assert np.array_equal(zb[b], _alone(inst, 24)), b
