@@ -672,6 +672,7 @@ struct plan_s {
   cudaEvent_t pev[6] = {};
   cudaEvent_t pend = nullptr;
   cudaGraphExec_t gexec[4] = {};  // captured iterations by (k parity, z buffer)
+  cudaGraphExec_t gexec8[4] = {}; // ... and runs of ITERS_PER_GRAPH iterations
   double ptime[4] = {0, 0, 0, 0};
   int pcount = 0;
   unsigned* h_res;  // pinned host word for residual readback
@@ -829,6 +830,45 @@ plan_status run_iteration(plan_t h) {
   }
   if (h->eta > 1) h->cur ^= 1;
   h->k += 1;
+  return PLAN_OK;
+}
+
+// Runs of ITERS_PER_GRAPH iterations replayed from one graph (an even count,
+// so the run ends at the parity and z buffer it started from): fewer launches
+// for problems small enough that launching is the cost.
+constexpr int ITERS_PER_GRAPH = 8;
+
+plan_status run_iterations(plan_t h, int n) {
+  plan_status st = ensure_prox_grid(h);
+  if (st != PLAN_OK) return st;
+  while (n >= ITERS_PER_GRAPH && h->cap && h->side && !h->profiling &&
+         h->k >= std::max(1, h->cfg.warm_iters)) {
+    const int key = ((h->k & 1) << 1) | h->cur;
+    if (!h->gexec8[key]) {
+      const int k0 = h->k, c0 = h->cur;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      plan_status cst = PLAN_OK;
+      for (int q = 0; q < ITERS_PER_GRAPH && cst == PLAN_OK; ++q) {
+        cst = enqueue_iteration(h, h->cap);
+        if (h->eta > 1) h->cur ^= 1;
+        h->k += 1;
+      }
+      h->k = k0;
+      h->cur = c0;
+      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+      if (cst != PLAN_OK) { if (g) cudaGraphDestroy(g); return cst; }
+      if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h->gexec8[key], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(h->gexec8[key], h->stream));
+    h->k += ITERS_PER_GRAPH;
+    n -= ITERS_PER_GRAPH;
+  }
+  for (; n > 0; --n)
+    if ((st = run_iteration(h)) != PLAN_OK) return st;
   return PLAN_OK;
 }
 
@@ -1061,6 +1101,8 @@ void plan_destroy(plan_t h) {
     if (h->pev[q]) cudaEventDestroy(h->pev[q]);
   for (int q = 0; q < 4; ++q)
     if (h->gexec[q]) cudaGraphExecDestroy(h->gexec[q]);
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec8[q]) cudaGraphExecDestroy(h->gexec8[q]);
   if (h->pend) cudaEventDestroy(h->pend);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -1094,10 +1136,8 @@ plan_status plan_iterate(plan_t h, int k_iters, float* max_residual) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
   if (k_iters < 0) return fail(PLAN_EINVAL, "k_iters must be >= 0");
   if (k_iters > 0) h->adj_valid = false;
-  for (int it = 0; it < k_iters; ++it) {
-    plan_status st = run_iteration(h);
-    if (st != PLAN_OK) return st;
-  }
+  plan_status st = run_iterations(h, k_iters);
+  if (st != PLAN_OK) return st;
   if (max_residual) return read_residual(h, max_residual);
   return PLAN_OK;
 }
@@ -1531,6 +1571,8 @@ plan_status plan_set_energy(plan_t h, int on) {
   // the captured iterations hold the old mode
   for (int q = 0; q < 4; ++q)
     if (h->gexec[q]) { cudaGraphExecDestroy(h->gexec[q]); h->gexec[q] = nullptr; }
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec8[q]) { cudaGraphExecDestroy(h->gexec8[q]); h->gexec8[q] = nullptr; }
   h->noenergy = off;
   Dev P = h->dev(h->k);
   if (off) {
@@ -1603,12 +1645,10 @@ plan_status plan_unroll(plan_t h, int K, int checkpoint_every) {
   st = plan_reset(h);
   if (st != PLAN_OK) return st;
   h->ck_cur.assign(A.nck, 0);
-  for (int k = 0; k < K; ++k) {
-    if (k % C == 0) {
-      h->ck_cur[k / C] = h->cur;
-      if ((st = snapshot(h, A, k / C, true)) != PLAN_OK) return st;
-    }
-    if ((st = run_iteration(h)) != PLAN_OK) return st;
+  for (int k = 0; k < K; k += C) {
+    h->ck_cur[k / C] = h->cur;
+    if ((st = snapshot(h, A, k / C, true)) != PLAN_OK) return st;
+    if ((st = run_iterations(h, std::min(C, K - k))) != PLAN_OK) return st;
   }
   h->ck_cur[A.nck - 1] = h->cur;
   if ((st = snapshot(h, A, A.nck - 1, true)) != PLAN_OK) return st;
