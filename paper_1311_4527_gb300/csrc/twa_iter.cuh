@@ -98,8 +98,8 @@ __device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, f
 // depend on the order of the atomics, so z is deterministic and is the
 // correctly rounded mean of the incoming m's.  A non-finite or out-of-range m
 // sets status bit 1, which the consensus pass turns into a NaN residual.
-__device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m) {
-  const float scale = P.fix[0], bound = P.fix[1];
+__device__ __forceinline__ void contribute(const Dev& P, float scale, float bound, int i, int s,
+                                           float2 m) {
   if (!(fabsf(m.x) <= bound && fabsf(m.y) <= bound)) {
     atomicOr(P.status, 2u);
     return;
@@ -108,6 +108,9 @@ __device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m)
   atomicAdd(P.accx + node, (unsigned long long)__float2ll_rn(m.x * scale));
   atomicAdd(P.accy + node, (unsigned long long)__float2ll_rn(m.y * scale));
   atomicAdd(P.accc + node, 1u);
+}
+__device__ __forceinline__ void contribute(const Dev& P, int i, int s, float2 m) {
+  contribute(P, P.fix[0], P.fix[1], i, s, m);
 }
 
 // Standard-ADMM mode, a factor that was feasible in the previous iteration:
@@ -583,8 +586,10 @@ __device__ __forceinline__ void prox_item(const Dev& P, uint32_t fid) {
   const uint32_t row = fid >> 5, c = fid & 31;
   const uint32_t blk = row >> 5, r = row & 31;
   const int s = (int)(blk / P.ntp);
-  const int2 IJ = P.tiles[blk - (uint32_t)s * P.ntp];
-  const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
+  int I, J;
+  tile_of(P.nt, (int)(blk - (uint32_t)s * P.ntp), I, J);
+  const int i = I * TILE + r, j = J * TILE + c;
+  const float scale = P.fix[0], bound = P.fix[1];  // loaded beside the minimizer
   const float4 a = P.ulo[fid], b = P.uhi[fid];
   const float2 nil = P.z[(size_t)i * E1 + s] - lo2(a), nih = P.z[(size_t)i * E1 + s + 1] - lo2(b);
   const float2 njl = P.z[(size_t)j * E1 + s] - hi2(a), njh = P.z[(size_t)j * E1 + s + 1] - hi2(b);
@@ -603,12 +608,12 @@ __device__ __forceinline__ void prox_item(const Dev& P, uint32_t fid) {
   P.xlo[fid] = pack(xil, xjl);
   P.xhi[fid] = pack(xih, xjh);
   if (!pin_lo) {
-    contribute(P, i, s, xil + lo2(a));
-    contribute(P, j, s, xjl + hi2(a));
+    contribute(P, scale, bound, i, s, xil + lo2(a));
+    contribute(P, scale, bound, j, s, xjl + hi2(a));
   }
   if (!pin_hi) {
-    contribute(P, i, s + 1, xih + lo2(b));
-    contribute(P, j, s + 1, xjh + hi2(b));
+    contribute(P, scale, bound, i, s + 1, xih + lo2(b));
+    contribute(P, scale, bound, j, s + 1, xjh + hi2(b));
   }
 }
 
@@ -620,6 +625,7 @@ __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, b
   const int sp = 1 + t / P.p;
   const int i = t - (sp - 1) * P.p;
   const size_t node = (size_t)i * (P.eta + 1) + sp;
+  const unsigned status = *P.status;  // issued with the sums, not after them
   const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
   const unsigned cnt = P.accc[node];
   P.accx[node] = 0ull;
@@ -642,7 +648,7 @@ __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, b
   // step 6: the back weight is rho0 where some factor sent rho0, else 0
   if (P.noenergy) P.wnode[node] = cnt > 0u ? 1 : 0;
   P.z_next[node] = zn;
-  bad = (*P.status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
+  bad = (status & 2u) != 0u || !(fabsf(zn.x - zo.x) + fabsf(zn.y - zo.y) >= 0.f);
   dz = bad ? 0.f : maxabs2(zn - zo);
 }
 
