@@ -532,6 +532,9 @@ struct Layout {
 bool sizes_ok(const plan_config* c) {
   if (c->p < 1 || c->eta < 1 || c->n_walls < 0) return false;
   if (c->p > (1 << 16) || c->eta > (1 << 12) || c->n_walls > 4096) return false;
+  // pair slots are addressed by 32-bit indices (worklist entries, fid)
+  const unsigned long long nt = (c->p + TILE - 1) / TILE, ntp = nt * (nt + 1) / 2;
+  if ((unsigned long long)c->eta * ntp * TILE * TILE > 0xffffffffull) return false;
   return true;
 }
 

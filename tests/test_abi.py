@@ -191,3 +191,10 @@ def test_static_and_batch_paths_refuse_the_variant_modes(lib):
     h = ctypes.c_void_p()
     code = lib.plan_batch_create(1, cfgs, arr, arr, arr, arr, None, None, 0, None, ctypes.byref(h))
     assert code == 7
+
+
+def test_problems_beyond_32_bit_pair_slots_are_rejected(lib):
+    n = ctypes.c_size_t()
+    # 65,536 agents x 16 segments: 2,098,176 tile pairs x 16 x 1,024 > 2^32 slots
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(65536, 16)), ctypes.byref(n)) == 1
+    assert lib.plan_workspace_size(ctypes.byref(_cfg(65536, 1)), ctypes.byref(n)) == 0
