@@ -13,8 +13,10 @@ Per-factor Jacobians are taken by central differences of the oracle's own
 minimizers (``oracle.prox``) in FP64, so this reference is independent of
 any analytic derivation; the differences use a step of 1e-6 of the problem
 scale, small enough not to change the minimizer's branch in the cases the
-tests use.  Walls, standard-ADMM mode, kept u and the rho warm-up are not
-covered.
+tests use.  Wall factors and velocity-limit factors are gated like the
+collision factors (their u lives only while they stay active).  The
+feasibility mode, standard-ADMM mode, kept u, the rho warm-up and the local
+planner are not covered.
 """
 from __future__ import annotations
 
@@ -47,15 +49,40 @@ def _jac_fd(f, v, h):
 
 
 def record(prob: twa.Problem, K: int):
-    """Forward K iterations, keeping what the adjoint needs per iteration."""
-    assert prob.n_walls == 0 and not prob.admm and not prob.u_keep and prob.warm_iters == 0
+    """Forward K iterations, keeping what the adjoint needs per iteration:
+    the state at the start of the iteration and which collision factors and
+    gated segment factors (walls, velocity limits) were active."""
+    assert (prob.energy and not prob.admm and not prob.u_keep and prob.warm_iters == 0
+            and not prob.vo)
     st = twa.initial_state(prob)
     tape = []
     for _ in range(K):
         new, info = twa.iterate(prob, st)
-        tape.append((st, info.active_coll))
+        seg = set()
+        for w, s, i in zip(*np.nonzero(info.active_wall)):
+            seg.add(("w", int(w), int(s), int(i)))
+        for kind, act in info.extra["active_vel"].items():
+            for s, i in zip(*np.nonzero(act)):
+                seg.add(("v", kind, int(s), int(i)))
+        tape.append((st, info.active_coll, seg))
         st = new
     return st, tape
+
+
+def _seg_factor(prob, st, key):
+    """(u (2, 2), minimizer of n (4,) -> x (4,) with radius argument, radius
+    index or None) of a gated segment factor at state st."""
+    rho = prob.rho0
+    typ, w, s, i = key
+    wl = INF if s == 0 else rho
+    wh = INF if s + 1 == prob.eta else rho
+    if typ == "w":
+        xL, xR = prob.walls[w, :2], prob.walls[w, 2:]
+        f = lambda v, r: np.concatenate(prox.wall_prox(v[:2], v[2:], wl, wh, xL, xR, r)[:2])
+        return st.u_wall[w, s, i], f, i
+    lim = (prob.vmax if w == "max" else prob.vmin)[i, s]
+    f = lambda v, r: np.concatenate(prox.velocity_prox(v[:2], v[2:], wl, wh, lim, w)[:2])
+    return st.u_vel[w][s, i], f, None
 
 
 def branches(prob: twa.Problem, K: int) -> np.ndarray:
@@ -81,6 +108,25 @@ def branches(prob: twa.Problem, K: int) -> np.ndarray:
     return out
 
 
+def seg_branches(prob: twa.Problem, K: int):
+    """Per iteration, the active gated segment factors (walls, velocity
+    limits) with a code 1 + (lower end moved) + 2 (upper end moved): two runs
+    with equal lists took the same branches of those minimizers."""
+    _, tape = record(prob, K)
+    out = []
+    for st, _, seg in tape:
+        codes = {}
+        for key in seg:
+            u, fn, _ = _seg_factor(prob, st, key)
+            _, _, s, i = key
+            nv = np.concatenate([st.z[i, s] - u[0], st.z[i, s + 1] - u[1]])
+            x = fn(nv, prob.radius[i])
+            sc = 1e-12 * max(1.0, float(np.abs(nv).max()))
+            codes[key] = 1 + int(np.abs(x[:2] - nv[:2]).max() > sc) + 2 * int(np.abs(x[2:] - nv[2:]).max() > sc)
+        out.append(codes)
+    return out
+
+
 def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None):
     """dL/d(start, goal, radius, cost) for dL/dz^K = dz_K (p, eta+1, 2)."""
     p, eta = prob.p, prob.eta
@@ -97,13 +143,14 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
     g_cost = np.zeros((p, eta))
     zbar = dz_K.astype(np.float64).copy()          # adjoint of z^{k+1}
     ubar_coll = {}                                   # (s, q) -> (4, 2) adjoint of u^{k+1}
+    ubar_seg = {}                                    # gated segment factor -> (2, 2)
     ubar_kin = np.zeros((eta, p, 2, 2))
     free = np.ones((p, eta + 1), dtype=bool)
     free[:, 0] = False
     free[:, eta] = False
 
     for k in range(K - 1, -1, -1):
-        st, act = tape[k]
+        st, act, seg = tape[k]
         z, u_coll, u_kin = st.z, st.u_coll, st.u_kin
         # fixed ends of z^{k+1}
         g_start += zbar[:, 0]
@@ -123,6 +170,13 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
                     cnt[ag, ss] += 1.0
                     if free[ag, ss]:
                         zhat[ag, ss] -= alpha * ub[e]
+        for key in seg:
+            ub = ubar_seg.get(key, np.zeros((2, 2)))
+            _, _, s, i = key
+            for e, ss in ((0, s), (1, s + 1)):
+                cnt[i, ss] += 1.0
+                if free[i, ss]:
+                    zhat[i, ss] -= alpha * ub[e]
         # step 5: z^{k+1} = mean of m over active edges (free nodes)
         mbar_node = np.where(free[..., None], zhat / np.maximum(cnt, 1.0)[..., None], 0.0)
         new_zbar = np.zeros_like(zbar)
@@ -184,9 +238,33 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
                     if free[a, b]:
                         out[e] = ubar_acc[e] - nbar[2 * e:2 * e + 2]
                 new_ubar_coll[(s, q)] = out
+        # gated segment factors (walls, velocity limits)
+        new_ubar_seg = {}
+        for key in seg:
+            u, fn, ri = _seg_factor(prob, st, key)
+            _, _, s, i = key
+            nv = np.concatenate([z[i, s] - u[0], z[i, s + 1] - u[1]])
+            r = prob.radius[i]
+            J = _jac_fd(lambda v: fn(v, r), nv, h)
+            ub = ubar_seg.get(key, np.zeros((2, 2)))
+            xbar = np.zeros(4)
+            out = np.zeros((2, 2))
+            for e, ss in ((0, s), (1, s + 1)):
+                if free[i, ss]:
+                    xbar[2 * e:2 * e + 2] = alpha * ub[e] + mbar_node[i, ss]
+            nbar = J.T @ xbar
+            if ri is not None:
+                g_rad[ri] += float(((fn(nv, r + h) - fn(nv, r - h)) / (2 * h)) @ xbar)
+            for e, ss in ((0, s), (1, s + 1)):
+                new_zbar[i, ss] += nbar[2 * e:2 * e + 2]
+                if free[i, ss]:
+                    out[e] = ub[e] + mbar_node[i, ss] - nbar[2 * e:2 * e + 2]
+            new_ubar_seg[key] = out
         # u^k of a collision factor is live only if it was active at k-1
         prev_act = tape[k - 1][1] if k > 0 else None
+        prev_seg = tape[k - 1][2] if k > 0 else set()
         ubar_coll = {}
+        ubar_seg = {key: v for key, v in new_ubar_seg.items() if key in prev_seg}
         if prev_act is not None:
             for (s, q), v in new_ubar_coll.items():
                 if prev_act[s, q]:

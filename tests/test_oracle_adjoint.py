@@ -137,3 +137,44 @@ def test_adjoint_with_fixed_end_collision_branches(seed):
     fd = ((W * adjoint.zK(pp, k)).sum() - (W * adjoint.zK(pm, k)).sum()) / (2 * EPS)
     an = sum(float((gi * d[n]).sum()) for gi, n in zip(g, ("start", "goal", "radius", "cost")))
     assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3), (an, fd)
+
+
+def _corridor():
+    """Two agents swapping along a corridor too narrow to pass without the
+    walls' factors becoming active."""
+    return twa.Problem(p=2, eta=4, start=np.array([[-1.2, 0.05], [1.2, -0.05]]),
+                       goal=np.array([[1.2, -0.02], [-1.2, 0.02]]), radius=np.array([0.2, 0.2]),
+                       cost=np.ones((2, 4)),
+                       walls=np.array([[-3.0, 0.36, 3.0, 0.36], [3.0, -0.36, -3.0, -0.36]]),
+                       rho0=1.0, alpha=0.1)
+
+
+def _velocity_limited():
+    return twa.Problem.from_instance(workloads.circle4(), vmax=np.full((4, 4), 0.56),
+                                     vmin=np.full((4, 4), 0.3))
+
+
+@pytest.mark.parametrize("case", ["walls", "velocity"])
+def test_adjoint_through_gated_segment_factors(case):
+    """Wall factors (a corridor swap) and maximum / minimum velocity factors
+    in the gradient: every parameter group perturbed at once, K = 150, no
+    branch flips (collision and segment-factor branch tapes equal)."""
+    prob = _corridor() if case == "walls" else _velocity_limited()
+    k = 150
+    sb = adjoint.seg_branches(prob, k)
+    assert sum(len(x) for x in sb) > 100
+    A0 = _acts(prob, k)
+    W = np.random.default_rng(7).standard_normal((prob.p, prob.eta + 1, 2))
+    g = adjoint.backward(prob, k, W)
+    for seed in (1, 2):
+        r = np.random.default_rng(seed)
+        d = {n: r.standard_normal(getattr(prob, n).shape) for n in ("start", "goal", "radius", "cost")}
+        runs = []
+        for sign in (1, -1):
+            pr = _shift(prob, sign, d)
+            pr.walls, pr.vmax, pr.vmin = prob.walls, prob.vmax, prob.vmin
+            assert np.array_equal(_acts(pr, k), A0) and adjoint.seg_branches(pr, k) == sb
+            runs.append((W * adjoint.zK(pr, k)).sum())
+        fd = (runs[0] - runs[1]) / (2 * EPS)
+        an = sum(float((gi * d[n]).sum()) for gi, n in zip(g, ("start", "goal", "radius", "cost")))
+        assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3), (seed, an, fd)
