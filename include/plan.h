@@ -305,8 +305,11 @@ plan_status plan_set_params(plan_t plan, const float* radius, const float* cost_
  * (p x 2), d_radius (p), d_cost_w (laid out as cost_w).  K must be the K of
  * the last plan_unroll, with no state change in between (else PLAN_EINVAL);
  * the plan is left at iteration K, and plan_backward may be called again
- * with another dL_dz.  Wall factors, PLAN_ADMM, PLAN_U_KEEP and a rho
- * warm-up give PLAN_EUNSUPPORTED.  Enqueued on the plan's stream.
+ * with another dL_dz.  Wall and velocity-limit factors are differentiated
+ * like collision factors; the feasibility problem (PLAN_NO_ENERGY or
+ * plan_set_energy(plan, 0)), the local planner (PLAN_VO), PLAN_ADMM,
+ * PLAN_U_KEEP and a rho warm-up give PLAN_EUNSUPPORTED.  Enqueued on the
+ * plan's stream.
  */
 plan_status plan_unroll(plan_t plan, int K, int checkpoint_every);
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,

@@ -1275,10 +1275,12 @@ plan_status plan_profile(plan_t h, int enable, float* ms, int* iterations) {
 namespace {
 
 __global__ void record_kernel(Dev P, const float2* zk, float2* tz, float4* tukin, uint32_t* tfid,
-                              float4* tucl, float4* tuch, unsigned* tcount) {
+                              float4* tucl, float4* tuch, unsigned* tcount, uint32_t* tsidx,
+                              float4* tsu, unsigned* tscount) {
   const unsigned cnt = *P.work_count;
   const unsigned nz = (unsigned)P.p * (P.eta + 1), nk = (unsigned)P.eta * P.p;
-  const unsigned n = max(max(nz, nk), cnt);
+  const unsigned nseg = (unsigned)(P.nw + P.nv) * nk;
+  const unsigned n = max(max(max(nz, nk), cnt), nseg);
   if (blockIdx.x == 0 && threadIdx.x == 0) *tcount = cnt;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     if (t < nz) tz[t] = zk[t];
@@ -1289,11 +1291,19 @@ __global__ void record_kernel(Dev P, const float2* zk, float2* tz, float4* tukin
       tucl[t] = P.ulo[f];
       tuch[t] = P.uhi[f];
     }
+    if (t < nseg) {  // active walls and velocity limits, compacted (tscount zeroed before)
+      const unsigned i = t % P.p, ws = t / P.p;
+      if ((P.wbits[(size_t)ws * P.nt + i / TILE] >> (i % TILE)) & 1u) {
+        const unsigned at = atomicAdd(tscount, 1u);
+        tsidx[at] = t;
+        tsu[at] = P.uwall[t];
+      }
+    }
   }
 }
 
 __global__ void __launch_bounds__(256) bw_scatter_kernel(AdjDev A) {
-  const unsigned n = (unsigned)(A.eta * A.p) + *A.count;
+  const unsigned n = (unsigned)(A.eta * A.p) + *A.count + *A.scount;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     bw_scatter_item(A, t);
 }
@@ -1304,7 +1314,7 @@ __global__ void bw_node_kernel(AdjDev A) {
 }
 
 __global__ void __launch_bounds__(256) bw_factor_kernel(AdjDev A) {
-  const unsigned n = (unsigned)(A.eta * A.p) + *A.count;
+  const unsigned n = (unsigned)(A.eta * A.p) + *A.count + *A.scount;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     bw_factor_item(A, t);
 }
@@ -1343,10 +1353,18 @@ struct Region { size_t off, bytes; };
 
 std::vector<Region> ck_regions(plan_t h) {
   const size_t zb = (size_t)h->p * (h->eta + 1) * 8, kin = (size_t)h->eta * h->p * 16;
-  return {{h->L.z0, zb}, {h->L.z1, zb}, {h->L.bits, (size_t)h->eta * h->ntp * TILE * 4},
-          {h->L.ulo, h->slots * 16}, {h->L.uhi, h->slots * 16}, {h->L.xlo, h->slots * 16},
-          {h->L.xhi, h->slots * 16}, {h->L.ukin, kin}, {h->L.xkin, kin}, {h->L.wcount, 8},
-          {h->L.res, 16}, {h->L.status, 4}};
+  const size_t ng = (size_t)h->nw + h->nv;  // walls and velocity limits
+  std::vector<Region> r = {
+      {h->L.z0, zb}, {h->L.z1, zb}, {h->L.bits, (size_t)h->eta * h->ntp * TILE * 4},
+      {h->L.ulo, h->slots * 16}, {h->L.uhi, h->slots * 16}, {h->L.xlo, h->slots * 16},
+      {h->L.xhi, h->slots * 16}, {h->L.ukin, kin}, {h->L.xkin, kin}, {h->L.wcount, 8},
+      {h->L.res, 16}, {h->L.status, 4}};
+  if (ng) {
+    r.push_back({h->L.uwall, ng * kin});
+    r.push_back({h->L.xwall, ng * kin});
+    r.push_back({h->L.wbits, ng * h->eta * h->nt * 4});
+  }
+  return r;
 }
 
 // Offsets inside the plan's differentiation block.
@@ -1355,7 +1373,8 @@ struct AdjLayout {
   int nck;
   size_t cap, slot_bytes, tape0;
   size_t t_z, t_ukin, t_count, t_fid, t_ucl, t_uch;  // within one tape slot
-  size_t ubk, ubl, ubh, stamp, zbA, zbB, S, cnt, mbar, gs, gg, gr, gc;
+  size_t t_scount, t_sidx, t_su, scap;
+  size_t ubk, ubl, ubh, stamp, ubs, sstamp, zbA, zbB, S, cnt, mbar, gs, gg, gr, gc;
   size_t total;
 };
 
@@ -1374,6 +1393,10 @@ AdjLayout adj_layout(plan_t h, int K, int C) {
   A.t_fid = take(A.cap * 4);
   A.t_ucl = take(A.cap * 16);
   A.t_uch = take(A.cap * 16);
+  A.scap = std::max<size_t>(1, (size_t)(h->nw + h->nv) * eta * p);
+  A.t_scount = take(4);
+  A.t_sidx = take(A.scap * 4);
+  A.t_su = take(A.scap * 16);
   A.slot_bytes = o;
   o = 0;
   A.ck0 = take(A.ck_bytes * A.nck);
@@ -1382,6 +1405,8 @@ AdjLayout adj_layout(plan_t h, int K, int C) {
   A.ubl = take(h->slots * 16);
   A.ubh = take(h->slots * 16);
   A.stamp = take(h->slots * 4);
+  A.ubs = take(A.scap * 16);
+  A.sstamp = take(A.scap * 4);
   A.zbA = take(p * E1 * 16);
   A.zbB = take(p * E1 * 16);
   A.S = take(p * E1 * 16);
@@ -1412,6 +1437,9 @@ AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char*
   D.tiles = h->at<int2>(h->L.tiles);
   D.radius = h->at<float>(h->L.radius);
   D.cost = h->at<float>(h->L.cost);
+  D.nw = h->nw; D.nv = h->nv; D.vmin_mask = h->vmin_mask;
+  D.walls = h->at<float4>(h->L.walls);
+  D.vlim = h->at<float>(h->L.vlim);
   char* t = h->adj + A.tape0 + (size_t)slot * A.slot_bytes;
   D.z = reinterpret_cast<const float2*>(t + A.t_z);
   D.ukin = reinterpret_cast<const float4*>(t + A.t_ukin);
@@ -1419,6 +1447,11 @@ AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char*
   D.fid = reinterpret_cast<const uint32_t*>(t + A.t_fid);
   D.ucl = reinterpret_cast<const float4*>(t + A.t_ucl);
   D.uch = reinterpret_cast<const float4*>(t + A.t_uch);
+  D.sidx = reinterpret_cast<const uint32_t*>(t + A.t_sidx);
+  D.su = reinterpret_cast<const float4*>(t + A.t_su);
+  D.scount = reinterpret_cast<const unsigned*>(t + A.t_scount);
+  D.ubs = reinterpret_cast<float4*>(h->adj + A.ubs);
+  D.sstamp = reinterpret_cast<int*>(h->adj + A.sstamp);
   D.ubk = reinterpret_cast<float4*>(h->adj + A.ubk);
   D.ubl = reinterpret_cast<float4*>(h->adj + A.ubl);
   D.ubh = reinterpret_cast<float4*>(h->adj + A.ubh);
@@ -1436,12 +1469,12 @@ AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char*
 }
 
 plan_status adj_supported(plan_t h) {
-  if (h->nw) return fail(PLAN_EUNSUPPORTED, "the adjoint does not cover wall factors yet");
   if (h->cfg.flags & (PLAN_ADMM | PLAN_U_KEEP))
     return fail(PLAN_EUNSUPPORTED, "the adjoint covers TWA with the reset rule only");
   if (h->cfg.warm_iters > 0) return fail(PLAN_EUNSUPPORTED, "the adjoint needs a constant rho0");
-  if (h->noenergy || h->nv || h->vo)
-    return fail(PLAN_EUNSUPPORTED, "the adjoint covers the kinetic, collision factors only");
+  if (h->noenergy || h->vo)
+    return fail(PLAN_EUNSUPPORTED, "the adjoint needs the kinetic factors (not the feasibility "
+                                   "problem or the local planner)");
   return PLAN_OK;
 }
 
@@ -1676,6 +1709,7 @@ plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, f
   // adjoint state: u adjoints 0, no stamps, gradients 0, zbar = dL/dz^K
   CK(cudaMemsetAsync(h->adj + A.ubk, 0, (size_t)h->eta * p * 16, h->stream));
   CK(cudaMemsetAsync(h->adj + A.stamp, 0xff, h->slots * 4, h->stream));
+  CK(cudaMemsetAsync(h->adj + A.sstamp, 0xff, A.scap * 4, h->stream));
   CK(cudaMemsetAsync(h->adj + A.S, 0, nodes * 16, h->stream));
   CK(cudaMemsetAsync(h->adj + A.cnt, 0, nodes * 4, h->stream));
   CK(cudaMemsetAsync(h->adj + A.gs, 0, A.gc + p * h->eta * 8 - A.gs, h->stream));
@@ -1696,10 +1730,13 @@ plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, f
       const float2* zk = h->cur ? h->at<float2>(h->L.z1) : h->at<float2>(h->L.z0);
       if ((st = run_iteration(h)) != PLAN_OK) return st;
       char* t = h->adj + A.tape0 + (size_t)(k - c0) * A.slot_bytes;
+      CK(cudaMemsetAsync(t + A.t_scount, 0, 4, h->stream));
       record_kernel<<<h->prox_grid, 256, 0, h->stream>>>(
           h->dev(k), zk, reinterpret_cast<float2*>(t + A.t_z), reinterpret_cast<float4*>(t + A.t_ukin),
           reinterpret_cast<uint32_t*>(t + A.t_fid), reinterpret_cast<float4*>(t + A.t_ucl),
-          reinterpret_cast<float4*>(t + A.t_uch), reinterpret_cast<unsigned*>(t + A.t_count));
+          reinterpret_cast<float4*>(t + A.t_uch), reinterpret_cast<unsigned*>(t + A.t_count),
+          reinterpret_cast<uint32_t*>(t + A.t_sidx), reinterpret_cast<float4*>(t + A.t_su),
+          reinterpret_cast<unsigned*>(t + A.t_scount));
       CK(cudaGetLastError());
     }
     // the adjoint steps of the segment, last iteration first

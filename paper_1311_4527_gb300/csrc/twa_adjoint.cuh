@@ -166,4 +166,107 @@ TWA_DEV void energy_vjp(float2 n_lo, float2 n_hi, float rho, bool pin_lo, bool p
   cbar = 2.f * rho * inv * inv * dot(xbl - xbh, n_hi - n_lo);
 }
 
+// ---------------------------------------------------------------------------
+// Walls (Appendix D's capsule) and velocity limits (Appendices F, G)
+// ---------------------------------------------------------------------------
+// For a fixed direction n the capsule's support is h(n) = <c, n> + r with c
+// the end circle that attains the max, so each end's output is the disk's
+// with w - c in place of w and R = r; dphi follows the branch as for the
+// disk, with the branch's own circle (a kink direction does not move).
+TWA_DEV float2 active_circle(float2 c0, float2 c1, float2 n) {
+  return dot(c0, n) >= dot(c1, n) ? c0 : c1;
+}
+
+// Adjoint of capsule_prox_free (wl = wh = w) -> (vl, vh): abar, bbar, rbar.
+TWA_DEV void capsule_free_vjp(float2 a, float2 b, float w, float2 c0, float2 c1, float r,
+                              float2 vlbar, float2 vhbar, float2& abar, float2& bbar,
+                              float& rbar) {
+  int tag;
+  const float2 n = capsule_dir_free(a, b, w, w, c0, c1, r, tag);
+  const float2 cs = active_circle(c0, c1, n);
+  float phib = 0.f;
+  rbar = 0.f;
+  end_vjp(a - cs, vlbar, n, r, abar, rbar, phib);
+  end_vjp(b - cs, vhbar, n, r, bbar, rbar, phib);
+  if (tag < 2) return;  // the fallback or a kink: n does not move
+  const int ci = (tag - 2) >> 2, kind = (tag - 2) & 3;
+  const float2 cc = ci ? c1 : c0;
+  if (kind == 0) stationary_vjp(a - cc, b - cc, w, w, r, n, phib, abar, bbar, rbar);
+  else if (kind == 1) inner_vjp(a - cc, n, phib, abar);
+  else inner_vjp(b - cc, n, phib, bbar);
+}
+
+// Adjoint of capsule_prox_pinned(q, w) -> v.
+TWA_DEV void capsule_pinned_vjp(float2 q, float2 w, float2 c0, float2 c1, float r, float2 vbar,
+                                float2& qbar, float2& wbar, float& rbar) {
+  float2 n;
+  int tag;
+  qbar = mk(0.f, 0.f);
+  rbar = 0.f;
+  if (!capsule_dir_pinned(q, w, c0, c1, r, n, tag)) { wbar = vbar; return; }
+  const float2 cs = active_circle(c0, c1, n);
+  float phib = 0.f;
+  end_vjp(w - cs, vbar, n, r, wbar, rbar, phib);
+  if (tag < 2) return;
+  const int ci = (tag - 2) >> 2, kind = (tag - 2) & 3;
+  const float2 cc = ci ? c1 : c0;
+  if (kind == 0) tangent_vjp(q - cc, n, phib, qbar, rbar);
+  else inner_vjp(w - cc, n, phib, wbar);
+}
+
+// Adjoint of the wall factor's minimizer for classes 1 (rho0) / 2 (fixed
+// end): x = n at a fixed end.  xbar at a fixed end is 0 by the caller.
+TWA_DEV void wall_vjp(float2 nl, float2 nh, bool pin_lo, bool pin_hi, float2 c0, float2 c1,
+                      float r, float rho, float2 xbl, float2 xbh, float2& nbl, float2& nbh,
+                      float& rbar) {
+  rbar = 0.f;
+  nbl = xbl; nbh = xbh;
+  if (pin_lo && pin_hi) return;
+  if (pin_lo) {
+    float2 qb, wb;
+    capsule_pinned_vjp(nl, nh, c0, c1, r, xbh, qb, wb, rbar);
+    nbl = nbl + qb; nbh = wb;
+  } else if (pin_hi) {
+    float2 qb, wb;
+    capsule_pinned_vjp(nh, nl, c0, c1, r, xbl, qb, wb, rbar);
+    nbh = nbh + qb; nbl = wb;
+  } else {
+    capsule_free_vjp(nl, nh, 0.5f * rho, c0, c1, r, xbl, xbh, nbl, nbh, rbar);
+  }
+}
+
+// Adjoint of velocity_prox for classes 1 / 2 (equal finite weights keep the
+// midpoint and set x_lo - x_hi = C u, u = (n_lo - n_hi) / L; a fixed end
+// stays and the other end is C u from it).
+TWA_DEV void velocity_vjp(float2 nl, float2 nh, bool pin_lo, bool pin_hi, float C, float2 xbl,
+                          float2 xbh, float2& nbl, float2& nbh) {
+  nbl = xbl; nbh = xbh;
+  if (pin_lo && pin_hi) return;
+  const float2 d = nl - nh;
+  const float L = hypotf(d.x, d.y);
+  // du = (I - u u^T) dd / L; u is fixed when the ends coincide
+  const float2 u = L > 0.f ? (1.f / L) * d : mk(-1.f, 0.f);
+  auto proj = [&](float2 g) {  // (I - u u^T) g / L
+    if (!(L > 0.f)) return mk(0.f, 0.f);
+    const float gu = dot(g, u);
+    return (1.f / L) * (g - gu * u);
+  };
+  if (pin_lo) {  // x_lo = n_lo, x_hi = n_lo - C u
+    const float2 pd = (-C) * proj(xbh);
+    nbl = xbl + xbh + pd;
+    nbh = -1.f * pd;
+    return;
+  }
+  if (pin_hi) {  // x_hi = n_hi, x_lo = n_hi + C u
+    const float2 pd = C * proj(xbl);
+    nbh = xbh + xbl - pd;
+    nbl = pd;
+    return;
+  }
+  const float2 mb = 0.5f * (xbl + xbh);   // d/dn of the midpoint
+  const float2 pd = (0.5f * C) * proj(xbl - xbh);
+  nbl = mb + pd;
+  nbh = mb - pd;
+}
+
 }  // namespace twa

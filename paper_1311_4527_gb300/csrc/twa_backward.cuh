@@ -14,7 +14,8 @@
 // At fixed nodes z is the start or goal, x is unused and u stays 0.  A
 // collision edge's u^{k+1} matters only if the factor is active in both k and
 // k+1 (else it is reset or unused), so its adjoint is kept with the iteration
-// that wrote it (stamp) and read as 0 unless the stamp is k + 1.
+// that wrote it (stamp) and read as 0 unless the stamp is k + 1.  Wall and
+// velocity-limit factors are gated the same way and carried alike.
 //
 // Sums into nodes use FP64 atomics (order-dependent in the last bits only).
 #pragma once
@@ -29,6 +30,10 @@ struct AdjDev {
   const int2* tiles;
   const float* radius;
   const float* cost;        // [p][eta] c_{i,s}
+  int nw, nv;               // wall kinds, then velocity-limit kinds (gated segment factors)
+  unsigned vmin_mask;       // velocity kind v is a minimum
+  const float4* walls;      // [nw]
+  const float* vlim;        // [nv][p][eta]
   // the tape of iteration k
   const float2* z;          // z^k, [p][eta+1]
   const float4* ukin;       // u^k of the kinetic edges, [eta][p]
@@ -36,11 +41,16 @@ struct AdjDev {
   const float4* ucl;        // their u^k at the lower break-point: (u_i, u_j)
   const float4* uch;        // ... at the upper break-point
   const unsigned* count;    // how many
+  const uint32_t* sidx;     // gated segment factors active in iteration k: (g eta + s) p + i
+  const float4* su;         // their u^k (lower, upper)
+  const unsigned* scount;   // how many
   // adjoint state
   float4* ubk;              // kinetic u adjoints, [eta][p]: of u^{k+1} in, u^k out
   float4* ubl;              // collision u adjoints by slot (lower, upper)
   float4* ubh;
   int* stamp;               // the iteration whose u adjoint a slot holds
+  float4* ubs;              // gated segment factor u adjoints, [(nw + nv) eta p]
+  int* sstamp;              // ... and the iteration that wrote them
   const double2* zb_in;     // dL/dz^{k+1}
   double2* zb_out;          // dL/dz^k, accumulated
   double2* S;               // alpha * sum of u adjoints per node
@@ -75,6 +85,15 @@ __device__ __forceinline__ void scatter_edge(const AdjDev& A, int i, int s, floa
 // Pass 1: alpha * u adjoints and edge counts into the nodes.
 __device__ __forceinline__ void bw_scatter_item(const AdjDev& A, unsigned t) {
   const unsigned nkin = (unsigned)(A.eta * A.p);
+  const unsigned ncoll = *A.count;
+  if (t >= nkin + ncoll) {  // a gated segment factor
+    const uint32_t g = A.sidx[t - nkin - ncoll];
+    const int i = (int)(g % A.p), s = (int)((g / A.p) % A.eta);
+    const float4 ub = (A.sstamp[g] == A.k + 1) ? A.ubs[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s > 0) scatter_edge(A, i, s, lo2(ub));
+    if (s + 1 < A.eta) scatter_edge(A, i, s + 1, hi2(ub));
+    return;
+  }
   if (t < nkin) {
     const int s = (int)(t / A.p), i = (int)(t - (unsigned)s * A.p);
     const float4 ub = A.ubk[t];
@@ -124,10 +143,41 @@ __device__ __forceinline__ float2 edge_ubar(bool fixed, float2 ub, float2 mb, fl
   return fixed ? mk(0.f, 0.f) : mk(ub.x + mb.x - nb.x, ub.y + mb.y - nb.y);
 }
 
+// Pass 3 for a wall or velocity-limit factor (gated like a collision factor).
+__device__ __forceinline__ void bw_seg_item(const AdjDev& A, unsigned w) {
+  const int E1 = A.eta + 1;
+  const uint32_t g = A.sidx[w];
+  const int i = (int)(g % A.p), s = (int)((g / A.p) % A.eta);
+  const int kind = (int)(g / ((uint32_t)A.p * A.eta));
+  const bool pin_lo = (s == 0), pin_hi = (s == A.eta - 1);
+  const float4 u = A.su[w];
+  const float2 nl = A.z[(size_t)i * E1 + s] - lo2(u), nh = A.z[(size_t)i * E1 + s + 1] - hi2(u);
+  const float4 ub = (A.sstamp[g] == A.k + 1) ? A.ubs[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 ml, mh;
+  const float2 xl = edge_xbar(A, pin_lo, i, s, lo2(ub), ml);
+  const float2 xh = edge_xbar(A, pin_hi, i, s + 1, hi2(ub), mh);
+  float2 bl, bh;
+  if (kind < A.nw) {
+    const float4 W = A.walls[kind];
+    float rb;
+    wall_vjp(nl, nh, pin_lo, pin_hi, mk(W.x, W.y), mk(W.z, W.w), A.radius[i], A.rho, xl, xh, bl, bh, rb);
+    atomicAdd(A.g_r + i, (double)rb);
+  } else {
+    const int v = kind - A.nw;
+    velocity_vjp(nl, nh, pin_lo, pin_hi, A.vlim[((size_t)v * A.p + i) * A.eta + s], xl, xh, bl, bh);
+  }
+  atomic_add2(A.zb_out + (size_t)i * E1 + s, bl);
+  atomic_add2(A.zb_out + (size_t)i * E1 + s + 1, bh);
+  A.ubs[g] = pack(edge_ubar(pin_lo, lo2(ub), ml, bl), edge_ubar(pin_hi, hi2(ub), mh, bh));
+  A.sstamp[g] = A.k;
+}
+
 // Pass 3: the adjoint of one factor's minimizer.
 __device__ __forceinline__ void bw_factor_item(const AdjDev& A, unsigned t) {
   const int E1 = A.eta + 1;
   const unsigned nkin = (unsigned)(A.eta * A.p);
+  const unsigned ncoll = *A.count;
+  if (t >= nkin + ncoll) { bw_seg_item(A, t - nkin - ncoll); return; }
   if (t < nkin) {
     const int s = (int)(t / A.p), i = (int)(t - (unsigned)s * A.p);
     const bool pin_lo = (s == 0), pin_hi = (s == A.eta - 1);

@@ -390,35 +390,47 @@ TWA_DEV float capsule_E(float2 a, float2 b, float wl, float wh, float2 c0, float
   return 0.5f * wl * ga * ga + 0.5f * wh * gb * gb;
 }
 
-TWA_NOINLINE void capsule_prox_free(float2 a, float2 b, float wl, float wh, float2 c0,
-                                               float2 c1, float r, float2& vl, float2& vh) {
+// Kinds of winning capsule direction (Best::tag): 0 the (1, 0) fallback,
+// 1 a kink, and per end circle ci: 2 + 4 ci a stationary point of its
+// both-stretched piece (free) or a tangent from the fixed end (pinned),
+// 3 + 4 ci the single-hinge direction of the lower (free) / free (pinned)
+// end, 4 + 4 ci that of the upper end (free).
+TWA_DEV float2 capsule_dir_free(float2 a, float2 b, float wl, float wh, float2 c0, float2 c1,
+                                float r, int& tag) {
   Best best;
   best.init();
-  best.offer(mk(1.f, 0.f), capsule_E(a, b, wl, wh, c0, c1, r, mk(1.f, 0.f)));
+  best.offer(mk(1.f, 0.f), capsule_E(a, b, wl, wh, c0, c1, r, mk(1.f, 0.f)), 0);
   float2 e = c1 - c0;
   if (e.x != 0.f || e.y != 0.f) {  // kinks: both end circles give the same support
     float2 k0 = normalized(perp(e));
-    best.offer(k0, capsule_E(a, b, wl, wh, c0, c1, r, k0));
-    best.offer(-k0, capsule_E(a, b, wl, wh, c0, c1, r, -k0));
+    best.offer(k0, capsule_E(a, b, wl, wh, c0, c1, r, k0), 1);
+    best.offer(-k0, capsule_E(a, b, wl, wh, c0, c1, r, -k0), 1);
   }
   for (int ci = 0; ci < 2; ++ci) {
     float2 cc = ci ? c1 : c0;
     float2 ac = a - cc, bc = b - cc;
     float2 t[4];
     int nt = trs_global(ac, bc, wl, wh, r, t);
-    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]));
+    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
     nt = trs_local(ac, bc, wl, wh, r, t);
-    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]));
+    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
     if (dot(ac, ac) > 0.f) {
       float2 n = normalized(ac);
-      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n));
+      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n), 3 + 4 * ci);
     }
     if (dot(bc, bc) > 0.f) {
       float2 n = normalized(bc);
-      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n));
+      best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n), 4 + 4 * ci);
     }
   }
-  float2 n = best.n;
+  tag = best.tag;
+  return best.n;
+}
+
+TWA_NOINLINE void capsule_prox_free(float2 a, float2 b, float wl, float wh, float2 c0,
+                                               float2 c1, float r, float2& vl, float2& vh) {
+  int tag;
+  float2 n = capsule_dir_free(a, b, wl, wh, c0, c1, r, tag);
   float h = capsule_h(c0, c1, r, n);
   vl = a + fmaxf(h - dot(a, n), 0.f) * n;
   vh = b + fmaxf(h - dot(b, n), 0.f) * n;
@@ -428,9 +440,10 @@ TWA_NOINLINE void capsule_prox_free(float2 a, float2 b, float wl, float wh, floa
 // from q to both end circles, the kinks, and the single-hinge directions;
 // only directions that still separate q from the capsule are kept.
 // Returns false if no candidate separates q (q inside the capsule).
-TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, float r,
-                                                 float2& vw) {
+TWA_DEV bool capsule_dir_pinned(float2 q, float2 w, float2 c0, float2 c1, float r, float2& dir,
+                                int& tag) {
   float2 cand[8];
+  int ctag[8];
   int nc = 0;
   for (int ci = 0; ci < 2; ++ci) {
     float2 cc = ci ? c1 : c0;
@@ -438,17 +451,17 @@ TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, 
     if (dot(qc, qc) >= r * r) {
       float2 t0, t1;
       tangent_normals(qc, r, t0, t1);
-      cand[nc++] = normalized(t0);
-      cand[nc++] = normalized(t1);
+      ctag[nc] = 2 + 4 * ci; cand[nc++] = normalized(t0);
+      ctag[nc] = 2 + 4 * ci; cand[nc++] = normalized(t1);
     }
     float2 wc = w - cc;
-    if (dot(wc, wc) > 0.f) cand[nc++] = normalized(wc);
+    if (dot(wc, wc) > 0.f) { ctag[nc] = 3 + 4 * ci; cand[nc++] = normalized(wc); }
   }
   float2 e = c1 - c0;
   if (e.x != 0.f || e.y != 0.f) {
     float2 k0 = normalized(perp(e));
-    cand[nc++] = k0;
-    cand[nc++] = -k0;
+    ctag[nc] = 1; cand[nc++] = k0;
+    ctag[nc] = 1; cand[nc++] = -k0;
   }
   float scale = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)),
                       fmaxf(fmaxf(fabsf(c0.x), fabsf(c0.y)), fmaxf(fabsf(c1.x), fabsf(c1.y)))) + r;
@@ -460,13 +473,22 @@ TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, 
     float h = capsule_h(c0, c1, r, cand[k]);
     if (dot(q, cand[k]) - h >= -tol) {
       float g = fmaxf(h - dot(w, cand[k]), 0.f);
-      best.offer(cand[k], 0.5f * g * g);
+      best.offer(cand[k], 0.5f * g * g, ctag[k]);
       any = true;
     }
   }
-  if (!any) { vw = w; return false; }
-  float h = capsule_h(c0, c1, r, best.n);
-  vw = w + fmaxf(h - dot(w, best.n), 0.f) * best.n;
+  dir = best.n;
+  tag = best.tag;
+  return any;
+}
+
+TWA_NOINLINE bool capsule_prox_pinned(float2 q, float2 w, float2 c0, float2 c1, float r,
+                                                 float2& vw) {
+  float2 n;
+  int tag;
+  if (!capsule_dir_pinned(q, w, c0, c1, r, n, tag)) { vw = w; return false; }
+  float h = capsule_h(c0, c1, r, n);
+  vw = w + fmaxf(h - dot(w, n), 0.f) * n;
   return true;
 }
 

@@ -81,6 +81,25 @@ void h_energy_vjp(const float* nl, const float* nh, float rho, int pin_lo, int p
   out[0] = bl.x; out[1] = bl.y; out[2] = bh.x; out[3] = bh.y; out[4] = cb;
 }
 
+// Wall factor adjoint (classes rho0 / fixed ends): n 4 floats (lo, hi), wall
+// 4 floats, xbar 4 floats; out: nbar (4) then the adjoint of r.
+void h_wall_vjp(const float* n, int pin_lo, int pin_hi, const float* wall, float r, float rho,
+                const float* xb, float* out) {
+  float2 bl, bh;
+  float rb;
+  wall_vjp(mk(n[0], n[1]), mk(n[2], n[3]), pin_lo != 0, pin_hi != 0, mk(wall[0], wall[1]),
+           mk(wall[2], wall[3]), r, rho, mk(xb[0], xb[1]), mk(xb[2], xb[3]), bl, bh, rb);
+  out[0] = bl.x; out[1] = bl.y; out[2] = bh.x; out[3] = bh.y; out[4] = rb;
+}
+
+// Velocity-limit factor adjoint: out nbar (4).
+void h_velocity_vjp(const float* n, int pin_lo, int pin_hi, float C, const float* xb, float* out) {
+  float2 bl, bh;
+  velocity_vjp(mk(n[0], n[1]), mk(n[2], n[3]), pin_lo != 0, pin_hi != 0, C, mk(xb[0], xb[1]),
+               mk(xb[2], xb[3]), bl, bh);
+  out[0] = bl.x; out[1] = bl.y; out[2] = bh.x; out[3] = bh.y;
+}
+
 // Winning candidate kind of the free disk minimizer (DiskTag).
 int h_disk_tag(const float* a, const float* b, float wl, float wh, float R) {
   int tag;

@@ -21,7 +21,8 @@ TOL = 2e-4
 def _planner(prob, **kw):
     import paper_1311_4527_gb300 as pk
     return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=prob.cost,
-                      rho0=prob.rho0, alpha=prob.alpha, **kw)
+                      walls=prob.walls if prob.n_walls else None, rho0=prob.rho0,
+                      alpha=prob.alpha, vmax=prob.vmax, vmin=prob.vmin, **kw)
 
 
 def _gpu_grads(pl, K, W, every=0):
@@ -57,10 +58,21 @@ def _pinned_case():
                        walls=np.zeros((0, 4)), rho0=1.0, alpha=0.1)
 
 
-@pytest.mark.parametrize("case", ["circle4", "pinned3"])
+def _corridor():
+    return twa.Problem(p=2, eta=4, start=np.array([[-1.2, 0.05], [1.2, -0.05]]),
+                       goal=np.array([[1.2, -0.02], [-1.2, 0.02]]), radius=np.array([0.2, 0.2]),
+                       cost=np.ones((2, 4)),
+                       walls=np.array([[-3.0, 0.36, 3.0, 0.36], [3.0, -0.36, -3.0, -0.36]]),
+                       rho0=1.0, alpha=0.1)
+
+
+@pytest.mark.parametrize("case", ["circle4", "pinned3", "walls", "velocity"])
 def test_adjoint_matches_the_oracle_adjoint(case):
-    prob = twa.Problem.from_instance(workloads.circle4()) if case == "circle4" else _pinned_case()
-    K = 200 if case == "circle4" else 120
+    prob = {"circle4": lambda: twa.Problem.from_instance(workloads.circle4()),
+            "pinned3": _pinned_case, "walls": _corridor,
+            "velocity": lambda: twa.Problem.from_instance(
+                workloads.circle4(), vmax=np.full((4, 4), 0.56), vmin=np.full((4, 4), 0.3))}[case]()
+    K = {"circle4": 200, "pinned3": 120, "walls": 150, "velocity": 150}[case]
     assert _activity_matches(prob, K)
     W = np.random.default_rng(2024).standard_normal((prob.p, prob.eta + 1, 2))
     ref = adjoint.backward(prob, K, W)
@@ -128,11 +140,11 @@ def test_errors():
     with pytest.raises(pk.PlanError):
         pl.backward(torch.zeros((prob.p, prob.eta + 1, 2)))
     pl.close()
-    walled = pk.Planner.from_instance(workloads.small_square(40, 4, seed=1))
+    feas = pk.Planner.from_instance(workloads.circle4(), energy=False)
     with pytest.raises(pk.PlanError) as e:
-        walled.unroll(3)
+        feas.unroll(3)
     assert e.value.status == "PLAN_EUNSUPPORTED"
-    walled.close()
+    feas.close()
 
 
 @pytest.fixture(scope="module")

@@ -262,3 +262,74 @@ def test_energy_adjoint_matches_oracle_differences(H):
             H.h_energy_vjp(p1, p2, ctypes.c_float(rho), pl, ph, ctypes.c_float(c), px, out.ctypes.data_as(FP))
             ref = np.concatenate([ref_n, [ref_c]])
             assert np.abs(out - ref).max() <= 1e-5 * (1 + np.abs(ref).max()), (pl, ph, out, ref)
+
+
+def test_wall_adjoint_matches_oracle_differences(H):
+    """The FP32 adjoint of the wall minimizer (capsule, free and with either
+    end fixed) against J^T xbar of the FP64 oracle wall minimizer by central
+    differences; near-ties and branch boundaries within the step skipped."""
+    rng = np.random.default_rng(33)
+    wall = np.array([-0.6, 0.1, 0.7, -0.2])
+    errs = {0: [], 1: [], 2: []}
+    for trial in range(1500):
+        pin = trial % 3
+        r = float(np.float32(rng.uniform(0.2, 0.5)))
+        n = _f32(rng.normal(size=4) * 0.8)
+        if prox.dist_segment_segment(n[:2], n[2:], wall[:2], wall[2:]) >= r:
+            continue
+        if pin == 1 and prox.dist_point_segment(n[:2], wall[:2], wall[2:]) < r * 1.01:
+            continue
+        if pin == 2 and prox.dist_point_segment(n[2:], wall[:2], wall[2:]) < r * 1.01:
+            continue
+        wl = math.inf if pin == 1 else 1.0
+        wh = math.inf if pin == 2 else 1.0
+        if prox.wall_prox(n[:2], n[2:], wl, wh, wall[:2], wall[2:], r, want_gap=True)[3] < 1e-3:
+            continue
+        xb = rng.normal(size=4)
+        if pin == 1:
+            xb[:2] = 0.0
+        if pin == 2:
+            xb[2:] = 0.0
+        f = lambda v, rr=r: np.concatenate(prox.wall_prox(v[:2], v[2:], wl, wh, wall[:2], wall[2:], rr)[:2])
+        r1, r2 = _jt(f, n, xb, 1e-6), _jt(f, n, xb, 1e-5)
+        if np.abs(r1 - r2).max() > 1e-5 * (1 + np.abs(r1).max()):
+            continue
+        dr = float(xb @ (f(n, r + 1e-6) - f(n, r - 1e-6))) / 2e-6
+        ref = np.concatenate([r1, [dr]])
+        N, pn = _a(n)
+        Wl, pw = _a(wall)
+        X, px = _a(xb)
+        out = np.zeros(5, np.float32)
+        H.h_wall_vjp(pn, int(pin == 1), int(pin == 2), pw, ctypes.c_float(r), ctypes.c_float(1.0), px,
+                     out.ctypes.data_as(FP))
+        errs[pin].append(np.abs(out - ref).max() / (1 + np.abs(ref).max()))
+    for pin, e in errs.items():
+        e = np.asarray(e)
+        assert e.size > 100, (pin, e.size)
+        assert np.median(e) < 1e-6 and e.max() < 5e-4, (pin, np.median(e), e.max())
+
+
+def test_velocity_adjoint_matches_oracle_differences(H):
+    rng = np.random.default_rng(34)
+    for kind in ("max", "min"):
+        for _ in range(200):
+            n = _f32(rng.normal(size=4))
+            L = float(np.linalg.norm(n[:2] - n[2:]))
+            C = float(np.float32(L * (0.6 if kind == "max" else 1.6)))
+            xb = rng.normal(size=4)
+            for pin in (0, 1, 2):
+                wl = math.inf if pin == 1 else 1.0
+                wh = math.inf if pin == 2 else 1.0
+                x = xb.copy()
+                if pin == 1:
+                    x[:2] = 0.0
+                if pin == 2:
+                    x[2:] = 0.0
+                f = lambda v: np.concatenate(prox.velocity_prox(v[:2], v[2:], wl, wh, C, kind)[:2])
+                ref = _jt(f, n, x, 1e-6)
+                N, pn = _a(n)
+                X, px = _a(x)
+                out = np.zeros(4, np.float32)
+                H.h_velocity_vjp(pn, int(pin == 1), int(pin == 2), ctypes.c_float(C), px,
+                                 out.ctypes.data_as(FP))
+                assert np.abs(out - ref).max() <= 2e-5 * (1 + np.abs(ref).max()), (kind, pin, out, ref)
