@@ -306,10 +306,11 @@ plan_status plan_set_params(plan_t plan, const float* radius, const float* cost_
  * the last plan_unroll, with no state change in between (else PLAN_EINVAL);
  * the plan is left at iteration K, and plan_backward may be called again
  * with another dL_dz.  Wall and velocity-limit factors are differentiated
- * like collision factors; the feasibility problem (PLAN_NO_ENERGY or
- * plan_set_energy(plan, 0)), the local planner (PLAN_VO), PLAN_ADMM,
- * PLAN_U_KEEP and a rho warm-up give PLAN_EUNSUPPORTED.  Enqueued on the
- * plan's stream.
+ * like collision factors, and a PLAN_VO plan gives the gradient of one
+ * local-planner epoch (start = x(0), goal = x_ref, cost_w = C'); the
+ * feasibility problem (PLAN_NO_ENERGY or plan_set_energy(plan, 0)),
+ * PLAN_ADMM, PLAN_U_KEEP and a rho warm-up give PLAN_EUNSUPPORTED.
+ * Enqueued on the plan's stream.
  */
 plan_status plan_unroll(plan_t plan, int K, int checkpoint_every);
 plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start, float* d_goal,

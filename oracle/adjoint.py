@@ -14,9 +14,10 @@ minimizers (``oracle.prox``) in FP64, so this reference is independent of
 any analytic derivation; the differences use a step of 1e-6 of the problem
 scale, small enough not to change the minimizer's branch in the cases the
 tests use.  Wall factors and velocity-limit factors are gated like the
-collision factors (their u lives only while they stay active).  The
-feasibility mode, standard-ADMM mode, kept u, the rho warm-up and the local
-planner are not covered.
+collision factors (their u lives only while they stay active).  The local
+planner's epoch (``vo``) is the same recursion on its graph.  The
+feasibility mode, standard-ADMM mode, kept u and the rho warm-up are not
+covered.
 """
 from __future__ import annotations
 
@@ -52,8 +53,7 @@ def record(prob: twa.Problem, K: int):
     """Forward K iterations, keeping what the adjoint needs per iteration:
     the state at the start of the iteration and which collision factors and
     gated segment factors (walls, velocity limits) were active."""
-    assert (prob.energy and not prob.admm and not prob.u_keep and prob.warm_iters == 0
-            and not prob.vo)
+    assert prob.energy and not prob.admm and not prob.u_keep and prob.warm_iters == 0
     st = twa.initial_state(prob)
     tape = []
     for _ in range(K):
@@ -148,6 +148,8 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
     free = np.ones((p, eta + 1), dtype=bool)
     free[:, 0] = False
     free[:, eta] = False
+    # the local planner has its kinetic factor on the second segment only
+    kin_segs = [1] if prob.vo else list(range(eta))
 
     for k in range(K - 1, -1, -1):
         st, act, seg = tape[k]
@@ -158,7 +160,7 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
         # step 7: u^{k+1} = u + alpha (x - z^{k+1}) on active edges at free nodes
         zhat = zbar.copy()
         cnt = np.zeros((p, eta + 1))
-        for s in range(eta):
+        for s in kin_segs:
             cnt[:, s] += 1.0
             cnt[:, s + 1] += 1.0
             zhat[:, s] -= alpha * ubar_kin[s, :, 0] * free[:, s, None]
@@ -183,7 +185,7 @@ def backward(prob: twa.Problem, K: int, dz_K: np.ndarray, h: float | None = None
         new_ubar_kin = np.zeros_like(ubar_kin)
         new_ubar_coll = {}
         # kinetic factors
-        for s in range(eta):
+        for s in kin_segs:
             for i in range(p):
                 wl = INF if s == 0 else rho
                 wh = INF if s + 1 == eta else rho

@@ -1438,6 +1438,7 @@ AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char*
   D.radius = h->at<float>(h->L.radius);
   D.cost = h->at<float>(h->L.cost);
   D.nw = h->nw; D.nv = h->nv; D.vmin_mask = h->vmin_mask;
+  D.vo = h->vo ? 1 : 0;
   D.walls = h->at<float4>(h->L.walls);
   D.vlim = h->at<float>(h->L.vlim);
   char* t = h->adj + A.tape0 + (size_t)slot * A.slot_bytes;
@@ -1472,9 +1473,9 @@ plan_status adj_supported(plan_t h) {
   if (h->cfg.flags & (PLAN_ADMM | PLAN_U_KEEP))
     return fail(PLAN_EUNSUPPORTED, "the adjoint covers TWA with the reset rule only");
   if (h->cfg.warm_iters > 0) return fail(PLAN_EUNSUPPORTED, "the adjoint needs a constant rho0");
-  if (h->noenergy || h->vo)
+  if (h->noenergy)
     return fail(PLAN_EUNSUPPORTED, "the adjoint needs the kinetic factors (not the feasibility "
-                                   "problem or the local planner)");
+                                   "problem)");
   return PLAN_OK;
 }
 
@@ -1750,7 +1751,7 @@ plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, f
     }
   }
   const AdjDev D = adj_dev(h, A, 0, 0, zb_in, zb_out);
-  const double norm = (h->cfg.flags & PLAN_COST_UNNORM) ? 1.0 : 1.0 / ((double)p * h->eta);
+  const double norm = (h->cfg.flags & (PLAN_COST_UNNORM | PLAN_VO)) ? 1.0 : 1.0 / ((double)p * h->eta);
   bw_final_kernel<<<(unsigned)((p + 127) / 128), 128, 0, h->stream>>>(
       D, reinterpret_cast<const double2*>(zb_in), norm, (h->cfg.flags & PLAN_COST_PER_SEGMENT) ? 1 : 0,
       reinterpret_cast<float2*>(d_start), reinterpret_cast<float2*>(d_goal), d_radius, d_cost_w);

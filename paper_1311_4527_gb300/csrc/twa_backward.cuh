@@ -31,6 +31,7 @@ struct AdjDev {
   const float* radius;
   const float* cost;        // [p][eta] c_{i,s}
   int nw, nv;               // wall kinds, then velocity-limit kinds (gated segment factors)
+  int vo;                   // local planner epoch: no kinetic factor on segment 0
   unsigned vmin_mask;       // velocity kind v is a minimum
   const float4* walls;      // [nw]
   const float* vlim;        // [nv][p][eta]
@@ -96,6 +97,7 @@ __device__ __forceinline__ void bw_scatter_item(const AdjDev& A, unsigned t) {
   }
   if (t < nkin) {
     const int s = (int)(t / A.p), i = (int)(t - (unsigned)s * A.p);
+    if (A.vo && s == 0) return;
     const float4 ub = A.ubk[t];
     if (s > 0) scatter_edge(A, i, s, lo2(ub));
     if (s + 1 < A.eta) scatter_edge(A, i, s + 1, hi2(ub));
@@ -180,6 +182,7 @@ __device__ __forceinline__ void bw_factor_item(const AdjDev& A, unsigned t) {
   if (t >= nkin + ncoll) { bw_seg_item(A, t - nkin - ncoll); return; }
   if (t < nkin) {
     const int s = (int)(t / A.p), i = (int)(t - (unsigned)s * A.p);
+    if (A.vo && s == 0) return;
     const bool pin_lo = (s == 0), pin_hi = (s == A.eta - 1);
     const float4 u = A.ukin[t];
     const float2 nl = A.z[(size_t)i * E1 + s] - lo2(u), nh = A.z[(size_t)i * E1 + s + 1] - hi2(u);

@@ -22,7 +22,7 @@ def _planner(prob, **kw):
     import paper_1311_4527_gb300 as pk
     return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=prob.cost,
                       walls=prob.walls if prob.n_walls else None, rho0=prob.rho0,
-                      alpha=prob.alpha, vmax=prob.vmax, vmin=prob.vmin, **kw)
+                      alpha=prob.alpha, vmax=prob.vmax, vmin=prob.vmin, vo=prob.vo, **kw)
 
 
 def _gpu_grads(pl, K, W, every=0):
@@ -66,13 +66,22 @@ def _corridor():
                        rho0=1.0, alpha=0.1)
 
 
-@pytest.mark.parametrize("case", ["circle4", "pinned3", "walls", "velocity"])
+def _vo_epoch():
+    from oracle import vo
+    x0 = np.array([[-0.5, 0.01], [0.5, -0.01], [0.05, 0.6]])
+    dest = np.array([[2.0, 0.0], [-2.0, 0.0], [0.0, -2.0]])
+    return vo.problem(x0, vo.targets(x0, dest, 0.8), np.array([0.2, 0.2, 0.15]),
+                      np.array([1.0, 1.001, 1.002]), rho0=10.0)
+
+
+@pytest.mark.parametrize("case", ["circle4", "pinned3", "walls", "velocity", "local_planner"])
 def test_adjoint_matches_the_oracle_adjoint(case):
     prob = {"circle4": lambda: twa.Problem.from_instance(workloads.circle4()),
             "pinned3": _pinned_case, "walls": _corridor,
             "velocity": lambda: twa.Problem.from_instance(
-                workloads.circle4(), vmax=np.full((4, 4), 0.56), vmin=np.full((4, 4), 0.3))}[case]()
-    K = {"circle4": 200, "pinned3": 120, "walls": 150, "velocity": 150}[case]
+                workloads.circle4(), vmax=np.full((4, 4), 0.56), vmin=np.full((4, 4), 0.3)),
+            "local_planner": _vo_epoch}[case]()
+    K = {"circle4": 200, "pinned3": 120, "walls": 150, "velocity": 150, "local_planner": 150}[case]
     assert _activity_matches(prob, K)
     W = np.random.default_rng(2024).standard_normal((prob.p, prob.eta + 1, 2))
     ref = adjoint.backward(prob, K, W)

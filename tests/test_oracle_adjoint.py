@@ -178,3 +178,33 @@ def test_adjoint_through_gated_segment_factors(case):
         fd = (runs[0] - runs[1]) / (2 * EPS)
         an = sum(float((gi * d[n]).sum()) for gi, n in zip(g, ("start", "goal", "radius", "cost")))
         assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3), (seed, an, fd)
+
+
+def test_adjoint_of_a_local_planner_epoch():
+    """The velocity-obstacle epoch (Section 5): gradient of its solution
+    after K = 150 iterations with respect to the current positions x(0)
+    (start), the reference positions (goal), radii and the C'_i, against
+    central differences, no branch flips."""
+    from oracle import vo
+    x0 = np.array([[-0.5, 0.01], [0.5, -0.01], [0.05, 0.6]])
+    dest = np.array([[2.0, 0.0], [-2.0, 0.0], [0.0, -2.0]])
+    prob = vo.problem(x0, vo.targets(x0, dest, 0.8), np.array([0.2, 0.2, 0.15]),
+                      np.array([1.0, 1.001, 1.002]), rho0=10.0)
+    k = 150
+    A0 = _acts(prob, k)
+    assert A0.any() and not A0[:, 1].any()
+    W = np.random.default_rng(3).standard_normal((3, 3, 2))
+    g = adjoint.backward(prob, k, W)
+    assert np.all(g[3][:, 0] == 0.0)  # no kinetic factor on the epoch's own motion
+    r = np.random.default_rng(1)
+    d = {n: r.standard_normal(getattr(prob, n).shape) for n in ("start", "goal", "radius", "cost")}
+    d["cost"][:, 0] = 0.0
+    runs = []
+    for sign in (1, -1):
+        pr = _shift(prob, sign, d)
+        pr.vo, pr.cost_unnorm = True, True
+        assert np.array_equal(_acts(pr, k), A0)
+        runs.append((W * adjoint.zK(pr, k)).sum())
+    fd = (runs[0] - runs[1]) / (2 * EPS)
+    an = sum(float((gi * d[n]).sum()) for gi, n in zip(g, ("start", "goal", "radius", "cost")))
+    assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3), (an, fd)
