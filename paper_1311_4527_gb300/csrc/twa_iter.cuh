@@ -95,8 +95,9 @@ __device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, f
 
 // Step 5's sums in 64-bit fixed point: each FP32 m converts exactly (the scale
 // is a power of two chosen from the layout's extent), integer addition does not
-// depend on the order of the atomics, so z is deterministic and is the
-// correctly rounded mean of the incoming m's.  A non-finite or out-of-range m
+// depend on the order of the atomics, so z is deterministic: the exact sum
+// rounded once to FP32 and divided by the count in FP32 (within 1.5 units in
+// the last place of the exact mean).  A non-finite or out-of-range m
 // sets status bit 1, which the consensus pass turns into a NaN residual.
 __device__ __forceinline__ void contribute(const Dev& P, float scale, float bound, int i, int s,
                                            float2 m) {
@@ -639,11 +640,12 @@ __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, b
     const unsigned deg = 2u * (unsigned)(P.p - 1) + 2u + 2u * (unsigned)P.nw;
     const long long rest = (long long)(deg - cnt);
     const long long qx = __float2ll_rn(zo.x * P.fix[0]), qy = __float2ll_rn(zo.y * P.fix[0]);
-    const double den = (double)P.fix[0] * (double)deg;
-    zn = mk((float)((double)(sx + rest * qx) / den), (float)((double)(sy + rest * qy) / den));
+    const float den = P.fix[0] * (float)deg;  // exact: a power of two times a small count
+    zn = mk(__ll2float_rn(sx + rest * qx) / den, __ll2float_rn(sy + rest * qy) / den);
   } else if (cnt > 0u) {
-    const double den = (double)P.fix[0] * (double)cnt;
-    zn = mk((float)((double)sx / den), (float)((double)sy / den));
+    // the exact integer sum rounded once to FP32, then one FP32 division
+    const float den = P.fix[0] * (float)cnt;
+    zn = mk(__ll2float_rn(sx) / den, __ll2float_rn(sy) / den);
   }
   // step 6: the back weight is rho0 where some factor sent rho0, else 0
   if (P.noenergy) P.wnode[node] = cnt > 0u ? 1 : 0;
