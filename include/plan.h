@@ -174,13 +174,15 @@ typedef struct {
 /* Sizes and counters (synchronises to count the active factors). */
 plan_status plan_get_info(plan_t plan, plan_info* info);
 
-/* Per-kernel timing of the next iterations (CUDA events on the streams the
- * kernels run on).  enable = 1 starts collecting (and synchronises once per
+/* Per-kernel timing of the next iterations (CUDA events on the plan's
+ * stream).  enable = 1 starts collecting (and synchronises once per
  * iteration, so timings are taken without overlap between iterations);
  * enable = 0 stops and writes the average milliseconds per iteration of the
- * four kernels to ms[0..3] = {collision test, collision minimizer, kinetic and
- * wall factors, consensus} and their count to *iterations (either may be
- * NULL).  Errors: PLAN_EINVAL, PLAN_ECUDA. */
+ * three kernels to ms[0..3] = {pass 1: collision tests, with the kinetic
+ * factors and wall tests in the same launch; pass 2: wall and collision
+ * minimizers; 0 (no separate kinetic / wall launch); consensus} and their
+ * count to *iterations (either may be NULL).  Errors: PLAN_EINVAL (a batch
+ * member), PLAN_ECUDA. */
 plan_status plan_profile(plan_t plan, int enable, float* ms, int* iterations);
 
 /*

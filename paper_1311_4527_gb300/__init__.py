@@ -439,11 +439,13 @@ class Planner:
         _check(_lib.plan_profile(self._h, 1, None, None))
 
     def profile_stop(self):
-        """Average ms per iteration of {test, minimizer, segment, consensus}."""
+        """Average ms per iteration of the three passes: test (collision
+        tests with the kinetic factors and wall tests in the same launch),
+        minimizer (walls and pairs) and consensus."""
         ms = (c_float * 4)()
         n = c_int(0)
         _check(_lib.plan_profile(self._h, 0, ms, byref(n)))
-        return dict(test=ms[0], minimizer=ms[1], segment=ms[2], consensus=ms[3], iterations=n.value)
+        return dict(test=ms[0], minimizer=ms[1], consensus=ms[3], iterations=n.value)
 
     def info(self):
         inf = plan_info()

@@ -2,13 +2,13 @@
 // planner (Bento, Derbinsky, Alonso-Mora, Yedidia, NIPS 2013): workspace
 // layout, input checks, state reset / import / export, the residual, and the
 // per-iteration launch sequence.  The iteration's per-block work lives in
-// twa_iter.cuh; one iteration is four kernels:
+// twa_iter.cuh; one iteration is three kernels on one stream:
 //
 //   test_kernel      every collision factor: deferred u step, n = z - u,
-//                    collision test, activity bits, worklist of active pairs
-//   segment_kernel   kinetic and wall factors (on a second stream, beside the
-//                    collision passes)
-//   prox_kernel      the collision minimizer of every active pair, adding
+//                    collision test, activity bits, worklist of active pairs;
+//                    in the same launch, the kinetic factors and the wall
+//                    tests (worklist of active walls)
+//   prox_kernel      the minimizer of every active wall and pair, adding
 //                    m = x + u into exact fixed-point consensus sums
 //   consensus_kernel z = sum m / count per free break-point
 //
@@ -34,35 +34,83 @@ namespace {
 constexpr int TEST_WARPS = 4;
 constexpr int TEST_ROWS = TILE / TEST_WARPS;
 
+// Pass 1 is one launch: its first nseg = eta x (agent tiles) blocks take the
+// kinetic and wall factors of one (segment, agent tile) each (segment_block,
+// dispatched first), the rest the collision blocks.  Both kinds of work
+// depend only on z^k, so one launch replaces two streams and their join.
 template <bool DENSE>
-__global__ void __launch_bounds__(32 * TEST_WARPS) test_kernel(Dev P) {
-  test_block<DENSE, TEST_ROWS>(P, blockIdx.x);
+__global__ void __launch_bounds__(32 * TEST_WARPS, 8) test_kernel(Dev P, int nseg) {
+  if ((int)blockIdx.x < nseg) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
+    segment_block<true>(P, blockIdx.x);
+    return;
+  }
+  test_block<DENSE, TEST_ROWS>(P, blockIdx.x - nseg);
 }
 
-// Gated state: one warp per tile, lane = row agent (test_tile_rows).
+// Gated state: one warp per tile, lane = row agent (test_tile_rows).  The
+// register cap keeps the collision blocks at their own count (48), which
+// sets the occupancy; the kinetic and wall blocks spill a little under it.
 constexpr int TILES_PER_CTA = 4;
-__global__ void __launch_bounds__(32 * TILES_PER_CTA) test_rows_kernel(Dev P) {
+__global__ void __launch_bounds__(32 * TILES_PER_CTA, 10) test_rows_kernel(Dev P, int nseg) {
   __shared__ float4 col[TILES_PER_CTA][64];
-  const int warp = threadIdx.x >> 5;
-  const int blk = blockIdx.x * TILES_PER_CTA + warp;
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
+  if ((int)blockIdx.x < nseg) {
+    segment_block<true>(P, blockIdx.x);
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int blk = ((int)blockIdx.x - nseg) * TILES_PER_CTA + warp;
   if (blk >= P.eta * P.ntp) return;  // warp-uniform
   if (P.vo && blk >= P.ntp) return;  // no collision factors on the second segment
   test_tile_rows(P, blk, col[warp]);
 }
 
-__global__ void __launch_bounds__(THREADS) segment_kernel(Dev P) { segment_block(P, blockIdx.x); }
+// Worklist items are dealt to warps round-robin (item t to warp t mod W,
+// lane t / W mod 32), so that a short list spreads over every SM instead of
+// filling the first few warps: each minimizer is a long dependent chain, and
+// a warp's time grows with the number of (divergent) items it holds.
+__device__ __forceinline__ unsigned long long dealt_first(unsigned long long& stride) {
+  const unsigned long long W = (gridDim.x * blockDim.x) >> 5;
+  stride = 32ull * W;
+  return (unsigned long long)(threadIdx.x & 31) * W + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+}
 
+// Pass 2: every active wall's minimizer on a warp of its own (all lanes
+// cooperating), the first warp of each of the first n_wall CTAs, so that
+// these long chains sit on different SMs.  The collision minimizers go in
+// groups of 32 consecutive worklist entries (pairs of one tile, so of one
+// segment: the lanes take the same branches) to the other warps, ordered so
+// that consecutive groups land on different CTAs and so spread over the SMs.
+// (More active walls than CTAs: walls over all warps, then pairs.)
 __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
-  const unsigned n = *P.work_count;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-    prox_item(P, P.work[t]);
+  const unsigned long long nc = *P.work_count, nwl = *P.wwork_count;
+  const unsigned long long wpb = blockDim.x >> 5, G = gridDim.x, b = blockIdx.x;
+  const unsigned long long wib = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  unsigned long long v, Wc;  // this warp's place among the collision warps, their number
+  if (nwl <= G) {
+    if (b < nwl && wib == 0) {
+      wall_prox_item_warp(P, P.wwork[b]);
+      return;
+    }
+    Wc = G * wpb - nwl;
+    v = wib == 0 ? b - nwl : (G - nwl) + (wib - 1) * G + b;
+  } else {
+    for (unsigned long long t = b * wpb + wib; t < nwl; t += G * wpb) wall_prox_item_warp(P, P.wwork[t]);
+    Wc = G * wpb;
+    v = wib * G + b;
+  }
+  for (unsigned long long t = 32ull * v + lane; t < nc; t += 32ull * Wc) prox_item(P, P.work[t]);
 }
 
 __global__ void consensus_kernel(Dev P) {
   const int nfree = (P.eta - 1) * P.p;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *P.work_count_next = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *P.work_count_next = 0u;
+    *P.wwork_count_next = 0u;
+  }
   float dz = 0.f;
   bool bad = false;
   if (t < nfree) consensus_node(P, t, dz, bad);
@@ -524,7 +572,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
-  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wcount, accx, accy, accc, fix,
+  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, accx, accy,
+      accc, fix,
       res, status, count;
   size_t total;
 };
@@ -568,7 +617,8 @@ Layout layout_for(const plan_config* c) {
   L.xwall = take(ng * eta * p * 16);
   L.wbits = take(ng * eta * nt * 4);
   L.work = take(slots * 4);
-  L.wcount = take(2 * 4);
+  L.wwork = take(nw * eta * p * 4);
+  L.wcount = take(4 * 4);  // collision and wall worklist counters, by iteration parity
   L.accx = take(p * (eta + 1) * 8);
   L.accy = take(p * (eta + 1) * 8);
   L.accc = take(p * (eta + 1) * 4);
@@ -668,9 +718,7 @@ struct plan_s {
   int k;
   int cur;  // which z buffer holds z^k
   int prox_grid = 0;  // CTAs of the minimizer pass (resident CTAs per SM x SMs)
-  cudaStream_t side = nullptr;   // second stream for the kinetic and wall factors
   cudaStream_t cap = nullptr;    // private stream for capturing the iteration graphs
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool profiling = false;        // plan_profile: per-kernel event timing
   cudaEvent_t pev[6] = {};
   cudaEvent_t pend = nullptr;
@@ -728,6 +776,9 @@ struct plan_s {
     P.work = at<uint32_t>(L.work);
     P.work_count = at<unsigned>(L.wcount) + (kk & 1);
     P.work_count_next = at<unsigned>(L.wcount) + ((kk + 1) & 1);
+    P.wwork = at<uint32_t>(L.wwork);
+    P.wwork_count = at<unsigned>(L.wcount) + 2 + (kk & 1);
+    P.wwork_count_next = at<unsigned>(L.wcount) + 2 + ((kk + 1) & 1);
     P.accx = at<unsigned long long>(L.accx);
     P.accy = at<unsigned long long>(L.accy);
     P.accc = at<unsigned>(L.accc);
@@ -765,27 +816,14 @@ plan_status ensure_prox_grid(plan_t h) {
 plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   Dev P = h->dev(h->k);
   const unsigned grid = (unsigned)((size_t)h->eta * h->ntp);
-  const int seg_threads = 32 * std::min(1 + h->nw + h->nv, WARPS);
-  const bool prof = h->profiling && h->side;
-  if (h->side) {
-    // kinetic and wall factors run beside the collision passes
-    CK(cudaEventRecord(h->ev_fork, ms));
-    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    if (prof) CK(cudaEventRecord(h->pev[4], h->side));
-    segment_kernel<<<h->eta * h->nt, seg_threads, 0, h->side>>>(P);
-    if (prof) CK(cudaEventRecord(h->pev[5], h->side));
-    CK(cudaEventRecord(h->ev_join, h->side));
-  } else {
-    segment_kernel<<<h->eta * h->nt, seg_threads, 0, ms>>>(P);
-  }
+  const int nseg = h->eta * h->nt;  // kinetic and wall blocks, ahead of the collision blocks
+  const bool prof = h->profiling;
   if (prof) CK(cudaEventRecord(h->pev[0], ms));
-  if (P.dense) test_kernel<true><<<grid, 32 * TEST_WARPS, 0, ms>>>(P);
-  else test_rows_kernel<<<(grid + TILES_PER_CTA - 1) / TILES_PER_CTA, 32 * TILES_PER_CTA, 0, ms>>>(P);
+  if (P.dense) test_kernel<true><<<nseg + grid, 32 * TEST_WARPS, 0, ms>>>(P, nseg);
+  else test_rows_kernel<<<nseg + (grid + TILES_PER_CTA - 1) / TILES_PER_CTA, 32 * TILES_PER_CTA, 0, ms>>>(P, nseg);
   if (prof) CK(cudaEventRecord(h->pev[1], ms));
   prox_kernel<<<h->prox_grid, 256, 0, ms>>>(P);
   if (prof) CK(cudaEventRecord(h->pev[2], ms));
-  if (h->side) CK(cudaStreamWaitEvent(ms, h->ev_join, 0));
-  if (prof) CK(cudaEventRecord(h->pev[3], ms));
   // the consensus kernel also clears the next iteration's worklist counter, so
   // it runs even when there is no free break-point (eta = 1)
   const int nfree = (h->eta - 1) * h->p;
@@ -796,8 +834,8 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
     float t[4];
     CK(cudaEventElapsedTime(&t[0], h->pev[0], h->pev[1]));
     CK(cudaEventElapsedTime(&t[1], h->pev[1], h->pev[2]));
-    CK(cudaEventElapsedTime(&t[2], h->pev[4], h->pev[5]));
-    CK(cudaEventElapsedTime(&t[3], h->pev[3], h->pend));
+    t[2] = 0.f;  // the kinetic and wall blocks run inside the pass-1 launch
+    CK(cudaEventElapsedTime(&t[3], h->pev[2], h->pend));
     for (int q = 0; q < 4; ++q) h->ptime[q] += t[q];
     h->pcount += 1;
   }
@@ -810,7 +848,7 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
 plan_status run_iteration(plan_t h) {
   plan_status st = ensure_prox_grid(h);
   if (st != PLAN_OK) return st;
-  const bool graphable = h->cap && h->side && !h->profiling && h->k >= std::max(1, h->cfg.warm_iters);
+  const bool graphable = h->cap && !h->profiling && h->k >= std::max(1, h->cfg.warm_iters);
   if (graphable) {
     const int key = ((h->k & 1) << 1) | h->cur;
     if (!h->gexec[key]) {
@@ -844,7 +882,7 @@ constexpr int ITERS_PER_GRAPH = 8;
 plan_status run_iterations(plan_t h, int n) {
   plan_status st = ensure_prox_grid(h);
   if (st != PLAN_OK) return st;
-  while (n >= ITERS_PER_GRAPH && h->cap && h->side && !h->profiling &&
+  while (n >= ITERS_PER_GRAPH && h->cap && !h->profiling &&
          h->k >= std::max(1, h->cfg.warm_iters)) {
     const int key = ((h->k & 1) << 1) | h->cur;
     if (!h->gexec8[key]) {
@@ -959,7 +997,7 @@ plan_status plan_reset(plan_t h) {
     if (ng) CK(cudaMemsetAsync(h->at<void>(h->L.uwall), 0, ng * h->eta * h->p * 16, h->stream));
   }
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
-  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1056,10 +1094,7 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
       delete h;
       return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
     }
-    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
       plan_destroy(h);
       return fail(PLAN_ECUDA, "stream or event creation failed");
     }
@@ -1095,11 +1130,8 @@ plan_status plan_create(const plan_config* cfg, const float* start, const float*
 void plan_destroy(plan_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
-  if (h->side) cudaStreamSynchronize(h->side);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_res) cudaFreeHost(h->h_res);
-  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int q = 0; q < 6; ++q)
     if (h->pev[q]) cudaEventDestroy(h->pev[q]);
   for (int q = 0; q < 4; ++q)
@@ -1107,7 +1139,6 @@ void plan_destroy(plan_t h) {
   for (int q = 0; q < 4; ++q)
     if (h->gexec8[q]) cudaGraphExecDestroy(h->gexec8[q]);
   if (h->pend) cudaEventDestroy(h->pend);
-  if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->adj) cudaFree(h->adj);
   delete h;
@@ -1217,7 +1248,7 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   plan_status wst = derive_wnode(h);
   if (wst != PLAN_OK) return wst;
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
-  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 8, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1250,7 +1281,7 @@ plan_status plan_get_info(plan_t h, plan_info* info) {
 
 plan_status plan_profile(plan_t h, int enable, float* ms, int* iterations) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
-  if (!h->side) return fail(PLAN_EINVAL, "this plan has no second stream to time");
+  if (!h->cap) return fail(PLAN_EINVAL, "a batch member cannot be timed on its own");
   if (enable) {
     for (int q = 0; q < 6; ++q)
       if (!h->pev[q]) CK(cudaEventCreate(&h->pev[q]));
@@ -1357,7 +1388,7 @@ std::vector<Region> ck_regions(plan_t h) {
   std::vector<Region> r = {
       {h->L.z0, zb}, {h->L.z1, zb}, {h->L.bits, (size_t)h->eta * h->ntp * TILE * 4},
       {h->L.ulo, h->slots * 16}, {h->L.uhi, h->slots * 16}, {h->L.xlo, h->slots * 16},
-      {h->L.xhi, h->slots * 16}, {h->L.ukin, kin}, {h->L.xkin, kin}, {h->L.wcount, 8},
+      {h->L.xhi, h->slots * 16}, {h->L.ukin, kin}, {h->L.xkin, kin}, {h->L.wcount, 16},
       {h->L.res, 16}, {h->L.status, 4}};
   if (ng) {
     r.push_back({h->L.uwall, ng * kin});
@@ -1958,7 +1989,7 @@ __global__ void batch_segment_kernel(const Dev* tab, const int* pre, int n, cons
   }
   __syncthreads();
   if (frozen[sb]) return;
-  segment_block(sP, sblk);
+  segment_block<false>(sP, sblk);
 }
 
 // Exclusive prefix of the members' worklist lengths (frozen members: 0).
@@ -1984,11 +2015,12 @@ __global__ void batch_scan_kernel(const Dev* tab, int n, const uint8_t* frozen, 
 }
 
 __global__ void __launch_bounds__(256) batch_prox_kernel(const Dev* tab, const int* pre_work, int n) {
-  const int total = pre_work[n];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int b = find_member(pre_work, n, t);
+  const unsigned long long total = (unsigned long long)pre_work[n];
+  unsigned long long stride;
+  for (unsigned long long t = dealt_first(stride); t < total; t += stride) {
+    const int b = find_member(pre_work, n, (int)t);
     const Dev& P = tab[b];
-    prox_item(P, P.work[t - pre_work[b]]);
+    prox_item(P, P.work[(int)t - pre_work[b]]);
   }
 }
 

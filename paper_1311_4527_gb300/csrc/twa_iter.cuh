@@ -6,9 +6,12 @@
 //   collision factors: finish the deferred dual update of the pairs that were
 //   active (step 7 of the previous iteration), n = z - u (step 1), collision
 //   test and weight (steps 2-3), activity bits, worklist of active pairs.
-// segment_block: the kinetic and wall factors of one (segment, agent tile).
+// segment_block: the kinetic and wall factors of one (segment, agent tile);
+//   the single-planner kernels run these blocks in the same launch as pass 1
+//   and leave the active walls' capsule minimizers to pass 2
+//   (wall_prox_item_warp, one warp per wall), which spreads them over the GPU.
 // Pass 2, prox_item: the collision minimizer of one active pair; adds its
-//   m = x + u to the consensus sums.
+//   m = x + u to the consensus sums (wall_prox_item_warp: the same for a wall).
 // Pass 3, consensus_node: z = sum m / count per free break-point (step 5).
 //
 // Step 7 needs z^{k+1}, which exists only after every factor ran, so x^{k+1}
@@ -69,6 +72,10 @@ struct Dev {
   uint32_t* work;        // active collision slots of this iteration
   unsigned* work_count;  // their number
   unsigned* work_count_next;  // the counter the next iteration appends to
+  uint32_t* wwork;       // active wall factors ((w eta + s) p + i) of this iteration whose
+                         // minimizer runs in pass 2 (wall_prox_item_warp)
+  unsigned* wwork_count;       // their number
+  unsigned* wwork_count_next;  // the counter the next iteration appends to
   unsigned long long* accx;  // [p][eta+1] fixed-point sums of rho0-weighted m.x
   unsigned long long* accy;  //                                 ... of m.y
   unsigned* accc;        // [p][eta+1] number of rho0-weighted incoming edges
@@ -147,14 +154,11 @@ __device__ __forceinline__ void coll_minimizer(float2 nil, float2 nih, float2 nj
   float2 sl = nil + njl, sh = nih + njh;     // sum coordinates x_i + x_j
   xil = nil; xih = nih; xjl = njl; xjh = njh;
   if (pin_lo && pin_hi) return;
-  if (pin_lo) {
-    float2 vh = disk_prox_pinned(cl, ch, R);
-    xih = 0.5f * (sh - vh);
-    xjh = 0.5f * (sh + vh);
-  } else if (pin_hi) {
-    float2 vl = disk_prox_pinned(ch, cl, R);
-    xil = 0.5f * (sl - vl);
-    xjl = 0.5f * (sl + vl);
+  if (pin_lo || pin_hi) {  // one call site for both fixed ends
+    const float2 v = disk_prox_pinned(pin_lo ? cl : ch, pin_lo ? ch : cl, R);
+    const float2 sm = pin_lo ? sh : sl;
+    const float2 xi = 0.5f * (sm - v), xj = 0.5f * (sm + v);
+    if (pin_lo) { xih = xi; xjh = xj; } else { xil = xi; xjl = xj; }
   } else {
     float2 vl, vh;
     float w = 0.5f * rho;  // rho rho / (rho + rho)
@@ -223,7 +227,9 @@ __device__ __forceinline__ void end_classes(const Dev& P, int i, int s, bool pin
 // Gated segment factor w of (i, s): a wall (w < nw, Eq. wall_minimizer) or a
 // maximum / minimum velocity factor (w >= nw, Eq. max_vel_min).  Forward
 // weight rho0 when the n's violate it, else 0.  Called by a full warp (lane =
-// agent of tile I).
+// agent of tile I).  DEFER: the capsule minimizers of active walls go to the
+// wall worklist (P.wwork) instead of running here.
+template <bool DEFER>
 __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi, int s, int I,
                                             float2 zl, float2 zh, float r, bool pin_lo,
                                             bool pin_hi, float& res) {
@@ -264,14 +270,28 @@ __device__ __forceinline__ void wall_factor(const Dev& P, int w, int i, bool vi,
   }
   const uint32_t nw = __ballot_sync(FULL, act);
   if (lane == 0 && nw != word) P.wbits[widx] = nw;
+  if (DEFER && !vel) {
+    // the capsule minimizers go to the minimizer pass, spread over the GPU
+    // (one warp with several active walls would run them one after another)
+    if (act) P.uwall[idx] = pack(ul, uh);
+    else if (vi && P.dense) P.uwall[idx] = pack(ul, uh);
+    if (nw) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(P.wwork_count, (unsigned)__popc(nw));
+      base = __shfl_sync(FULL, base, 0);
+      if (act) P.wwork[base + __popc(nw & ((1u << lane) - 1u))] = (uint32_t)idx;
+    }
+    return;
+  }
   if (act) {
     float2 xl = nl, xh = nh;
     int cl, ch;
     end_classes(P, i, s, pin_lo, pin_hi, cl, ch);
     if (vel) {
       velocity_prox(nl, nh, cl, ch, C, xl, xh);
-    } else if (!capsule_prox_classes(nl, nh, cl, ch, c0, c1, r, 0.5f * P.rho, xl, xh)) {
-      atomicOr(P.status, 1u);
+    } else if (!DEFER) {
+      if (!capsule_prox_classes(nl, nh, cl, ch, c0, c1, r, 0.5f * P.rho, xl, xh))
+        atomicOr(P.status, 1u);
     }
     P.xwall[idx] = pack(xl, xh);
     P.uwall[idx] = pack(ul, uh);
@@ -556,7 +576,8 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
 
 // Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
 // s and one agent tile: warp f < 1 + n_walls takes factor kind f (0 =
-// kinetic, else wall f - 1), lane = agent.
+// kinetic, else wall f - 1), lane = agent.  DEFER: see wall_factor.
+template <bool DEFER>
 __device__ __forceinline__ void segment_block(const Dev& P, int blk) {
   const int s = blk / P.nt;
   const int I = blk - s * P.nt;
@@ -573,11 +594,44 @@ __device__ __forceinline__ void segment_block(const Dev& P, int blk) {
     if (f == 0) {
       if (vi && !P.noenergy && !(P.vo && s == 0)) kinetic_factor(P, i, s, zl, zh, pin_lo, pin_hi, res);
     } else if (!(P.vo && s != 0)) {
-      wall_factor(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
+      wall_factor<DEFER>(P, f - 1, i, vi, s, I, zl, zh, r, pin_lo, pin_hi, res);
     }
   }
   res = warp_max(res);
   if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+}
+
+// The capsule minimizer (Eq. wall_minimizer) of one active wall factor from
+// the wall worklist, with the u that its segment block finished (so n = z - u
+// is the value it tested).  Called by all 32 lanes of a warp with the same
+// item: both ends free (the common case) shares the candidate solves out
+// over the lanes; lane 0 stores the result.
+__device__ __forceinline__ void wall_prox_item_warp(const Dev& P, uint32_t idx) {
+  const uint32_t i = idx % (uint32_t)P.p, ws = idx / (uint32_t)P.p;
+  const int s = (int)(ws % (uint32_t)P.eta), w = (int)(ws / (uint32_t)P.eta);
+  const int E1 = P.eta + 1;
+  const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
+  const float4 u4 = P.uwall[idx];
+  const float2 ul = lo2(u4), uh = hi2(u4);
+  const float2 nl = P.z[(size_t)i * E1 + s] - ul, nh = P.z[(size_t)i * E1 + s + 1] - uh;
+  const float4 W = P.walls[w];
+  const float2 c0 = mk(W.x, W.y), c1 = mk(W.z, W.w);
+  const float r = P.radius[i];
+  int cl, ch;
+  end_classes(P, (int)i, s, pin_lo, pin_hi, cl, ch);
+  float2 xl = nl, xh = nh;
+  bool ok = true;
+  if (cl == 1 && ch == 1) {
+    const float wgt = 0.5f * P.rho;
+    capsule_prox_free_warp(nl, nh, wgt, wgt, c0, c1, r, xl, xh);
+  } else {
+    ok = capsule_prox_classes(nl, nh, cl, ch, c0, c1, r, 0.5f * P.rho, xl, xh);
+  }
+  if ((threadIdx.x & 31) != 0) return;
+  if (!ok) atomicOr(P.status, 1u);
+  P.xwall[idx] = pack(xl, xh);
+  if (!pin_lo) contribute(P, (int)i, s, xl + ul);
+  if (!pin_hi) contribute(P, (int)i, s + 1, xh + uh);
 }
 
 // Pass 2: the collision minimizer (Eq. coll_minimizer_problem through
@@ -629,10 +683,10 @@ __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, b
   const unsigned status = *P.status;  // issued with the sums, not after them
   const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
   const unsigned cnt = P.accc[node];
+  const float2 zo = P.z[node];  // every load before the stores, so that they overlap
   P.accx[node] = 0ull;
   P.accy[node] = 0ull;
   P.accc[node] = 0u;
-  const float2 zo = P.z[node];
   float2 zn = zo;  // every incoming weight zero: treated as 1, which gives z unchanged
   if (P.admm) {
     // every edge is weighted; each feasible collision or wall factor sent

@@ -44,8 +44,13 @@ namespace twa {
 
 // Host and device: the same FP32 code is also compiled into a host-side test
 // harness (tests/minimizer_harness.cu) that compares it with the FP64 oracle.
+// Everything is inlined, and candidate directions are written to fixed
+// array slots only (put_dir, unrolled loops), so that the minimizers keep
+// their candidates in registers: a call or a dynamically indexed array puts
+// them in local memory, whose latency sits on the minimizer's long dependent
+// chain.
 #define TWA_DEV __host__ __device__ __forceinline__
-#define TWA_NOINLINE __host__ __device__ __noinline__
+#define TWA_NOINLINE TWA_DEV
 #ifndef TWA_ITER_HOOK
 #define TWA_ITER_HOOK(kind)
 #endif
@@ -81,10 +86,25 @@ TWA_DEV float frsqrt(float x) {
 #endif
 }
 
+// out[n++] = v with constant indices (up to 4 slots).
+TWA_DEV void put_dir(float2* out, int& n, float2 v) {
+  if (n == 0) out[0] = v;
+  else if (n == 1) out[1] = v;
+  else if (n == 2) out[2] = v;
+  else out[3] = v;
+  ++n;
+}
+
 // Angle of a unit vector in [0, 2 pi): the tie-break order of directions.
-TWA_DEV float angle_of(float2 n) {
+// Not inlined: it runs only on exact ties, and a copy at every tie-break
+// would crowd the minimizers' instruction stream.
+__host__ __device__ __noinline__ float angle_of(float2 n) {
   float t = atan2f(n.y, n.x);
   return t < 0.f ? t + 6.283185307179586f : t;
+}
+// a before b in the tie-break order
+__host__ __device__ __noinline__ bool angle_less(float2 a, float2 b) {
+  return angle_of(a) < angle_of(b);
 }
 
 // Squared distance from the origin to segment [p0, p1].  Interior projections
@@ -123,7 +143,7 @@ struct Best {
   int tag;
   TWA_DEV void init() { n = mk(1.f, 0.f); E = INFINITY; tag = 0; }
   TWA_DEV void offer(float2 c, float e, int t = 0) {
-    if (e < E || (e == E && angle_of(c) < angle_of(n))) { n = c; E = e; tag = t; }
+    if (e < E || (e == E && angle_less(c, n))) { n = c; E = e; tag = t; }
   }
 };
 
@@ -230,8 +250,12 @@ TWA_NOINLINE int trs_global(float2 a, float2 b, float wl, float wh, float R,
 // so there are 0 or 2 roots (one is the local-but-not-global minimum); with
 // s1 = 0 or s2 = 0 the stationary points at mu = lambda1 or lambda2 are added.
 // Writes up to 4 directions; used by the wall minimizer, whose capsule
-// restricts each end circle to a half-plane of directions.
-TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, float2* out) {
+// restricts each end circle to a half-plane of directions.  part = 0 or 1
+// writes only the directions of that part of the sequence (0: the special
+// cases or the root left of t_m, 1: the root right of it), for callers that
+// split the work over threads; -1 writes all.
+TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, float2* out,
+                           int part = -1) {
   float m11 = wl * a.x * a.x + wh * b.x * b.x;
   float m22 = wl * a.y * a.y + wh * b.y * b.y;
   float m12 = wl * a.x * a.y + wh * b.x * b.y;
@@ -246,25 +270,27 @@ TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, floa
   float A1 = R * fabsf(s1), A2 = R * fabsf(s2);
   int n = 0;
   if (A1 == 0.f && A2 == 0.f) return 0;
+  if ((A2 == 0.f || A1 == 0.f) && part == 1) return 0;
   if (A2 == 0.f) {  // hard case at mu = lambda2, and the root t = A1
     if (A1 < d) {
       float n1 = -R * s1 / d;
       float n2 = sqrtf(fmaxf(0.f, 1.f - n1 * n1));
-      out[n++] = n1 * e1 + n2 * e2;
-      out[n++] = n1 * e1 + (-n2) * e2;
-      out[n++] = (s1 > 0.f ? -1.f : 1.f) * e1;
+      out[0] = n1 * e1 + n2 * e2;
+      out[1] = n1 * e1 + (-n2) * e2;
+      out[2] = (s1 > 0.f ? -1.f : 1.f) * e1;
+      n = 3;
     }
     return n;
   }
   if (A1 == 0.f) {  // the root t = d - A2
-    if (A2 < d) out[n++] = (s2 > 0.f ? 1.f : -1.f) * e2;
+    if (A2 < d) { out[0] = (s2 > 0.f ? 1.f : -1.f) * e2; n = 1; }
     return n;
   }
   float c1 = cbrtf(A1 * A1), c2 = cbrtf(A2 * A2);
   float tm = d * c1 / (c1 + c2);
   float phim = (A1 / tm) * (A1 / tm) + (A2 / (d - tm)) * (A2 / (d - tm));
   if (!(phim <= 1.f)) return 0;
-  for (int side = 0; side < 2; ++side) {
+  for (int side = (part == 1) ? 1 : 0; side < ((part == 0) ? 1 : 2); ++side) {
     // h(t) = phi(t)^(-1/2) - 1 is increasing on (0, tm] and decreasing on
     // [tm, d); each root is approached from its pole side, where h <= 0 (at
     // t = A1, resp. t = d - A2), so that the Newton steps move monotonically.
@@ -293,7 +319,7 @@ TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, floa
     float n1, n2;
     if (fabsf(p1) <= fabsf(p2)) { n1 = p1; n2 = copysignf(sqrtf(fmaxf(0.f, 1.f - p1 * p1)), p2); }
     else { n2 = p2; n1 = copysignf(sqrtf(fmaxf(0.f, 1.f - p2 * p2)), p1); }
-    out[n++] = normalized(n1 * e1 + n2 * e2);
+    put_dir(out, n, normalized(n1 * e1 + n2 * e2));
   }
   return n;
 }
@@ -344,16 +370,20 @@ TWA_DEV float2 disk_dir_free(float2 a, float2 b, float wl, float wh, float R, in
   best.offer(mk(1.f, 0.f), hinge_E(a, b, wl, wh, R, mk(1.f, 0.f)), DISK_DEFAULT);
   float2 c[2];
   int nc = trs_global(a, b, wl, wh, R, c);
-  for (int k = 0; k < nc; ++k) best.offer(c[k], hinge_E(a, b, wl, wh, R, c[k]), DISK_GLOBAL);
-  if (dot(b, b) >= R * R) {  // b's hinge can be zero: best a-term on that arc
-    bool tg;
-    float2 n = arc_argmax(b, R, a, tg);
-    best.offer(n, hinge_E(a, b, wl, wh, R, n), tg ? DISK_A_TANGENT : DISK_A_INNER);
-  }
-  if (dot(a, a) >= R * R) {
-    bool tg;
-    float2 n = arc_argmax(a, R, b, tg);
-    best.offer(n, hinge_E(a, b, wl, wh, R, n), tg ? DISK_B_TANGENT : DISK_B_INNER);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (k < nc) best.offer(c[k], hinge_E(a, b, wl, wh, R, c[k]), DISK_GLOBAL);
+  // side 0: b's hinge can be zero, best a-term on that arc; side 1: the same
+  // with a and b exchanged (one copy of the code, run twice)
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const float2 q = side ? a : b, w = side ? b : a;
+    if (dot(q, q) >= R * R) {
+      bool tg;
+      float2 n = arc_argmax(q, R, w, tg);
+      best.offer(n, hinge_E(a, b, wl, wh, R, n),
+                 side ? (tg ? DISK_B_TANGENT : DISK_B_INNER) : (tg ? DISK_A_TANGENT : DISK_A_INNER));
+    }
   }
   tag = best.tag;
   return best.n;
@@ -390,6 +420,28 @@ TWA_DEV float capsule_E(float2 a, float2 b, float wl, float wh, float2 c0, float
   return 0.5f * wl * ga * ga + 0.5f * wh * gb * gb;
 }
 
+// On the half-plane of directions where end circle ci gives the capsule's
+// support (<c_ci - c_other, n> >= 0), the energy is that circle's disk
+// energy.  Write n = c nu + s e (e the outward wall direction at that end, nu
+// its normal, s >= 0) and beta_x, gamma_x for the coordinates of x - c_ci
+// along nu and e.  When neither target lies beyond the end (gamma <= 0),
+// <x - c_ci, n> <= c beta_x, so the energy is at least
+// G(c) = wl/2 [r - c beta_a]_+^2 + wh/2 [r - c beta_b]_+^2, which equals the
+// kink energies at c = +-1; with both targets on one side of the wall's line
+// (beta_a, beta_b of one sign) G is monotone in c, so nothing in that
+// half-plane is below the better kink and the circle's candidates can be
+// skipped.  False for a zero-length wall.
+TWA_DEV bool capsule_end_dominated(float2 a, float2 b, float2 c0, float2 c1, int ci) {
+  const float2 e = c1 - c0;
+  if (e.x == 0.f && e.y == 0.f) return false;
+  const float2 cc = ci ? c1 : c0;
+  const float2 out = ci ? e : -e;
+  const float2 nu = perp(e);
+  const float ga = dot(a - cc, out), gb = dot(b - cc, out);
+  const float ba = dot(a - cc, nu), bb = dot(b - cc, nu);
+  return ga <= 0.f && gb <= 0.f && ((ba >= 0.f && bb >= 0.f) || (ba <= 0.f && bb <= 0.f));
+}
+
 // Kinds of winning capsule direction (Best::tag): 0 the (1, 0) fallback,
 // 1 a kink, and per end circle ci: 2 + 4 ci a stationary point of its
 // both-stretched piece (free) or a tangent from the fixed end (pinned),
@@ -406,14 +458,20 @@ TWA_DEV float2 capsule_dir_free(float2 a, float2 b, float wl, float wh, float2 c
     best.offer(k0, capsule_E(a, b, wl, wh, c0, c1, r, k0), 1);
     best.offer(-k0, capsule_E(a, b, wl, wh, c0, c1, r, -k0), 1);
   }
+#pragma unroll 1
   for (int ci = 0; ci < 2; ++ci) {
+    if (capsule_end_dominated(a, b, c0, c1, ci)) continue;
     float2 cc = ci ? c1 : c0;
     float2 ac = a - cc, bc = b - cc;
     float2 t[4];
     int nt = trs_global(ac, bc, wl, wh, r, t);
-    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (k < nt) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
     nt = trs_local(ac, bc, wl, wh, r, t);
-    for (int k = 0; k < nt; ++k) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < nt) best.offer(t[k], capsule_E(a, b, wl, wh, c0, c1, r, t[k]), 2 + 4 * ci);
     if (dot(ac, ac) > 0.f) {
       float2 n = normalized(ac);
       best.offer(n, capsule_E(a, b, wl, wh, c0, c1, r, n), 3 + 4 * ci);
@@ -436,46 +494,119 @@ TWA_NOINLINE void capsule_prox_free(float2 a, float2 b, float wl, float wh, floa
   vh = b + fmaxf(h - dot(b, n), 0.f) * n;
 }
 
+#ifdef __CUDACC__
+// capsule_prox_free by a whole warp (every lane calls it with the same
+// arguments and gets the same result): the candidate directions of
+// capsule_dir_free are shared out over 9 lanes (the fallback and kinks; per
+// end circle the global stationary point, the two halves of trs_local and the
+// single-hinge directions), each lane keeps its best in the same order, and a
+// warp reduction on (E, angle, position in the sequence) picks the candidate
+// that the sequential scan keeps.  The secular solves then run side by side
+// instead of one after another.
+__device__ __forceinline__ void capsule_prox_free_warp(float2 a, float2 b, float wl, float wh,
+                                                       float2 c0, float2 c1, float r, float2& vl,
+                                                       float2& vh) {
+  const int lane = threadIdx.x & 31;
+  Best best;
+  best.init();
+  bool any = false;
+  auto offer = [&](float2 c) {
+    best.offer(c, capsule_E(a, b, wl, wh, c0, c1, r, c), 0);
+    any = true;
+  };
+  if (lane == 0) {
+    offer(mk(1.f, 0.f));
+    float2 e = c1 - c0;
+    if (e.x != 0.f || e.y != 0.f) {
+      float2 k0 = normalized(perp(e));
+      offer(k0);
+      offer(-k0);
+    }
+  } else if (lane < 9 && !capsule_end_dominated(a, b, c0, c1, (lane - 1) >> 2)) {
+    const int ci = (lane - 1) >> 2, task = (lane - 1) & 3;
+    const float2 cc = ci ? c1 : c0;
+    const float2 ac = a - cc, bc = b - cc;
+    float2 t[4];
+    int nt = 0;
+    if (task == 0) nt = trs_global(ac, bc, wl, wh, r, t);
+    else if (task < 3) nt = trs_local(ac, bc, wl, wh, r, t, task - 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < nt) offer(t[k]);
+    if (task == 3) {
+      if (dot(ac, ac) > 0.f) offer(normalized(ac));
+      if (dot(bc, bc) > 0.f) offer(normalized(bc));
+    }
+  }
+  // reduction: lower E, then smaller angle, then the earlier lane (whose
+  // candidates come first in the sequential order)
+  float E = any ? best.E : INFINITY;
+  float2 n = best.n;
+  int src = any ? lane : 32;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+    const float nx = __shfl_xor_sync(0xffffffffu, n.x, o), ny = __shfl_xor_sync(0xffffffffu, n.y, o);
+    const int src2 = __shfl_xor_sync(0xffffffffu, src, o);
+    bool take;
+    if (src2 == 32) take = false;
+    else if (src == 32) take = true;
+    else if (E2 < E) take = true;
+    else if (E2 == E) {
+      const float g2 = angle_of(mk(nx, ny)), g = angle_of(n);
+      take = g2 < g || (g2 == g && src2 < src);
+    } else {
+      // NaN energies never win in the sequential scan, and the fallback
+      // (lane 0) is always offered first
+      take = false;
+    }
+    if (take) { E = E2; n = mk(nx, ny); src = src2; }
+  }
+  const float h = capsule_h(c0, c1, r, n);
+  vl = a + fmaxf(h - dot(a, n), 0.f) * n;
+  vh = b + fmaxf(h - dot(b, n), 0.f) * n;
+}
+#endif
+
 // One end pinned at q; free end target w.  Candidates: tangent directions
 // from q to both end circles, the kinks, and the single-hinge directions;
 // only directions that still separate q from the capsule are kept.
 // Returns false if no candidate separates q (q inside the capsule).
 TWA_DEV bool capsule_dir_pinned(float2 q, float2 w, float2 c0, float2 c1, float r, float2& dir,
                                 int& tag) {
-  float2 cand[8];
-  int ctag[8];
-  int nc = 0;
-  for (int ci = 0; ci < 2; ++ci) {
-    float2 cc = ci ? c1 : c0;
-    float2 qc = q - cc;
-    if (dot(qc, qc) >= r * r) {
-      float2 t0, t1;
-      tangent_normals(qc, r, t0, t1);
-      ctag[nc] = 2 + 4 * ci; cand[nc++] = normalized(t0);
-      ctag[nc] = 2 + 4 * ci; cand[nc++] = normalized(t1);
-    }
-    float2 wc = w - cc;
-    if (dot(wc, wc) > 0.f) { ctag[nc] = 3 + 4 * ci; cand[nc++] = normalized(wc); }
-  }
-  float2 e = c1 - c0;
-  if (e.x != 0.f || e.y != 0.f) {
-    float2 k0 = normalized(perp(e));
-    ctag[nc] = 1; cand[nc++] = k0;
-    ctag[nc] = 1; cand[nc++] = -k0;
-  }
   float scale = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)),
                       fmaxf(fmaxf(fabsf(c0.x), fabsf(c0.y)), fmaxf(fabsf(c1.x), fabsf(c1.y)))) + r;
   float tol = 4e-6f * scale;
   Best best;
   best.init();
   bool any = false;
-  for (int k = 0; k < nc; ++k) {
-    float h = capsule_h(c0, c1, r, cand[k]);
-    if (dot(q, cand[k]) - h >= -tol) {
-      float g = fmaxf(h - dot(w, cand[k]), 0.f);
-      best.offer(cand[k], 0.5f * g * g, ctag[k]);
+  // candidates in a fixed order, each kept if it separates q
+  auto offer = [&](float2 c, int t) {
+    float h = capsule_h(c0, c1, r, c);
+    if (dot(q, c) - h >= -tol) {
+      float g = fmaxf(h - dot(w, c), 0.f);
+      best.offer(c, 0.5f * g * g, t);
       any = true;
     }
+  };
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    float2 cc = ci ? c1 : c0;
+    float2 qc = q - cc;
+    if (dot(qc, qc) >= r * r) {
+      float2 t0, t1;
+      tangent_normals(qc, r, t0, t1);
+      offer(normalized(t0), 2 + 4 * ci);
+      offer(normalized(t1), 2 + 4 * ci);
+    }
+    float2 wc = w - cc;
+    if (dot(wc, wc) > 0.f) offer(normalized(wc), 3 + 4 * ci);
+  }
+  float2 e = c1 - c0;
+  if (e.x != 0.f || e.y != 0.f) {
+    float2 k0 = normalized(perp(e));
+    offer(k0, 1);
+    offer(-k0, 1);
   }
   dir = best.n;
   tag = best.tag;
@@ -532,11 +663,16 @@ TWA_DEV void disk_prox_classes(float2 a, float2 b, int cl, int ch, float R, floa
                                float2& vh) {
   vl = a; vh = b;
   if (cl == 2 && ch == 2) return;
-  if (cl == 2) { vh = disk_prox_pinned(a, b, R); return; }
-  if (ch == 2) { vl = disk_prox_pinned(b, a, R); return; }
-  if (cl == 0 && ch == 1) { vh = disk_project_out(b, R); vl = disk_prox_pinned(vh, a, R); return; }
-  if (cl == 1 && ch == 0) { vl = disk_project_out(a, R); vh = disk_prox_pinned(vl, b, R); return; }
-  disk_prox_free(a, b, w, w, R, vl, vh);
+  if (cl == ch) { disk_prox_free(a, b, w, w, R, vl, vh); return; }  // both rho0 or both zero
+  // one end fixed (class 2), or one end of zero weight, which first leaves
+  // the disk by the least amount and is then held there: either way the other
+  // end solves the fixed-end problem (one call site for the four cases)
+  const bool lo_fixed = (cl == 2) || (cl == 1 && ch == 0);
+  if (cl == 1 && ch == 0) vl = disk_project_out(a, R);
+  if (cl == 0 && ch == 1) vh = disk_project_out(b, R);
+  const float2 q = lo_fixed ? vl : vh, t = lo_fixed ? b : a;
+  const float2 v = disk_prox_pinned(q, t, R);
+  if (lo_fixed) vh = v; else vl = v;
 }
 
 // Capsule minimizer for weight classes; false if a fixed end lies inside.
@@ -544,18 +680,12 @@ TWA_DEV bool capsule_prox_classes(float2 a, float2 b, int cl, int ch, float2 c0,
                                   float w, float2& vl, float2& vh) {
   vl = a; vh = b;
   if (cl == 2 && ch == 2) return true;
-  if (cl == 2) return capsule_prox_pinned(a, b, c0, c1, r, vh);
-  if (ch == 2) return capsule_prox_pinned(b, a, c0, c1, r, vl);
-  if (cl == 0 && ch == 1) {
-    vh = capsule_project_out(b, c0, c1, r);
-    return capsule_prox_pinned(vh, a, c0, c1, r, vl);
-  }
-  if (cl == 1 && ch == 0) {
-    vl = capsule_project_out(a, c0, c1, r);
-    return capsule_prox_pinned(vl, b, c0, c1, r, vh);
-  }
-  capsule_prox_free(a, b, w, w, c0, c1, r, vl, vh);
-  return true;
+  if (cl == ch) { capsule_prox_free(a, b, w, w, c0, c1, r, vl, vh); return true; }  // equal weights
+  // as disk_prox_classes: the other end solves the fixed-end problem
+  const bool lo_fixed = (cl == 2) || (cl == 1 && ch == 0);
+  if (cl == 1 && ch == 0) vl = capsule_project_out(a, c0, c1, r);
+  if (cl == 0 && ch == 1) vh = capsule_project_out(b, c0, c1, r);
+  return lo_fixed ? capsule_prox_pinned(vl, b, c0, c1, r, vh) : capsule_prox_pinned(vh, a, c0, c1, r, vl);
 }
 
 // ---------------------------------------------------------------------------
