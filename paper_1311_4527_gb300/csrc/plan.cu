@@ -30,6 +30,17 @@
 
 namespace {
 
+// Programmatic dependent launch: the three kernels of an iteration are
+// launched with programmatic stream serialization, so each one's CTAs can be
+// scheduled while the previous kernel drains (every CTA lets its dependents
+// launch as soon as it starts); griddepcontrol.wait then holds them until the
+// previous kernel has completed and its writes are visible.  Without the
+// launch attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // The single-planner kernels: thin wrappers over the per-block work.
 constexpr int TEST_WARPS = 4;
 constexpr int TEST_ROWS = TILE / TEST_WARPS;
@@ -40,6 +51,7 @@ constexpr int TEST_ROWS = TILE / TEST_WARPS;
 // depend only on z^k, so one launch replaces two streams and their join.
 template <bool DENSE>
 __global__ void __launch_bounds__(32 * TEST_WARPS, 8) test_kernel(Dev P, int nseg) {
+  pdl_begin();
   if ((int)blockIdx.x < nseg) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
     segment_block<true>(P, blockIdx.x);
@@ -54,16 +66,23 @@ __global__ void __launch_bounds__(32 * TEST_WARPS, 8) test_kernel(Dev P, int nse
 constexpr int TILES_PER_CTA = 4;
 __global__ void __launch_bounds__(32 * TILES_PER_CTA, 10) test_rows_kernel(Dev P, int nseg) {
   __shared__ float4 col[TILES_PER_CTA][64];
+  __shared__ uint32_t nws[TILES_PER_CTA][32];
+  pdl_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
   if ((int)blockIdx.x < nseg) {
     segment_block<true>(P, blockIdx.x);
     return;
   }
   const int warp = threadIdx.x >> 5;
-  const int blk = ((int)blockIdx.x - nseg) * TILES_PER_CTA + warp;
-  if (blk >= P.eta * P.ntp) return;  // warp-uniform
-  if (P.vo && blk >= P.ntp) return;  // no collision factors on the second segment
-  test_tile_rows(P, blk, col[warp]);
+  // tiles are dispatched segment-minor (t -> segment t mod eta), so that the
+  // tiles of a crowded segment spread over the whole launch instead of all
+  // landing in its last wave
+  const int t = ((int)blockIdx.x - nseg) * TILES_PER_CTA + warp;
+  if (t >= P.eta * P.ntp) return;  // warp-uniform
+  const int s = t % P.eta;
+  if (P.vo && s != 0) return;  // no collision factors on the second segment
+  const int blk = s * P.ntp + t / P.eta;
+  test_tile_rows(P, blk, col[warp], nws[warp]);
 }
 
 // Worklist items are dealt to warps round-robin (item t to warp t mod W,
@@ -84,6 +103,7 @@ __device__ __forceinline__ unsigned long long dealt_first(unsigned long long& st
 // that consecutive groups land on different CTAs and so spread over the SMs.
 // (More active walls than CTAs: walls over all warps, then pairs.)
 __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
+  pdl_begin();
   const unsigned long long nc = *P.work_count, nwl = *P.wwork_count;
   const unsigned long long wpb = blockDim.x >> 5, G = gridDim.x, b = blockIdx.x;
   const unsigned long long wib = threadIdx.x >> 5;
@@ -105,6 +125,7 @@ __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
 }
 
 __global__ void consensus_kernel(Dev P) {
+  pdl_begin();
   const int nfree = (P.eta - 1) * P.p;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -812,6 +833,23 @@ plan_status ensure_prox_grid(plan_t h) {
   return PLAN_OK;
 }
 
+// A launch with programmatic stream serialization (see pdl_begin).
+template <typename... Args>
+cudaError_t launch_pdl(void (*kern)(Args...), unsigned grid, unsigned block, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Enqueue the kernels of iteration h->k (no state change on the host).
 plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   Dev P = h->dev(h->k);
@@ -819,15 +857,18 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   const int nseg = h->eta * h->nt;  // kinetic and wall blocks, ahead of the collision blocks
   const bool prof = h->profiling;
   if (prof) CK(cudaEventRecord(h->pev[0], ms));
-  if (P.dense) test_kernel<true><<<nseg + grid, 32 * TEST_WARPS, 0, ms>>>(P, nseg);
-  else test_rows_kernel<<<nseg + (grid + TILES_PER_CTA - 1) / TILES_PER_CTA, 32 * TILES_PER_CTA, 0, ms>>>(P, nseg);
+  if (P.dense)
+    CK(launch_pdl(test_kernel<true>, nseg + grid, 32 * TEST_WARPS, ms, P, nseg));
+  else
+    CK(launch_pdl(test_rows_kernel, nseg + (grid + TILES_PER_CTA - 1) / TILES_PER_CTA,
+                  32 * TILES_PER_CTA, ms, P, nseg));
   if (prof) CK(cudaEventRecord(h->pev[1], ms));
-  prox_kernel<<<h->prox_grid, 256, 0, ms>>>(P);
+  CK(launch_pdl(prox_kernel, h->prox_grid, 256, ms, P));
   if (prof) CK(cudaEventRecord(h->pev[2], ms));
   // the consensus kernel also clears the next iteration's worklist counter, so
   // it runs even when there is no free break-point (eta = 1)
   const int nfree = (h->eta - 1) * h->p;
-  consensus_kernel<<<std::max(1, (nfree + 63) / 64), 64, 0, ms>>>(P);
+  CK(launch_pdl(consensus_kernel, std::max(1, (nfree + 63) / 64), 64, ms, P));
   if (prof) {
     CK(cudaEventRecord(h->pend, ms));
     CK(cudaEventSynchronize(h->pend));
@@ -1963,6 +2004,7 @@ __global__ void __launch_bounds__(32 * TILES_PER_CTA) batch_test_rows_kernel(con
                                                                          const uint8_t* frozen) {
   __shared__ Dev sP[TILES_PER_CTA];
   __shared__ float4 col[TILES_PER_CTA][64];
+  __shared__ uint32_t nws[TILES_PER_CTA][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * TILES_PER_CTA + warp;
   if (t >= ntiles) return;  // warp-uniform
@@ -1975,7 +2017,7 @@ __global__ void __launch_bounds__(32 * TILES_PER_CTA) batch_test_rows_kernel(con
   __syncwarp();
   const int blk = t - pre[b];
   if (blk == 0 && lane == 0) *sP[warp].res_cur = 0u;
-  test_tile_rows(sP[warp], blk, col[warp]);
+  test_tile_rows(sP[warp], blk, col[warp], nws[warp]);
 }
 
 __global__ void batch_segment_kernel(const Dev* tab, const int* pre, int n, const uint8_t* frozen) {

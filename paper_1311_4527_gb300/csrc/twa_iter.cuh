@@ -476,7 +476,7 @@ __device__ __forceinline__ void test_block(const Dev& P, int blk) {
 // bounding-circle early out before the exact test.  Same decisions and
 // stores as test_block<false>; only the worklist order differs.
 // col: 64 float4 of shared memory per warp.
-__device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col) {
+__device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col, uint32_t* nws) {
   const int lane = threadIdx.x & 31;
   const int E1 = P.eta + 1;
   float res = 0.f;
@@ -511,22 +511,52 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   uint32_t valid = vi ? vmask : 0u;
   if (I == J) valid &= (lane == 31) ? 0u : (~0u << (lane + 1));  // pairs i < j
   uint32_t nword = 0u;
-  // pairs active in the last iteration: finish step 7, test n = z - u exactly
-  for (uint32_t pend = word; pend; pend &= pend - 1u) {
-    const int c = __ffs(pend) - 1;
-    const size_t fid = row * TILE + c;
-    const float4 cb = col[32 + c];
-    const float rjc = col[c].w;
-    const float4 a = P.ulo[fid], b = P.uhi[fid], xa = P.xlo[fid], xb = P.xhi[fid];
-    const float2 uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zil, P.alpha, res);
-    const float2 ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), lo2(cb), P.alpha, res);
-    const float2 uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zih, P.alpha, res);
-    const float2 ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), hi2(cb), P.alpha, res);
-    if (collides((lo2(cb) - ujl) - (zil - uil), (hi2(cb) - ujh) - (zih - uih), ri + rjc)) {
-      P.ulo[fid] = pack(uil, ujl);
-      P.uhi[fid] = pack(uih, ujh);
-      nword |= 1u << c;
+  // pairs active in the last iteration: finish step 7, test n = z - u
+  // exactly.  They are dealt over the whole warp, one pair per lane per
+  // round, so that their u / x loads overlap (a row's own pairs would be
+  // fetched one after another); the activity bits come back through nws.
+  unsigned pincl = __popc(word);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(FULL, pincl, o);
+    if (lane >= o) pincl += v;
+  }
+  const unsigned ptot = __shfl_sync(FULL, pincl, 31);
+  if (ptot) {
+    nws[lane] = 0u;
+    __syncwarp();
+    for (unsigned base = 0; base < ptot; base += 32) {  // warp-uniform
+      const unsigned g = base + lane;
+      int r = 0;  // the row of pair g: the first lane whose inclusive count exceeds g
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(FULL, pincl, r + step - 1) <= g) r += step;
+      const uint32_t wr = __shfl_sync(FULL, word, r);
+      const unsigned first = __shfl_sync(FULL, pincl, r) - __popc(wr);
+      const float2 zrl = mk(__shfl_sync(FULL, zil.x, r), __shfl_sync(FULL, zil.y, r));
+      const float2 zrh = mk(__shfl_sync(FULL, zih.x, r), __shfl_sync(FULL, zih.y, r));
+      const float rr = __shfl_sync(FULL, ri, r);
+      if (g < ptot) {
+        uint32_t w = wr;
+        for (unsigned q = first; q < g; ++q) w &= w - 1u;
+        const int c = __ffs(w) - 1;
+        const size_t fid = ((size_t)blk * TILE + r) * TILE + c;
+        const float4 cb = col[32 + c];
+        const float rjc = col[c].w;
+        const float4 a = P.ulo[fid], b = P.uhi[fid], xa = P.xlo[fid], xb = P.xhi[fid];
+        const float2 uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zrl, P.alpha, res);
+        const float2 ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), lo2(cb), P.alpha, res);
+        const float2 uih = finish_u(true, pin_hi, false, lo2(b), lo2(xb), zrh, P.alpha, res);
+        const float2 ujh = finish_u(true, pin_hi, false, hi2(b), hi2(xb), hi2(cb), P.alpha, res);
+        if (collides((lo2(cb) - ujl) - (zrl - uil), (hi2(cb) - ujh) - (zrh - uih), rr + rjc)) {
+          P.ulo[fid] = pack(uil, ujl);
+          P.uhi[fid] = pack(uih, ujh);
+          atomicOr(&nws[r], 1u << c);
+        }
+      }
     }
+    __syncwarp();
+    nword = nws[lane];
   }
   // every other valid pair: u = 0, n = z.  The bounding circles of all 32
   // columns first (branch-free), then the exact test on the near ones.
