@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(32 * TEST_WARPS, 8) test_kernel(Dev P, int nse
 // sets the occupancy; the kinetic and wall blocks spill a little under it.
 constexpr int TILES_PER_CTA = 4;
 __global__ void __launch_bounds__(32 * TILES_PER_CTA, 10) test_rows_kernel(Dev P, int nseg) {
-  __shared__ float4 col[TILES_PER_CTA][64];
+  __shared__ float4 col[TILES_PER_CTA][72];
   __shared__ uint32_t nws[TILES_PER_CTA][32];
   pdl_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
@@ -2003,7 +2003,7 @@ __global__ void __launch_bounds__(32 * TILES_PER_CTA) batch_test_rows_kernel(con
                                                                          int n, int ntiles,
                                                                          const uint8_t* frozen) {
   __shared__ Dev sP[TILES_PER_CTA];
-  __shared__ float4 col[TILES_PER_CTA][64];
+  __shared__ float4 col[TILES_PER_CTA][72];
   __shared__ uint32_t nws[TILES_PER_CTA][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * TILES_PER_CTA + warp;

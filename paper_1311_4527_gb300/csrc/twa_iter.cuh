@@ -476,6 +476,20 @@ __device__ __forceinline__ void test_block(const Dev& P, int blk) {
 // bounding-circle early out before the exact test.  Same decisions and
 // stores as test_block<false>; only the worklist order differs.
 // col: 64 float4 of shared memory per warp.
+// Bounding-circle filter of pass 1.  Agent i's segment lies in the disk of
+// centre m_i (its midpoint) and radius b_i (half its length plus r_i), so a
+// pair can only collide when |m_i - m_j| <= b_i + b_j, i.e. when
+//     m_i . m_j + b_i b_j >= Q_i / 2 + Q_j / 2,   Q = |m|^2 - b^2.
+// With a_i = Q_i / 2 - 2e-6 (|m_i|^2 + b_i^2) the test is
+// m_i . m_j + b_i b_j - a_i >= a_j.  The margin, 4e-6 of the magnitudes
+// involved, is about ten times the rounding of the expression and of the
+// bounding radii, so the filter never drops a pair that the exact test would
+// find colliding: the outcome is that of testing every pair exactly.
+__device__ __forceinline__ float bounding_offset(float2 m, float b) {
+  const float mm = dot(m, m), bb = b * b;
+  return 0.5f * (mm - bb) - 2e-6f * (mm + bb);
+}
+
 __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col, uint32_t* nws) {
   const int lane = threadIdx.x & 31;
   const int E1 = P.eta + 1;
@@ -484,7 +498,9 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   int I, J;
   tile_of(P.nt, blk - s * P.ntp, I, J);
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-  // column agents: (midpoint, bounding radius, r_j) and (z lo, z hi)
+  // column agents: (midpoint, bounding radius, bounding_offset), (z lo, z hi)
+  // and r_j (col holds 72 float4: the last 8 are the 32 radii)
+  float* rcol = reinterpret_cast<float*>(col + 64);
   const int j = J * TILE + lane;
   const bool vj = j < P.p;
   float2 zjl = mk(0.f, 0.f), zjh = zjl;
@@ -492,8 +508,10 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
   {
     const float2 m = 0.5f * (zjl + zjh);
-    col[lane] = make_float4(m.x, m.y, 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj, rj);
+    const float b = 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj;
+    col[lane] = make_float4(m.x, m.y, b, bounding_offset(m, b));
     col[32 + lane] = pack(zjl, zjh);
+    rcol[lane] = rj;
   }
   const uint32_t vmask = __ballot_sync(FULL, vj);
   __syncwarp();
@@ -542,7 +560,7 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
         const int c = __ffs(w) - 1;
         const size_t fid = ((size_t)blk * TILE + r) * TILE + c;
         const float4 cb = col[32 + c];
-        const float rjc = col[c].w;
+        const float rjc = rcol[c];
         const float4 a = P.ulo[fid], b = P.uhi[fid], xa = P.xlo[fid], xb = P.xhi[fid];
         const float2 uil = finish_u(true, pin_lo, false, lo2(a), lo2(xa), zrl, P.alpha, res);
         const float2 ujl = finish_u(true, pin_lo, false, hi2(a), hi2(xa), lo2(cb), P.alpha, res);
@@ -564,18 +582,19 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   if (__any_sync(FULL, rest != 0u)) {
     const float2 mi = 0.5f * (zil + zih);
     const float bi = 0.5f * sqrtf(dot(zih - zil, zih - zil)) + ri;
+    const float ai = bounding_offset(mi, bi);
     uint32_t near = 0u;
 #pragma unroll
     for (int c = 0; c < TILE; ++c) {
       const float4 A = col[c];
-      const float2 dm = mk(A.x, A.y) - mi;
-      const float br = bi + A.z;
-      near |= (dot(dm, dm) <= br * br * 1.00002f) ? (1u << c) : 0u;
+      // m_i . m_j + b_i b_j - a_i >= a_j: three FMAs and a compare per pair
+      const float t = fmaf(mi.x, A.x, fmaf(mi.y, A.y, fmaf(bi, A.z, -ai)));
+      near |= (t >= A.w) ? (1u << c) : 0u;
     }
     for (near &= rest; near; near &= near - 1u) {
       const int c = __ffs(near) - 1;
       const float4 B = col[32 + c];
-      if (collides(lo2(B) - zil, hi2(B) - zih, ri + col[c].w)) {
+      if (collides(lo2(B) - zil, hi2(B) - zih, ri + rcol[c])) {
         // a newly active pair starts from u = 0 (the slot may hold an old u)
         const size_t fid = row * TILE + c;
         P.ulo[fid] = make_float4(0.f, 0.f, 0.f, 0.f);

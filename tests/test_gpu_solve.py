@@ -54,16 +54,23 @@ def test_circle100_solve_is_feasible_when_converged():
     assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
 
 
-def test_dense_and_gated_state_are_bitwise_identical():
+@pytest.mark.parametrize("name", ["circle100", "square256"])
+def test_dense_and_gated_state_are_bitwise_identical(name):
+    """The gated state's bounding-circle filter drops no pair the exact test
+    would find active: both modes take the same branches everywhere (unit
+    circle, and a 40 x 40-scale square where the filter's margin is set by
+    large coordinates)."""
     import paper_1311_4527_gb300 as pk
-    inst = workloads.circle100()
-    zs = []
+    inst = workloads.circle100() if name == "circle100" else workloads.small_square(256, 8, seed=5, side=40.0)
+    zs, acts = [], []
     for flags in (0, pk.PLAN_DENSE_STATE):
         pl = pk.Planner.from_instance(inst, flags=flags)
         pl.iterate(150)
         zs.append(pl.trajectory().cpu().numpy())
+        acts.append(pl.info()["active_coll"])
         pl.close()
     assert np.array_equal(zs[0], zs[1])
+    assert acts[0] == acts[1]
 
 
 def test_runs_are_deterministic():
