@@ -82,7 +82,8 @@ struct Dev {
   const float* fix;      // fixed-point scale (a power of two) and |m| bound
   unsigned* res_cur;     // residual slot of this iteration (consensus part)
   unsigned* res_prev;    // residual slot of the previous iteration (primal part)
-  unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction
+  unsigned* status;      // bit 0: a pinned wall minimizer had no separating direction;
+                         // bit 1: a message out of the fixed-point range
 };
 
 __device__ __forceinline__ float maxabs2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
@@ -533,14 +534,14 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   // exactly.  They are dealt over the whole warp, one pair per lane per
   // round, so that their u / x loads overlap (a row's own pairs would be
   // fetched one after another); the activity bits come back through nws.
-  unsigned pincl = __popc(word);
+  if (__any_sync(FULL, word != 0u)) {
+    unsigned pincl = __popc(word);
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned v = __shfl_up_sync(FULL, pincl, o);
-    if (lane >= o) pincl += v;
-  }
-  const unsigned ptot = __shfl_sync(FULL, pincl, 31);
-  if (ptot) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(FULL, pincl, o);
+      if (lane >= o) pincl += v;
+    }
+    const unsigned ptot = __shfl_sync(FULL, pincl, 31);
     nws[lane] = 0u;
     __syncwarp();
     for (unsigned base = 0; base < ptot; base += 32) {  // warp-uniform
@@ -605,15 +606,15 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   }
   if (vi && nword != word) P.bits[row] = nword;
   // worklist: warp prefix sum of the rows' active counts, one atomic per warp
-  const unsigned cnt = __popc(nword);
-  unsigned incl = cnt;
+  if (__any_sync(FULL, nword != 0u)) {
+    const unsigned cnt = __popc(nword);
+    unsigned incl = cnt;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned v = __shfl_up_sync(FULL, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const unsigned total = __shfl_sync(FULL, incl, 31);
-  if (total) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(FULL, incl, 31);
     unsigned base = 0;
     if (lane == 31) base = atomicAdd(P.work_count, total);
     base = __shfl_sync(FULL, base, 31) + (incl - cnt);
