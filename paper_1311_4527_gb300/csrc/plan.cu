@@ -63,10 +63,11 @@ __global__ void __launch_bounds__(32 * TEST_WARPS, 8) test_kernel(Dev P, int nse
 // Gated state: one warp per tile, lane = row agent (test_tile_rows).  The
 // register cap keeps the collision blocks at their own count (48), which
 // sets the occupancy; the kinetic and wall blocks spill a little under it.
-constexpr int TILES_PER_CTA = 4;
-__global__ void __launch_bounds__(32 * TILES_PER_CTA, 10) test_rows_kernel(Dev P, int nseg) {
-  __shared__ float4 col[TILES_PER_CTA][72];
-  __shared__ uint32_t nws[TILES_PER_CTA][32];
+constexpr int TILES_PER_CTA = 4;  // the batched test pass
+constexpr int ROWS_WARPS = 4;     // tiles (warps) per CTA of test_rows_kernel (2 and 8 measured slower)
+__global__ void __launch_bounds__(32 * ROWS_WARPS, 40 / ROWS_WARPS) test_rows_kernel(Dev P, int nseg) {
+  __shared__ float4 col[ROWS_WARPS][72];
+  __shared__ uint32_t nws[ROWS_WARPS][32];
   pdl_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.res_cur = 0u;
   if ((int)blockIdx.x < nseg) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(32 * TILES_PER_CTA, 10) test_rows_kernel(Dev P
   // tiles are dispatched segment-minor (t -> segment t mod eta), so that the
   // tiles of a crowded segment spread over the whole launch instead of all
   // landing in its last wave
-  const int t = ((int)blockIdx.x - nseg) * TILES_PER_CTA + warp;
+  const int t = ((int)blockIdx.x - nseg) * ROWS_WARPS + warp;
   if (t >= P.eta * P.ntp) return;  // warp-uniform
   const int s = t % P.eta;
   if (P.vo && s != 0) return;  // no collision factors on the second segment
@@ -860,8 +861,8 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   if (P.dense)
     CK(launch_pdl(test_kernel<true>, nseg + grid, 32 * TEST_WARPS, ms, P, nseg));
   else
-    CK(launch_pdl(test_rows_kernel, nseg + (grid + TILES_PER_CTA - 1) / TILES_PER_CTA,
-                  32 * TILES_PER_CTA, ms, P, nseg));
+    CK(launch_pdl(test_rows_kernel, nseg + (grid + ROWS_WARPS - 1) / ROWS_WARPS,
+                  32 * ROWS_WARPS, ms, P, nseg));
   if (prof) CK(cudaEventRecord(h->pev[1], ms));
   CK(launch_pdl(prox_kernel, h->prox_grid, 256, ms, P));
   if (prof) CK(cudaEventRecord(h->pev[2], ms));

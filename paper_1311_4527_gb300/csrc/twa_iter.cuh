@@ -620,8 +620,10 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
     base = __shfl_sync(FULL, base, 31) + (incl - cnt);
     for (uint32_t w = nword; w; w &= w - 1u) P.work[base++] = (uint32_t)(row * TILE + (__ffs(w) - 1));
   }
-  res = warp_max(res);
-  if (lane == 0 && res > 0.f && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+  if (__any_sync(FULL, res > 0.f)) {  // only pairs active before have a residual
+    res = warp_max(res);
+    if (lane == 0 && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+  }
 }
 
 // Kinetic and wall factors (steps 1-3 and the pending step 7) of one segment
