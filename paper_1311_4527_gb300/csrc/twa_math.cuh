@@ -64,13 +64,24 @@ TWA_DEV float dot(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
 TWA_DEV float cross(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
 TWA_DEV float2 perp(float2 a) { return mk(-a.y, a.x); }
 TWA_DEV float2 normalized(float2 a) {
+#ifdef __CUDA_ARCH__
+  // one reciprocal square root (2 ulp) where |a|^2 is a normal float; the
+  // directions are unit to a few ulp either way
+  const float dd = a.x * a.x + a.y * a.y;
+  if (dd > 1e-30f && dd < 1e30f) {
+    const float s = rsqrtf(dd);
+    return mk(a.x * s, a.y * s);
+  }
+#endif
   float n = hypotf(a.x, a.y);
   return n > 0.f ? mk(a.x / n, a.y / n) : mk(1.f, 0.f);
 }
 
-// Fast division and reciprocal square root for the inner iterations of the
-// secular equations, which correct their own rounding; results use the
-// accurate operations.  The host build (test harness) uses the plain ones.
+// Fast division (2 ulp for divisors of normal magnitude; every divisor here
+// is a length, a curvature or a secular variable far from the float limits)
+// and reciprocal square root, for the secular iterations and the direction
+// arithmetic of the minimizers: fewer instructions on their long dependent
+// chains.  The host build (test harness) uses the plain operations.
 TWA_DEV float fdiv(float a, float b) {
 #ifdef __CUDA_ARCH__
   return __fdividef(a, b);
@@ -230,8 +241,8 @@ TWA_NOINLINE int trs_global(float2 a, float2 b, float wl, float wh, float R,
     if (fabsf(tn - t) <= 1e-6f * t || hi - lo <= 1e-6f * hi) { t = tn; break; }
     t = tn;
   }
-  float p1 = (t > 0.f) ? R * s1 / t : copysignf(INFINITY, s1);
-  float p2 = R * s2 / (d + t);
+  float p1 = (t > 0.f) ? fdiv(R * s1, t) : copysignf(INFINITY, s1);
+  float p2 = fdiv(R * s2, d + t);
   float n1, n2;
   if (fabsf(p1) <= fabsf(p2)) {
     n1 = p1;
@@ -315,7 +326,7 @@ TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, floa
       t = tn;
       if (done) break;
     }
-    float p1 = -R * s1 / t, p2 = R * s2 / (d - t);
+    float p1 = fdiv(-R * s1, t), p2 = fdiv(R * s2, d - t);
     float n1, n2;
     if (fabsf(p1) <= fabsf(p2)) { n1 = p1; n2 = copysignf(sqrtf(fmaxf(0.f, 1.f - p1 * p1)), p2); }
     else { n2 = p2; n1 = copysignf(sqrtf(fmaxf(0.f, 1.f - p2 * p2)), p1); }
@@ -328,7 +339,7 @@ TWA_NOINLINE int trs_local(float2 a, float2 b, float wl, float wh, float R, floa
 TWA_DEV void tangent_normals(float2 q, float R, float2& t0, float2& t1) {
   float L2 = dot(q, q);
   float s = sqrtf(fmaxf(L2 - R * R, 0.f));
-  float inv = 1.f / L2;
+  float inv = fdiv(1.f, L2);
   float2 pq = perp(q);
   t0 = mk((R * q.x + s * pq.x) * inv, (R * q.y + s * pq.y) * inv);
   t1 = mk((R * q.x - s * pq.x) * inv, (R * q.y - s * pq.y) * inv);
@@ -339,7 +350,10 @@ TWA_DEV void tangent_normals(float2 q, float R, float2& t0, float2& t1) {
 TWA_DEV float2 arc_argmax(float2 q, float R, float2 w, bool& tangent) {
   float nw = hypotf(w.x, w.y);
   tangent = false;
-  if (nw > 0.f && dot(q, w) >= R * nw) return mk(w.x / nw, w.y / nw);
+  if (nw > 0.f && dot(q, w) >= R * nw) {
+    const float inv = fdiv(1.f, nw);
+    return mk(w.x * inv, w.y * inv);
+  }
   tangent = true;
   float2 t0, t1;
   tangent_normals(q, R, t0, t1);
