@@ -75,14 +75,23 @@ __global__ void __launch_bounds__(32 * ROWS_WARPS, 40 / ROWS_WARPS) test_rows_ke
     return;
   }
   const int warp = threadIdx.x >> 5;
-  // tiles are dispatched segment-minor (t -> segment t mod eta), so that the
-  // tiles of a crowded segment spread over the whole launch instead of all
-  // landing in its last wave
+  // the first hcap warps take the tiles listed heavy by the previous
+  // iteration; the others go through every tile segment-minor (t -> segment
+  // t mod eta, so that a crowded segment spreads over the launch), skipping
+  // the listed ones
   const int t = ((int)blockIdx.x - nseg) * ROWS_WARPS + warp;
-  if (t >= P.eta * P.ntp) return;  // warp-uniform
-  const int s = t % P.eta;
-  if (P.vo && s != 0) return;  // no collision factors on the second segment
-  const int blk = s * P.ntp + t / P.eta;
+  int blk;
+  if (t < P.hcap) {
+    if (t >= (int)*P.hcount_cur) return;  // warp-uniform
+    blk = (int)P.heavy_cur[t];
+  } else {
+    const int tr = t - P.hcap;
+    if (tr >= P.eta * P.ntp) return;  // warp-uniform
+    const int s = tr % P.eta;
+    if (P.vo && s != 0) return;  // no collision factors on the second segment
+    blk = s * P.ntp + tr / P.eta;
+    if (P.hcap && P.tile_stamp[blk] == *P.iter) return;  // taken by a heavy warp
+  }
   test_tile_rows(P, blk, col[warp], nws[warp]);
 }
 
@@ -132,6 +141,10 @@ __global__ void consensus_kernel(Dev P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *P.work_count_next = 0u;
     *P.wwork_count_next = 0u;
+    if (P.hcap) {
+      *P.hcount_cur = 0u;  // read by this iteration's pass 1; the next-but-one builds into it
+      *P.iter += 1u;
+    }
   }
   float dz = 0.f;
   bool bad = false;
@@ -594,8 +607,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
-  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, accx, accy,
-      accc, fix,
+  size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, sched,
+      stamps, heavy, accx, accy, accc, fix,
       res, status, count;
   size_t total;
 };
@@ -608,6 +621,9 @@ bool sizes_ok(const plan_config* c) {
   if ((unsigned long long)c->eta * ntp * TILE * TILE > 0xffffffffull) return false;
   return true;
 }
+
+// Heavy-tile slots at the front of pass 1: an eighth of the tiles.
+size_t heavy_cap(size_t ntiles) { return std::max<size_t>(32, ntiles / 8); }
 
 Layout layout_for(const plan_config* c) {
   const size_t p = c->p, eta = c->eta, nw = c->n_walls;
@@ -641,6 +657,9 @@ Layout layout_for(const plan_config* c) {
   L.work = take(slots * 4);
   L.wwork = take(nw * eta * p * 4);
   L.wcount = take(4 * 4);  // collision and wall worklist counters, by iteration parity
+  L.sched = take(4 * 4);   // iteration number, heavy-tile counts by parity
+  L.stamps = take(eta * ntp * 4);
+  L.heavy = take(2 * heavy_cap(eta * ntp) * 4);
   L.accx = take(p * (eta + 1) * 8);
   L.accy = take(p * (eta + 1) * 8);
   L.accc = take(p * (eta + 1) * 4);
@@ -801,6 +820,16 @@ struct plan_s {
     P.wwork = at<uint32_t>(L.wwork);
     P.wwork_count = at<unsigned>(L.wcount) + 2 + (kk & 1);
     P.wwork_count_next = at<unsigned>(L.wcount) + 2 + ((kk + 1) & 1);
+    {
+      const size_t cap = heavy_cap((size_t)eta * ntp);
+      P.hcap = (int)cap;
+      P.iter = at<unsigned>(L.sched);
+      P.hcount_cur = at<unsigned>(L.sched) + 1 + (kk & 1);
+      P.hcount_next = at<unsigned>(L.sched) + 1 + ((kk + 1) & 1);
+      P.heavy_cur = at<uint32_t>(L.heavy) + (kk & 1) * cap;
+      P.heavy_next = at<uint32_t>(L.heavy) + ((kk + 1) & 1) * cap;
+      P.tile_stamp = at<unsigned>(L.stamps);
+    }
     P.accx = at<unsigned long long>(L.accx);
     P.accy = at<unsigned long long>(L.accy);
     P.accc = at<unsigned>(L.accc);
@@ -861,7 +890,7 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   if (P.dense)
     CK(launch_pdl(test_kernel<true>, nseg + grid, 32 * TEST_WARPS, ms, P, nseg));
   else
-    CK(launch_pdl(test_rows_kernel, nseg + (grid + ROWS_WARPS - 1) / ROWS_WARPS,
+    CK(launch_pdl(test_rows_kernel, nseg + (P.hcap + grid + ROWS_WARPS - 1) / ROWS_WARPS,
                   32 * ROWS_WARPS, ms, P, nseg));
   if (prof) CK(cudaEventRecord(h->pev[1], ms));
   CK(launch_pdl(prox_kernel, h->prox_grid, 256, ms, P));
@@ -1040,6 +1069,8 @@ plan_status plan_reset(plan_t h) {
   }
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1291,6 +1322,8 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   if (wst != PLAN_OK) return wst;
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1499,6 +1532,12 @@ plan_status snapshot(plan_t h, const AdjLayout& A, int idx, bool save) {
     char* ws = h->ws + r.off;
     CK(cudaMemcpyAsync(save ? ck : ws, save ? ws : ck, r.bytes, cudaMemcpyDeviceToDevice, h->stream));
     ck += a256(r.bytes);
+  }
+  if (!save) {
+    // the pass-1 heavy-tile lists belong to the iteration order that ran, not
+    // to the restored state: start over with none (results do not depend on it)
+    CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
+    CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
   }
   return PLAN_OK;
 }
@@ -2133,6 +2172,7 @@ plan_status batch_tables(plan_batch_s* B) {
       h->k = kk;
       h->cur = (h->eta > 1) ? (kk & 1) : 0;
       d[b] = h->dev(kk);
+      d[b].hcap = 0;  // the batched test pass keeps its own order
       // the table serves every later iteration of this parity, so the
       // previous iteration's residual slot is always the other one
       d[b].res_prev = h->at<unsigned>(h->L.res) + ((kk + 1) & 1);

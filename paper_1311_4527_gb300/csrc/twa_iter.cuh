@@ -72,6 +72,17 @@ struct Dev {
   uint32_t* work;        // active collision slots of this iteration
   unsigned* work_count;  // their number
   unsigned* work_count_next;  // the counter the next iteration appends to
+  // pass-1 scheduling (single plans; hcap = 0 turns it off): tiles whose
+  // exact-test work was large in the previous iteration are listed and
+  // dispatched first, on the first hcap warps of the launch, and stamped so
+  // that their place in the ordinary order is skipped
+  int hcap;                    // heavy-tile slots at the front of the launch
+  const uint32_t* heavy_cur;   // this iteration's heavy tiles (built by the previous one)
+  unsigned* hcount_cur;        // their number (cleared by the consensus pass for reuse)
+  uint32_t* heavy_next;        // the next iteration's heavy tiles (built by this pass 1)
+  unsigned* hcount_next;
+  unsigned* tile_stamp;        // [eta ntp] iteration number for which the tile is listed heavy
+  unsigned* iter;              // iteration number (advanced by the consensus pass)
   uint32_t* wwork;       // active wall factors ((w eta + s) p + i) of this iteration whose
                          // minimizer runs in pass 2 (wall_prox_item_warp)
   unsigned* wwork_count;       // their number
@@ -491,6 +502,10 @@ __device__ __forceinline__ float bounding_offset(float2 m, float b) {
   return 0.5f * (mm - bb) - 2e-6f * (mm + bb);
 }
 
+// A tile with at least this many exact tests (pairs past the bounding-circle
+// filter plus pairs active before) is listed heavy for the next iteration.
+constexpr unsigned HEAVY_TESTS = 160;
+
 __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col, uint32_t* nws) {
   const int lane = threadIdx.x & 31;
   const int E1 = P.eta + 1;
@@ -580,6 +595,7 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   // every other valid pair: u = 0, n = z.  The bounding circles of all 32
   // columns first (branch-free), then the exact test on the near ones.
   const uint32_t rest = valid & ~word;
+  unsigned work = __popc(word);  // exact tests of this row (scheduling of the next iteration)
   if (__any_sync(FULL, rest != 0u)) {
     const float2 mi = 0.5f * (zil + zih);
     const float bi = 0.5f * sqrtf(dot(zih - zil, zih - zil)) + ri;
@@ -592,6 +608,7 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
       const float t = fmaf(mi.x, A.x, fmaf(mi.y, A.y, fmaf(bi, A.z, -ai)));
       near |= (t >= A.w) ? (1u << c) : 0u;
     }
+    work += __popc(near & rest);
     for (near &= rest; near; near &= near - 1u) {
       const int c = __ffs(near) - 1;
       const float4 B = col[32 + c];
@@ -623,6 +640,16 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   if (__any_sync(FULL, res > 0.f)) {  // only pairs active before have a residual
     res = warp_max(res);
     if (lane == 0 && P.res_prev) atomic_max_nonneg(P.res_prev, res);
+  }
+  if (P.hcap) {  // a heavy tile goes first in the next iteration
+    const unsigned total = __reduce_add_sync(FULL, work);
+    if (lane == 0 && total >= HEAVY_TESTS) {
+      const unsigned k = atomicAdd(P.hcount_next, 1u);
+      if (k < (unsigned)P.hcap) {
+        P.heavy_next[k] = (uint32_t)blk;
+        P.tile_stamp[blk] = *P.iter + 1u;
+      }
+    }
   }
 }
 
