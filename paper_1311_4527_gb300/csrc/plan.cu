@@ -914,7 +914,7 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
   return PLAN_OK;
 }
 
-// One iteration: replay a captured CUDA graph of the four kernels when one
+// One iteration: replay a captured CUDA graph of the three kernels when one
 // fits (past the rho warm-up, not profiling), else launch them directly.
 plan_status run_iteration(plan_t h) {
   plan_status st = ensure_prox_grid(h);
