@@ -54,14 +54,21 @@ def test_circle100_solve_is_feasible_when_converged():
     assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
 
 
-@pytest.mark.parametrize("name", ["circle100", "square256"])
+@pytest.mark.parametrize("name", ["circle100", "square256", "square1024"])
 def test_dense_and_gated_state_are_bitwise_identical(name):
     """The gated state's bounding-circle filter drops no pair the exact test
-    would find active: both modes take the same branches everywhere (unit
-    circle, and a 40 x 40-scale square where the filter's margin is set by
-    large coordinates)."""
+    would find active, and its tile order (crowded tiles of the previous
+    iteration first, the rest segment-minor) changes nothing: both modes take
+    the same branches everywhere (unit circle; a 40 x 40-scale square where
+    the filter's margin is set by large coordinates; the p = 1024 square,
+    whose crowded tiles are dispatched first)."""
     import paper_1311_4527_gb300 as pk
-    inst = workloads.circle100() if name == "circle100" else workloads.small_square(256, 8, seed=5, side=40.0)
+    if name == "circle100":
+        inst = workloads.circle100()
+    elif name == "square256":
+        inst = workloads.small_square(256, 8, seed=5, side=40.0)
+    else:
+        inst = workloads.square1024()
     zs, acts = [], []
     for flags in (0, pk.PLAN_DENSE_STATE):
         pl = pk.Planner.from_instance(inst, flags=flags)
