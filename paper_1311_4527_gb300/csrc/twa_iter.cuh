@@ -756,8 +756,10 @@ __device__ __forceinline__ void prox_item(const Dev& P, uint32_t fid) {
 // no incoming weight means z is unchanged).  Clears the sums for the next
 // iteration.
 __device__ __forceinline__ void consensus_node(const Dev& P, int t, float& dz, bool& bad) {
-  const int sp = 1 + t / P.p;
-  const int i = t - (sp - 1) * P.p;
+  // consecutive threads take consecutive break-points of one agent, which
+  // are adjacent in the [p][eta+1] arrays (coalesced)
+  const int i = t / (P.eta - 1);
+  const int sp = 1 + (t - i * (P.eta - 1));
   const size_t node = (size_t)i * (P.eta + 1) + sp;
   const unsigned status = *P.status;  // issued with the sums, not after them
   const long long sx = (long long)P.accx[node], sy = (long long)P.accy[node];
