@@ -42,6 +42,13 @@ void h_capsule_prox_free(const float* a, const float* b, float wl, float wh, con
   out[0] = vl.x; out[1] = vl.y; out[2] = vh.x; out[3] = vh.y;
 }
 
+// the capsule minimizer's rule for skipping an end circle's candidates
+int h_capsule_end_dominated(const float* a, const float* b, const float* c0, const float* c1,
+                            int ci) {
+  return capsule_end_dominated(mk(a[0], a[1]), mk(b[0], b[1]), mk(c0[0], c0[1]), mk(c1[0], c1[1]),
+                               ci) ? 1 : 0;
+}
+
 int h_capsule_prox_pinned(const float* q, const float* w, const float* c0, const float* c1, float r,
                           float* out) {
   float2 v;

@@ -118,6 +118,51 @@ def test_capsule_minimizer_matches_the_oracle(H):
     assert n > 500
 
 
+def test_capsule_end_circle_skip_is_sound(H):
+    """Where the FP32 wall minimizer skips an end circle's candidates, no
+    direction of that circle's half-plane (where it gives the capsule's
+    support) has a lower capsule energy than the better kink: checked in
+    FP64 on 4,096 directions of the half-plane, for walls long and short
+    and targets near the wall, past its ends and across its line."""
+    rng = np.random.default_rng(29)
+    th = np.linspace(0.0, 2 * np.pi, 4096, endpoint=False)
+    dirs = np.stack([np.cos(th), np.sin(th)], axis=1)
+    checked = 0
+    for k in range(3000):
+        if k % 2:
+            c0, c1 = _f32([0.0, 0.0]), _f32([rng.uniform(0.5, 40.0), 0.0])
+            a = _f32([rng.uniform(-3, c1[0] + 3), rng.uniform(-1.0, 1.0)])
+        else:
+            c0, c1 = _f32(rng.normal(size=(2, 2)) * 2)
+            a = _f32(rng.normal(size=2) * 2)
+        b = _f32(a + rng.normal(size=2) * 1.0)
+        r = float(np.float32(rng.uniform(0.1, 0.5)))
+        wl, wh = (0.5, 0.5) if k % 3 else (0.5, 1.5)
+        e = c1 - c0
+        nu = np.array([-e[1], e[0]]) / np.linalg.norm(e)
+
+        def energy(n):
+            h = np.maximum(n @ c0, n @ c1) + r
+            ga = np.maximum(h - n @ a, 0.0)
+            gb = np.maximum(h - n @ b, 0.0)
+            return 0.5 * wl * ga * ga + 0.5 * wh * gb * gb
+
+        kink = min(energy(nu[None])[0], energy(-nu[None])[0])
+        for ci in (0, 1):
+            A, pa = _a(a)
+            B, pb = _a(b)
+            C0, p0 = _a(c0)
+            C1, p1 = _a(c1)
+            if not H.h_capsule_end_dominated(pa, pb, p0, p1, ci):
+                continue
+            cc, other = (c1, c0) if ci else (c0, c1)
+            half = dirs[dirs @ (cc - other) >= 0.0]
+            emin = energy(half).min()
+            assert emin >= kink * (1 - 1e-9) - 1e-12, (a, b, c0, c1, r, ci, emin, kink)
+            checked += 1
+    assert checked > 1000
+
+
 def test_pinned_minimizers_match_the_oracle(H):
     rng = np.random.default_rng(23)
     zero = np.zeros(2)
