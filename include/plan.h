@@ -70,6 +70,11 @@ typedef enum {
                                             wall and velocity factors on segment 0 only, the
                                             kinetic factor C'_i |x - x_ref|^2 (cost_w,
                                             unnormalised) on segment 1 only */
+#define PLAN_U_LITERAL         (1u << 9) /* dual step u += (alpha / rho) (x - z) as printed in
+                                            App. B step 7, rho the value in force in that
+                                            iteration (warm_rho during the warm-up); without
+                                            it u += alpha (x - z) (the scaled-dual form, the
+                                            same when rho = 1) */
 
 typedef struct {
   int p;              /* agents, >= 1 */
@@ -173,6 +178,30 @@ typedef struct {
 
 /* Sizes and counters (synchronises to count the active factors). */
 plan_status plan_get_info(plan_t plan, plan_info* info);
+
+/*
+ * Final feasibility and cost check of the current break-points z, in FP64 on
+ * the device (the FP32 z promoted exactly):
+ *   total_cost         : sum over agents and kinetic segments of
+ *                        c_{i,s} |z_i(s+1) - z_i(s)|^2, the cost of Eq.
+ *                        velo_cost_pair_wise (c_{i,s} = C_{i,s} / (p eta), or
+ *                        C_{i,s} with PLAN_COST_UNNORM);
+ *   min_pair_clearance : min over pairs i < j and segments s of the smallest
+ *                        distance between the two agents along the segment
+ *                        (linear motion between break-points) divided by
+ *                        r_i + r_j; Eq. basic_opt_prob holds when it is >= 1
+ *                        (+inf when p = 1);
+ *   min_wall_clearance : min over walls, agents and segments of the distance
+ *                        between the agent's segment and the wall segment
+ *                        divided by r_i (+inf without walls);
+ *   max_endpoint_error : max over agents of |z_i(0) - start_i|_inf and
+ *                        |z_i(eta) - goal_i|_inf.
+ * For a PLAN_VO plan the clearances cover segment 0 and the cost segment 1
+ * (the local planner's graph).  All pointers are HOST doubles and may be
+ * NULL.  Synchronises.  Errors: PLAN_EINVAL (null plan), PLAN_ECUDA.
+ */
+plan_status plan_check(plan_t plan, double* total_cost, double* min_pair_clearance,
+                       double* min_wall_clearance, double* max_endpoint_error);
 
 /* Per-kernel timing of the next iterations (CUDA events on the plan's
  * stream).  enable = 1 starts collecting (and synchronises once per
@@ -343,7 +372,13 @@ plan_status plan_backward(plan_t plan, int K, const float* dL_dz, float* d_start
  * that device current; make that first call before any stream capture.
  * Every call reuses the same array, so calls whose work overlaps on the GPU
  * (other streams, other threads) race and must be serialised by the caller.
- * Work is enqueued on cuda_stream; the call does not synchronise.
+ * Work is enqueued on cuda_stream; the call does not synchronise, so a
+ * numeric failure cannot be returned as a status: when a message of the
+ * iteration is non-finite or beyond the fixed-point range of the consensus
+ * sums (the case plan_iterate reports as PLAN_ENUMERIC), every entry of z_out
+ * is set to NaN.  Errors returned: PLAN_EINVAL (null pointers, sizes, flags,
+ * rho0 / alpha / warm_rho not positive), PLAN_EUNSUPPORTED, PLAN_ENOMEM
+ * (problem too large for the array), PLAN_ECUDA.
  */
 #define PLAN_STATIC_SCRATCH_BYTES (16u << 20)
 plan_status plan_iterate_static(const plan_config* cfg, const float* start, const float* goal,

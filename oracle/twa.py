@@ -37,8 +37,10 @@ Fig. special_update_rules):
   infinity; 0 if all incoming weights are 0; rho0 otherwise;
 * u step (step 7): u += alpha (x - z) on an edge whose forward and back
   weights are both rho0 (the scaled-dual form; identical to the printed
-  alpha/rho0 form when rho0 = 1); every other edge resets u to 0, or keeps u
-  unchanged under ``u_keep``;
+  alpha/rho0 form when rho0 = 1), or u += (alpha / rho0) (x - z) as printed
+  under ``u_literal``, rho0 being the value in force in that iteration (the
+  warm-up value during the warm-up); every other edge resets u to 0, or keeps
+  u unchanged under ``u_keep``;
 * ties inside a minimizer go to the lowest energy, then the smallest angle
   (see ``oracle.prox``);
 * initial state: z = start for every break-point except the goal node,
@@ -75,6 +77,7 @@ class Problem:
     rho0: float = 1.0
     alpha: float = 0.1
     u_keep: bool = False
+    u_literal: bool = False     # u step (alpha / rho0)(x - z) as printed in App. B step 7
     cost_unnorm: bool = False
     admm: bool = False          # standard ADMM: every factor always sends rho0
     energy: bool = True         # kinetic-energy factors present
@@ -348,7 +351,7 @@ def iterate(prob: Problem, st: State, record_edges: bool = False, record_branche
     wb_new[:, eta] = WI
 
     # --- step 7: u update -------------------------------------------------
-    a = prob.alpha
+    a = prob.alpha / rho0 if prob.u_literal else prob.alpha
     primal = 0.0
     new = st.copy()
     new.z = z_new

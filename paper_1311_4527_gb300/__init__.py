@@ -22,7 +22,8 @@ from .build import LIB, build  # noqa: F401
 
 __all__ = ["Planner", "PlannerBatch", "PlanError", "load_library", "unrolled_trajectory",
            "PLAN_U_KEEP", "PLAN_COST_UNNORM", "PLAN_COST_PER_SEGMENT", "PLAN_DENSE_STATE",
-           "PLAN_ADMM", "PLAN_NO_ENERGY", "PLAN_VMAX", "PLAN_VMIN", "PLAN_VO", "EXPORTED_SYMBOLS"]
+           "PLAN_ADMM", "PLAN_NO_ENERGY", "PLAN_VMAX", "PLAN_VMIN", "PLAN_VO", "PLAN_U_LITERAL",
+           "EXPORTED_SYMBOLS"]
 
 PLAN_U_KEEP = 1 << 0
 PLAN_COST_UNNORM = 1 << 1
@@ -33,6 +34,7 @@ PLAN_NO_ENERGY = 1 << 5
 PLAN_VMAX = 1 << 6
 PLAN_VMIN = 1 << 7
 PLAN_VO = 1 << 8
+PLAN_U_LITERAL = 1 << 9
 
 STATUS = {0: "PLAN_OK", 1: "PLAN_EINVAL", 2: "PLAN_ENOMEM", 3: "PLAN_ECUDA", 4: "PLAN_ENOTCONV",
           5: "PLAN_ENUMERIC", 6: "PLAN_EINFEASIBLE_INPUT", 7: "PLAN_EUNSUPPORTED"}
@@ -46,7 +48,8 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_batch_set_shape", "plan_batch_destroy", "plan_set_params",
                     "plan_unroll", "plan_set_velocity_limits", "plan_export_velocity_state",
                     "plan_import_velocity_state", "plan_set_energy", "plan_export_back_weights",
-                    "plan_import_back_weights", "plan_vo_epoch", "plan_get_endpoints"]
+                    "plan_import_back_weights", "plan_vo_epoch", "plan_get_endpoints",
+                    "plan_check"]
 
 
 class PlanError(RuntimeError):
@@ -108,6 +111,8 @@ def load_library(path: str | None = None):
     lib.plan_get_endpoints.argtypes = [c_void_p, fp, fp]
     lib.plan_iterate_static.argtypes = [POINTER(plan_config)] + [c_void_p] * 15 + [c_int, c_void_p]
     lib.plan_profile.argtypes = [c_void_p, c_int, fp, POINTER(c_int)]
+    dp = POINTER(ctypes.c_double)
+    lib.plan_check.argtypes = [c_void_p, dp, dp, dp, dp]
     pp = POINTER(c_void_p)
     lib.plan_batch_workspace_size.argtypes = [c_int, POINTER(plan_config), POINTER(c_size_t)]
     lib.plan_batch_create.argtypes = [c_int, POINTER(plan_config), pp, pp, pp, pp, pp, c_void_p,
@@ -446,6 +451,15 @@ class Planner:
         n = c_int(0)
         _check(_lib.plan_profile(self._h, 0, ms, byref(n)))
         return dict(test=ms[0], minimizer=ms[1], consensus=ms[3], iterations=n.value)
+
+    def check(self):
+        """FP64 final check of the current break-points on the device:
+        total kinetic cost, smallest pair clearance / (r_i + r_j), smallest
+        wall clearance / r_i and largest endpoint error (plan_check)."""
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(_lib.plan_check(self._h, *(byref(x) for x in v)))
+        return dict(total_cost=v[0].value, min_pair_clearance=v[1].value,
+                    min_wall_clearance=v[2].value, max_endpoint_error=v[3].value)
 
     def info(self):
         inf = plan_info()

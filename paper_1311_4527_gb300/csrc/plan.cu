@@ -181,6 +181,140 @@ __global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// plan_check: the final feasibility and cost check in FP64 (Eq.
+// velo_cost_pair_wise, Eq. basic_opt_prob) on the FP32 break-points z^k.
+// Smallest clearances are kept as squared ratios; a non-negative double's bit
+// pattern orders like the double, so 64-bit atomicMin takes their minimum.
+
+// Squared distance from the origin to the segment a -> b.
+__device__ __forceinline__ double origin_seg_dist2(double ax, double ay, double bx, double by) {
+  const double dx = bx - ax, dy = by - ay, dd = dx * dx + dy * dy;
+  double t = dd > 0.0 ? -(ax * dx + ay * dy) / dd : 0.0;
+  t = fmin(1.0, fmax(0.0, t));
+  const double cx = ax + t * dx, cy = ay + t * dy;
+  return cx * cx + cy * cy;
+}
+
+__device__ __forceinline__ void block_min_u64(unsigned long long v, unsigned long long* out) {
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : ~0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w < v ? w : v;
+    }
+    if (lane == 0) atomicMin(out, v);
+  }
+}
+
+// One block per (segment s, agent tile pair): min over its pairs i < j of
+// dist^2 / (r_i + r_j)^2, dist the smallest distance between the agents
+// over the segment (the origin against their relative motion).
+__global__ void check_pairs_kernel(Dev P, unsigned long long* out) {
+  const int s = blockIdx.x / P.ntp, tp = blockIdx.x - s * P.ntp;
+  const int2 IJ = P.tiles[tp];
+  const int E1 = P.eta + 1;
+  double best = __longlong_as_double(0x7ff0000000000000ll);
+  for (int q = threadIdx.x; q < TILE * TILE; q += blockDim.x) {
+    const int i = IJ.x * TILE + (q >> 5), j = IJ.y * TILE + (q & 31);
+    if (i >= j || j >= P.p) continue;
+    const float2 zil = P.z[(size_t)i * E1 + s], zih = P.z[(size_t)i * E1 + s + 1];
+    const float2 zjl = P.z[(size_t)j * E1 + s], zjh = P.z[(size_t)j * E1 + s + 1];
+    const double ax = (double)zjl.x - (double)zil.x, ay = (double)zjl.y - (double)zil.y;
+    const double bx = (double)zjh.x - (double)zih.x, by = (double)zjh.y - (double)zih.y;
+    const double R = (double)P.radius[i] + (double)P.radius[j];
+    best = fmin(best, origin_seg_dist2(ax, ay, bx, by) / (R * R));
+  }
+  block_min_u64((unsigned long long)__double_as_longlong(best), out);
+}
+
+// Squared distance from point (px, py) to the segment a -> b.
+__device__ __forceinline__ double point_seg_dist2(double px, double py, double ax, double ay,
+                                                  double bx, double by) {
+  return origin_seg_dist2(ax - px, ay - py, bx - px, by - py);
+}
+
+// One thread per (wall, segment, agent): dist^2 / r_i^2, dist the distance
+// between the agent's segment and the wall segment (0 if they cross).
+__global__ void check_walls_kernel(Dev P, int nseg, unsigned long long* out) {
+  const int E1 = P.eta + 1;
+  double best = __longlong_as_double(0x7ff0000000000000ll);
+  const long long n = (long long)P.nw * nseg * P.p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % P.p);
+    const int s = (int)((t / P.p) % nseg);
+    const int w = (int)(t / ((long long)P.p * nseg));
+    const float4 W = P.walls[w];
+    const float2 a = P.z[(size_t)i * E1 + s], b = P.z[(size_t)i * E1 + s + 1];
+    const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+    const double cx = W.x, cy = W.y, dx = W.z, dy = W.w;
+    const double o1 = (dx - cx) * (ay - cy) - (dy - cy) * (ax - cx);
+    const double o2 = (dx - cx) * (by - cy) - (dy - cy) * (bx - cx);
+    const double o3 = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    const double o4 = (bx - ax) * (dy - ay) - (by - ay) * (dx - ax);
+    double d2;
+    if (((o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0)) &&
+        ((o3 > 0.0 && o4 < 0.0) || (o3 < 0.0 && o4 > 0.0))) {
+      d2 = 0.0;  // the segments cross
+    } else {
+      d2 = fmin(fmin(point_seg_dist2(ax, ay, cx, cy, dx, dy), point_seg_dist2(bx, by, cx, cy, dx, dy)),
+                fmin(point_seg_dist2(cx, cy, ax, ay, bx, by), point_seg_dist2(dx, dy, ax, ay, bx, by)));
+    }
+    const double r = P.radius[i];
+    best = fmin(best, d2 / (r * r));
+  }
+  block_min_u64((unsigned long long)__double_as_longlong(best), out);
+}
+
+// One block: the total kinetic cost sum c_{i,s} |z_i(s+1) - z_i(s)|^2 over
+// the kinetic segments (fixed summation order, so the result is
+// deterministic), the largest endpoint error |z - start|, |z - goal|, and
+// the two clearance minima set to +inf for the kernels that follow.
+__global__ void check_cost_kernel(Dev P, const double* ccost, const float2* start, const float2* goal,
+                                  int s_lo, int s_hi, double* out) {
+  __shared__ double sc[256], se[256];
+  const int E1 = P.eta + 1;
+  double c = 0.0, e = 0.0;
+  for (int t = threadIdx.x; t < P.p * P.eta; t += blockDim.x) {
+    const int i = t / P.eta, s = t - i * P.eta;
+    if (s >= s_lo && s < s_hi) {
+      const float2 a = P.z[(size_t)i * E1 + s], b = P.z[(size_t)i * E1 + s + 1];
+      const double dx = (double)b.x - (double)a.x, dy = (double)b.y - (double)a.y;
+      c += ccost[t] * (dx * dx + dy * dy);
+    }
+  }
+  for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
+    const float2 a = P.z[(size_t)i * E1], b = P.z[(size_t)i * E1 + P.eta];
+    e = fmax(e, fmax(fabs((double)a.x - (double)start[i].x), fabs((double)a.y - (double)start[i].y)));
+    e = fmax(e, fmax(fabs((double)b.x - (double)goal[i].x), fabs((double)b.y - (double)goal[i].y)));
+  }
+  sc[threadIdx.x] = c;
+  se[threadIdx.x] = e;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+      se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sc[0];
+    out[1] = __longlong_as_double(0x7ff0000000000000ll);
+    out[2] = __longlong_as_double(0x7ff0000000000000ll);
+    out[3] = se[0];
+  }
+}
+
 // Primal residual max |x^k - z^k| over weighted edges, without changing state
 // (the same finishing arithmetic the next factor_kernel will apply).
 __global__ void residual_kernel(Dev P) {
@@ -609,7 +743,7 @@ struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
   size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, sched,
       stamps, heavy, accx, accy, accc, fix,
-      res, status, count;
+      res, status, count, ccost, chk;
   size_t total;
 };
 
@@ -667,6 +801,8 @@ Layout layout_for(const plan_config* c) {
   L.res = take(4 * 4);
   L.status = take(4);
   L.count = take(16);
+  L.ccost = take(p * eta * 8);  // FP64 kinetic coefficients for plan_check
+  L.chk = take(4 * 8);          // plan_check results
   L.total = o;
   return L;
 }
@@ -783,6 +919,10 @@ struct plan_s {
   float rho_at(int kk) const {
     return (kk < cfg.warm_iters) ? cfg.warm_rho : cfg.rho0;
   }
+  // first iteration whose kernel arguments no longer change with k (graphs
+  // are captured from there): past the warm-up, and past the deferred dual
+  // step of its last iteration
+  int graph_from() const { return cfg.warm_iters > 0 ? cfg.warm_iters + 1 : 1; }
 
   Dev dev(int kk) const {
     Dev P{};
@@ -794,7 +934,9 @@ struct plan_s {
     P.vlim = at<float>(L.vlim);
     P.wnode = at<uint8_t>(L.wnode);
     P.rho = rho_at(kk);
-    P.alpha = cfg.alpha;
+    // pass 1 of iteration kk finishes the dual step of iteration kk - 1, so
+    // the printed step alpha / rho takes the rho of that iteration
+    P.alpha = (cfg.flags & PLAN_U_LITERAL) ? cfg.alpha / rho_at(kk > 0 ? kk - 1 : 0) : cfg.alpha;
     // keeping u on inactive edges (or standard ADMM, which updates every u)
     // needs every u record, so both imply the dense state
     P.dense = (cfg.flags & (PLAN_DENSE_STATE | PLAN_U_KEEP | PLAN_ADMM)) ? 1 : 0;
@@ -919,7 +1061,7 @@ plan_status enqueue_iteration(plan_t h, cudaStream_t ms) {
 plan_status run_iteration(plan_t h) {
   plan_status st = ensure_prox_grid(h);
   if (st != PLAN_OK) return st;
-  const bool graphable = h->cap && !h->profiling && h->k >= std::max(1, h->cfg.warm_iters);
+  const bool graphable = h->cap && !h->profiling && h->k >= h->graph_from();
   if (graphable) {
     const int key = ((h->k & 1) << 1) | h->cur;
     if (!h->gexec[key]) {
@@ -953,8 +1095,7 @@ constexpr int ITERS_PER_GRAPH = 8;
 plan_status run_iterations(plan_t h, int n) {
   plan_status st = ensure_prox_grid(h);
   if (st != PLAN_OK) return st;
-  while (n >= ITERS_PER_GRAPH && h->cap && !h->profiling &&
-         h->k >= std::max(1, h->cfg.warm_iters)) {
+  while (n >= ITERS_PER_GRAPH && h->cap && !h->profiling && h->k >= h->graph_from()) {
     const int key = ((h->k & 1) << 1) | h->cur;
     if (!h->gexec8[key]) {
       const int k0 = h->k, c0 = h->cur;
@@ -1005,10 +1146,12 @@ plan_status upload_inputs(plan_t h, const float* start, const float* goal, const
   const plan_config& c = h->cfg;
   const size_t p = c.p, eta = c.eta;
   std::vector<float> cost(p * eta);
+  std::vector<double> ccost(p * eta);
   const double norm = (c.flags & (PLAN_COST_UNNORM | PLAN_VO)) ? 1.0 : 1.0 / ((double)p * eta);
   for (size_t i = 0; i < p; ++i)
     for (size_t s = 0; s < eta; ++s) {
       double C = (c.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i];
+      ccost[i * eta + s] = C * norm;
       cost[i * eta + s] = (float)(C * norm);
     }
   std::vector<int2> tiles;
@@ -1018,6 +1161,7 @@ plan_status upload_inputs(plan_t h, const float* start, const float* goal, const
   CK(cudaMemcpyAsync(h->at<void>(h->L.goal), goal, p * 8, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->at<void>(h->L.radius), radius, p * 4, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->at<void>(h->L.cost), cost.data(), p * eta * 4, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->at<void>(h->L.ccost), ccost.data(), p * eta * 8, cudaMemcpyHostToDevice, h->stream));
   if (h->nw)
     CK(cudaMemcpyAsync(h->at<void>(h->L.walls), walls, (size_t)h->nw * 16, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->at<void>(h->L.tiles), tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice, h->stream));
@@ -1102,7 +1246,7 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
   if (cfg->max_iter < 0) return fail(PLAN_EINVAL, "max_iter must be >= 0");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
                          PLAN_DENSE_STATE | PLAN_ADMM | PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN |
-                         PLAN_VO;
+                         PLAN_VO | PLAN_U_LITERAL;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
   if ((cfg->flags & PLAN_VO) && (cfg->eta != 2 || (cfg->flags & (PLAN_ADMM | PLAN_NO_ENERGY))))
     return fail(PLAN_EINVAL, "PLAN_VO needs eta = 2 and the kinetic factors, without PLAN_ADMM");
@@ -1331,6 +1475,35 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   return PLAN_OK;
 }
 
+plan_status plan_check(plan_t h, double* total_cost, double* min_pair_clearance,
+                       double* min_wall_clearance, double* max_endpoint_error) {
+  if (!h) return fail(PLAN_EINVAL, "null plan");
+  Dev P = h->dev(h->k);
+  double* out = h->at<double>(h->L.chk);
+  // the local planner's graph: kinetic factor on segment 1, the rest on segment 0
+  const int s_lo = h->vo ? 1 : 0;
+  const int nseg = h->vo ? 1 : h->eta;
+  check_cost_kernel<<<1, 256, 0, h->stream>>>(P, h->at<double>(h->L.ccost), h->at<float2>(h->L.start),
+                                              h->at<float2>(h->L.goal), s_lo, h->eta, out);
+  if (h->p > 1)
+    check_pairs_kernel<<<(unsigned)(nseg * h->ntp), 256, 0, h->stream>>>(
+        P, reinterpret_cast<unsigned long long*>(out + 1));
+  if (h->nw) {
+    const long long n = (long long)h->nw * nseg * h->p;
+    check_walls_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, h->stream>>>(
+        P, nseg, reinterpret_cast<unsigned long long*>(out + 2));
+  }
+  CK(cudaGetLastError());
+  double v[4];
+  CK(cudaMemcpyAsync(v, out, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (total_cost) *total_cost = v[0];
+  if (min_pair_clearance) *min_pair_clearance = std::sqrt(v[1]);
+  if (min_wall_clearance) *min_wall_clearance = std::sqrt(v[2]);
+  if (max_endpoint_error) *max_endpoint_error = v[3];
+  return PLAN_OK;
+}
+
 plan_status plan_get_info(plan_t h, plan_info* info) {
   if (!h || !info) return fail(PLAN_EINVAL, "null argument");
   const long long p = h->p, eta = h->eta;
@@ -1545,7 +1718,8 @@ plan_status snapshot(plan_t h, const AdjLayout& A, int idx, bool save) {
 AdjDev adj_dev(plan_t h, const AdjLayout& A, int slot, int k, char* zb_in, char* zb_out) {
   AdjDev D{};
   D.p = h->p; D.eta = h->eta; D.ntp = h->ntp; D.k = k;
-  D.rho = h->cfg.rho0; D.alpha = h->cfg.alpha;
+  D.rho = h->cfg.rho0;
+  D.alpha = (h->cfg.flags & PLAN_U_LITERAL) ? h->cfg.alpha / h->cfg.rho0 : h->cfg.alpha;
   D.tiles = h->at<int2>(h->L.tiles);
   D.radius = h->at<float>(h->L.radius);
   D.cost = h->at<float>(h->L.cost);
@@ -1748,23 +1922,29 @@ plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) 
     if (st != PLAN_OK) return st;
   }
   std::vector<float> cost;
+  std::vector<double> ccost;
   if (cost_w) {
     if (!finite_all(cost_w, ncost)) return fail(PLAN_EINVAL, "non-finite cost_w");
     for (size_t i = 0; i < ncost; ++i)
       if (cost_w[i] < 0.f) return fail(PLAN_EINVAL, "cost_w[%zu] must be >= 0", i);
     const double norm = (h->cfg.flags & (PLAN_COST_UNNORM | PLAN_VO)) ? 1.0 : 1.0 / ((double)p * eta);
     cost.resize(p * eta);
+    ccost.resize(p * eta);
     for (size_t i = 0; i < p; ++i)
-      for (size_t s = 0; s < eta; ++s)
-        cost[i * eta + s] = (float)(norm * ((h->cfg.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i]));
+      for (size_t s = 0; s < eta; ++s) {
+        ccost[i * eta + s] = norm * ((h->cfg.flags & PLAN_COST_PER_SEGMENT) ? cost_w[i * eta + s] : cost_w[i]);
+        cost[i * eta + s] = (float)ccost[i * eta + s];
+      }
   }
   h->adj_valid = false;
   if (radius) {
     h->h_radius.assign(radius, radius + p);
     CK(cudaMemcpyAsync(h->at<void>(h->L.radius), radius, p * 4, cudaMemcpyHostToDevice, h->stream));
   }
-  if (cost_w)
+  if (cost_w) {
     CK(cudaMemcpyAsync(h->at<void>(h->L.cost), cost.data(), p * eta * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->at<void>(h->L.ccost), ccost.data(), p * eta * 8, cudaMemcpyHostToDevice, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return PLAN_OK;
 }
@@ -1911,6 +2091,16 @@ __global__ void static_prep_kernel(int p, int eta, int nt, int ntp, unsigned fla
   }
 }
 
+// A message out of the fixed-point range (status bit 1) was left out of the
+// consensus sums: the plan path reports that as a NaN residual
+// (PLAN_ENUMERIC); here every entry of z_out becomes NaN instead, so that a
+// caller without a residual still sees it.
+__global__ void static_poison_kernel(const unsigned* status, float* z_out, int n) {
+  if ((*status & 2u) == 0u) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    z_out[t] = __int_as_float(0x7fc00000);
+}
+
 plan_status static_scratch_for_current_device(void** out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1940,12 +2130,15 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
   if (!sizes_ok(cfg)) return fail(PLAN_EINVAL, "p, eta or n_walls out of range");
   if (cfg->p > 1 && (!u_coll_in || !u_coll_out)) return fail(PLAN_EINVAL, "null u_coll");
   if (cfg->n_walls > 0 && (!walls || !u_wall_in || !u_wall_out)) return fail(PLAN_EINVAL, "null wall array");
-  if (!(cfg->rho0 > 0.f) || !(cfg->alpha > 0.f)) return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
+  if (!(cfg->rho0 > 0.f) || !std::isfinite(cfg->rho0) || !(cfg->alpha > 0.f) || !std::isfinite(cfg->alpha))
+    return fail(PLAN_EINVAL, "rho0 and alpha must be positive");
+  if (cfg->warm_iters < 0 || (cfg->warm_iters > 0 && (!(cfg->warm_rho > 0.f) || !std::isfinite(cfg->warm_rho))))
+    return fail(PLAN_EINVAL, "warm_rho must be positive when warm_iters > 0");
   if (k < 0) return fail(PLAN_EINVAL, "k must be >= 0");
   if (cfg->flags & (PLAN_NO_ENERGY | PLAN_VMAX | PLAN_VMIN | PLAN_VO))
     return fail(PLAN_EUNSUPPORTED, "plan_iterate_static runs the energy problem without velocity factors");
   const unsigned known = PLAN_U_KEEP | PLAN_COST_UNNORM | PLAN_COST_PER_SEGMENT |
-                         PLAN_DENSE_STATE | PLAN_ADMM;
+                         PLAN_DENSE_STATE | PLAN_ADMM | PLAN_U_LITERAL;
   if (cfg->flags & ~known) return fail(PLAN_EINVAL, "unknown flag bits 0x%x", cfg->flags & ~known);
   const Layout L = layout_for(cfg);
   if (L.total > PLAN_STATIC_SCRATCH_BYTES)
@@ -1992,6 +2185,11 @@ plan_status plan_iterate_static(const plan_config* cfg, const float* start, cons
     st = plan_export_state(&h, z_out, h.p > 1 ? u_coll_out : nullptr, u_kin_out,
                            h.nw ? u_wall_out : nullptr, h.p > 1 ? act_coll_out : nullptr,
                            h.nw ? act_wall_out : nullptr, nullptr);
+  if (st == PLAN_OK) {
+    const int nz = 2 * h.p * (h.eta + 1);
+    static_poison_kernel<<<(nz + 255) / 256, 256, 0, h.stream>>>(h.at<unsigned>(L.status), z_out, nz);
+    CK(cudaGetLastError());
+  }
   return st;
 }
 
@@ -2318,7 +2516,7 @@ plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const
       return fail(st, "%s", msg);
     }
     B->m.push_back(h);
-    B->warm = std::max(B->warm, cfgs[b].warm_iters);
+    B->warm = std::max(B->warm, h->graph_from());
     off += sz;
   }
   char* t = B->ws + off;

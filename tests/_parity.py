@@ -3,6 +3,12 @@ that state into the CUDA planner, run one GPU iteration and compare.
 
 Tolerance: an FP32 entry matches when |gpu - oracle| <= TOL * L, with L the
 workload's coordinate scale max(1, |start|_inf, |goal|_inf, |walls|_inf).
+The bound is relative to the layout's scale, not to each entry: every u and
+x - z is a difference of coordinates of size up to L, each rounded to FP32
+(half an ulp of L, 6e-8 L), and the minimizers' and consensus' arithmetic on
+those coordinates adds a few ulps of L, so an entry of size 1e-3 L cannot be
+computed to 2e-5 of itself.  ``compare`` also reports, per array, the median
+and largest entrywise error relative to max(|oracle|, TOL * L).
 
 Branches.  A factor whose activity test sits within MARGIN of the collision
 distance, or whose minimizer has a runner-up direction within GAP in energy,
@@ -40,6 +46,11 @@ def make_planner(prob, flags=0, **kw):
     flags = flags | (pk.PLAN_COST_UNNORM if prob.cost_unnorm else 0)
     if prob.u_keep:
         flags |= pk.PLAN_U_KEEP
+    if prob.u_literal:
+        flags |= pk.PLAN_U_LITERAL
+    if prob.warm_iters:
+        kw.setdefault("warm_iters", prob.warm_iters)
+        kw.setdefault("warm_rho", prob.warm_rho)
     if prob.admm:
         flags |= pk.PLAN_ADMM
     return pk.Planner(prob.start, prob.goal, prob.radius, prob.eta, cost_w=cost,
@@ -129,9 +140,18 @@ def compare(prob, new, info, gpu, tol=TOL):
     wdiff = (gpu["wback"] != new.wback) & ~bad_node
     assert not wdiff.any(), f"{int(wdiff.sum())} break-points differ in back weight"
     # --- values --------------------------------------------------------------
+    def rel(name, d, ref, mask):
+        """Median and largest |d| / max(|ref|, TOL L) over the compared entries."""
+        if not mask.any():
+            return
+        r = (d / np.maximum(np.abs(ref), tol * L))[mask]
+        stats[name + "_relmed"] = float(np.median(r))
+        stats[name + "_relmax"] = float(np.max(r))
+
     dz = np.abs(gpu["z"] - new.z)
     worst = float(np.max(dz[~bad_node])) if (~bad_node).any() else 0.0
     stats["z_maxerr"] = worst / L
+    rel("z", dz, new.z, np.broadcast_to(~bad_node[..., None], dz.shape))
     assert worst <= tol * L, f"z error {worst} > {tol * L}"
     seg_bad = bad_node[:, :-1] | bad_node[:, 1:]            # (p, eta)
     ok = ~excl
@@ -140,6 +160,8 @@ def compare(prob, new, info, gpu, tol=TOL):
     du = np.abs(gpu["u_coll"] - new.u_coll)
     worst = float(np.max(du[ok])) if ok.any() else 0.0
     stats["u_coll_maxerr"] = worst / L
+    # entrywise: the u of factors active in the oracle (every other u is 0 on both sides)
+    rel("u_coll", du, new.u_coll, np.broadcast_to((ok & act_o)[..., None, None], du.shape))
     stats["coll_compared_active"] = int((ok & act_o).sum())
     assert worst <= tol * L, f"u_coll error {worst} > {tol * L}"
     kin_ok = ~seg_bad.T                                     # (eta, p)
@@ -152,6 +174,7 @@ def compare(prob, new, info, gpu, tol=TOL):
     dk = np.abs(gpu["u_kin"] - new.u_kin)
     worst = float(np.max(dk[kin_ok])) if kin_ok.any() else 0.0
     stats["u_kin_maxerr"] = worst / L
+    rel("u_kin", dk, new.u_kin, np.broadcast_to(kin_ok[..., None, None], dk.shape))
     assert worst <= tol * L, f"u_kin error {worst} > {tol * L}"
     if prob.n_walls:
         okw = ~wex & ~seg_bad.T[None, :, :]

@@ -109,6 +109,7 @@ def test_bad_parameters_are_rejected(lib):
 
 
 def test_differentiation_entry_points_reject_null_plans(lib):
+    assert lib.plan_check(None, None, None, None, None) == 1
     assert lib.plan_backward(None, 1, None, None, None, None, None) == 1
     assert lib.plan_unroll(None, 10, 0) == 1
     assert lib.plan_set_params(None, None, None) == 1
@@ -123,6 +124,20 @@ def test_static_entry_point_rejects_a_problem_that_does_not_fit(lib):
     code = lib.plan_iterate_static(ctypes.byref(cfg), *([ptr] * 15), 0, None)
     assert code == 2
     assert b"static array" in lib.plan_last_error()
+
+
+def test_static_entry_point_checks_its_parameters_first(lib):
+    """plan_iterate_static validates rho0, alpha and the warm-up like
+    plan_create, before any pointer is used."""
+    dummy = np.zeros(8, dtype=np.float32)
+    ptr = ctypes.c_void_p(dummy.ctypes.data)
+    for kw in (dict(rho0=float("nan")), dict(alpha=0.0), dict(warm_iters=5, warm_rho=0.0),
+               dict(warm_iters=5, warm_rho=float("nan")), dict(warm_iters=-1)):
+        cfg = pk.make_config(8, 4, **kw)
+        assert lib.plan_iterate_static(ctypes.byref(cfg), *([ptr] * 15), 0, None) == 1, kw
+    code, _ = _create(lib, _cfg(2, 4, warm_iters=5, warm_rho=0.0), [[0, 0], [3, 0]],
+                      [[5, 5], [0, 5]], [0.2, 0.2])
+    assert code == 1
 
 
 @pytest.mark.parametrize("seed", range(4))

@@ -1,7 +1,8 @@
 """GPU parity: one FP32 CUDA iteration from an oracle iterate against the FP64
 oracle's next iterate, entry by entry (see tests/_parity.py for the rules).
 Cases span one tile and several tiles with ragged tails, walls, fixed ends,
-the U_KEEP reading, and the dense-state streaming mode."""
+the U_KEEP reading, the printed (alpha / rho0) dual step with and without the
+rho warm-up, and the dense-state streaming mode."""
 import numpy as np
 import pytest
 
@@ -83,6 +84,24 @@ def test_single_agent_and_single_segment():
 def test_u_keep_reading_parity():
     prob = _prob(workloads.circle4(), u_keep=True)
     _run(prob, [0, 6, 30])
+
+
+def test_literal_dual_step_parity():
+    """App. B step 7 as printed, u += (alpha / rho0)(x - z), on the p = 100
+    circle, whose rho0 = 2 makes it differ from the scaled-dual step."""
+    prob = _prob(workloads.circle100(), u_literal=True)
+    stats = _run(prob, [0, 12])
+    for s in stats:
+        assert s["coll_excluded"] <= 0.02 * s["coll_active"], s
+    assert stats[-1]["coll_compared_active"] > 0
+
+
+def test_literal_dual_step_across_the_rho_warm_up():
+    """The warm-up of Section 4 (rho = warm_rho for the first iterations):
+    the first iteration after it finishes the last warm-up iteration's dual
+    step, which divides alpha by warm_rho."""
+    prob = _prob(workloads.circle4(), u_literal=True, warm_iters=3, warm_rho=0.25)
+    _run(prob, [0, 2, 3, 4, 9])
 
 
 def test_per_segment_costs_and_unnormalised_cost_parity():

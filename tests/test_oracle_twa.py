@@ -165,6 +165,44 @@ def test_inactive_factors_reset_u_or_keep_it():
         assert np.array_equal(st.u_coll[~info.active_coll], prev[~info.active_coll])
 
 
+def test_literal_dual_step_is_the_scaled_step_with_alpha_over_rho():
+    """App. B step 7 as printed, u += (alpha / rho0)(x - z): with rho0 = 1 it
+    is the scaled-dual step exactly; with rho0 = 2 it is that step with
+    alpha / 2 (the minimizers and the consensus do not see alpha); during a
+    warm-up it divides by the warm-up rho of each iteration."""
+    inst = workloads.circle4()
+    a = twa.Problem.from_instance(inst, u_literal=True)
+    b = twa.Problem.from_instance(inst)
+    sa, sb = twa.initial_state(a), twa.initial_state(b)
+    for _ in range(40):
+        sa, _ = twa.iterate(a, sa)
+        sb, _ = twa.iterate(b, sb)
+    assert np.array_equal(sa.z, sb.z) and np.array_equal(sa.u_coll, sb.u_coll)
+    a = twa.Problem.from_instance(inst, u_literal=True)
+    a.rho0 = 2.0
+    b = twa.Problem.from_instance(inst)
+    b.rho0, b.alpha = 2.0, inst.alpha / 2.0
+    sa, sb = twa.initial_state(a), twa.initial_state(b)
+    for _ in range(40):
+        sa, _ = twa.iterate(a, sa)
+        sb, _ = twa.iterate(b, sb)
+    assert np.allclose(sa.z, sb.z, atol=1e-13) and np.allclose(sa.u_kin, sb.u_kin, atol=1e-13)
+    # warm-up: the first 3 iterations divide alpha by warm_rho = 0.25 (4 alpha)
+    a = twa.Problem.from_instance(inst, u_literal=True, warm_iters=3, warm_rho=0.25)
+    b = twa.Problem.from_instance(inst, warm_iters=3, warm_rho=0.25)
+    b.alpha = 4.0 * inst.alpha
+    sa, sb = twa.initial_state(a), twa.initial_state(b)
+    for _ in range(3):
+        sa, _ = twa.iterate(a, sa)
+        sb, _ = twa.iterate(b, sb)
+    assert np.allclose(sa.u_kin, sb.u_kin, atol=1e-13) and np.any(sa.u_kin != 0.0)
+    b.alpha = inst.alpha
+    for _ in range(5):
+        sa, _ = twa.iterate(a, sa)
+        sb, _ = twa.iterate(b, sb)
+    assert np.allclose(sa.z, sb.z, atol=1e-13)
+
+
 def test_fixed_ends_stay_exact_and_edges_to_them_carry_no_u():
     inst = workloads.circle4()
     prob = twa.Problem.from_instance(inst)
