@@ -38,6 +38,10 @@ UNIT = "factor-updates/s"
 # the current pass-1 kernels on square1024_eta16, from one single-pass ncu
 # capture of two launches each (profiles/test_kernel_traffic_square1024.md).
 TRAFFIC_SQUARE1024 = {"gated": 9.972e6, "dense": 486.32e6}
+# Warp instructions executed per launch of the gated pass-1 kernel on
+# square1024_eta16 (smsp__inst_executed.sum of the same capture): the work
+# the issue-rate roofline divides by the kernel time.
+WARP_INST_SQUARE1024 = {"gated": 6.79e6}
 
 
 def factor_counts(inst):
@@ -69,9 +73,37 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def issue_peak_g(sm_mhz):
+    """Warp-instruction issue peak: SMs x 4 schedulers x one warp instruction
+    per cycle each x SM clock, in G warp instructions per second."""
+    return sm_count() * 4 * sm_mhz * 1e6 / 1e9
+
+
+def host_cpu():
+    """The host's logical core count and CPU model (lscpu / /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
 
 
 class Clocks:
@@ -133,24 +165,58 @@ def aggregate(ms_local, units_local, world, dist=None, device=None):
     return float(mx[0].item()), float(sm[1].item())
 
 
-def cpu_baseline(inst, budget_s=20.0):
-    """The FP64 oracle, as it stands, on this host: whole iterations of the
-    same workload, as many as fit the budget (at least one)."""
+def _oracle_worker(args):
+    """One process: the FP64 oracle, as it stands, on whole iterations of a
+    named workload from its iterate `first`, for about budget_s seconds.
+    Returns (iterations, seconds, active pairs of the timed iterations)."""
+    name, first, budget_s = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    import workloads as wl
     from oracle import twa
+    inst = wl.by_name(name)
     prob = twa.Problem.from_instance(inst)
     st = twa.initial_state(prob)
-    st, _ = twa.iterate(prob, st)  # untimed: reach a mid-solve iterate
-    total = sum(factor_counts(inst).values())
-    n, t0 = 0, time.perf_counter()
-    while True:
+    for _ in range(first):
         st, _ = twa.iterate(prob, st)
+    n, act, t0 = 0, [], time.perf_counter()
+    while True:
+        st, info = twa.iterate(prob, st)
         n += 1
+        act.append(int(info.active_coll.sum()))
         if time.perf_counter() - t0 >= budget_s:
             break
-    dt = time.perf_counter() - t0
+    return n, time.perf_counter() - t0, act
+
+
+def cpu_baseline(inst, budget_s=20.0):
+    """The FP64 oracle, as it stands, on this host: whole iterations of the
+    same workload from its iterate 2 (an iteration's cost hardly depends on
+    the iterate: the p(p-1)/2 x eta distance tests dominate it), first in one
+    process, then in one process per host core at once (the oracle is
+    single-threaded numpy, so all cores means that many oracle instances)."""
+    import multiprocessing as mp
+    from oracle import twa
+    total = sum(factor_counts(inst).values())
+    ncpu, model = host_cpu()
+    n, dt, act = _oracle_worker((inst.name, 2, budget_s))
     out = {"value": total * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{n} full oracle iteration(s) of {inst.name} (iterations 2..{n + 1}), "
-                     f"{dt:.1f} s, numpy FP64 single thread"}
+           "cpu": model, "host_cores": ncpu,
+           "sample": f"{n} full oracle iteration(s) of {inst.name} (iterations 3..{n + 2}), "
+                     f"{dt:.1f} s, numpy FP64 single thread; active pairs "
+                     f"{min(act)}..{max(act)}"}
+    # all cores: one oracle process per core, spawned (this process holds a CUDA context)
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_oracle_worker, [(inst.name, 2, budget_s)] * ncpu)
+        its = sum(r[0] for r in res)
+        span = max(r[1] for r in res)
+        out["all_cores"] = {"value": total * its / span, "unit": UNIT, "cores": ncpu,
+                            "sample": f"{ncpu} oracle processes at once, {its} iterations in "
+                                      f"{span:.1f} s (iterations 3.. of {inst.name} each)"}
+    except Exception as e:  # memory or process limits of the host
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
     # the oracle's own solve of the CPU-sized circle swap (time to converge)
     small = workloads.circle4()
     t0 = time.perf_counter()
@@ -181,8 +247,9 @@ def run_reference(args, inst):
     n = len(times)
     ms = 1e3 * sum(times) / n
     value = total / (ms / 1e3)
+    ncpu, model = host_cpu()
     sample = (f"{n} of {args.steps} requested iterations of {inst.name} (capped at {budget:.0f} s) "
-              f"after 1 untimed warm-up iteration; numpy FP64, single thread")
+              f"after 1 untimed warm-up iteration; numpy FP64, single thread of {ncpu} ({model})")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": n,
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -222,16 +289,11 @@ def kernel_times(pl, stream, steps, flush):
 
 
 def _plan_quality(pk, inst, pl):
-    """Total kinetic cost (Eq. velo_cost_pair_wise) and clearances of the
-    planner's current trajectory, measured on the GPU with torch ops."""
-    import torch
-    from paper_1311_4527_gb300 import losses
-    z = pl.trajectory().double()
-    dev = z.device
-    radius = torch.tensor(inst.radius, dtype=torch.float64, device=dev)
-    cost = torch.tensor(inst.cost_w, dtype=torch.float64, device=dev)
-    coll, wall = losses.min_clearance(z, radius, inst.walls if inst.n_walls else None)
-    return float(losses.kinetic_energy(z, cost)), coll, wall
+    """Total kinetic cost (Eq. velo_cost_pair_wise) and the smallest pair and
+    wall clearance ratios of the planner's current trajectory, from the FP64
+    device check (plan_check)."""
+    c = pl.check()
+    return c["total_cost"], c["min_pair_clearance"], c["min_wall_clearance"]
 
 
 def _solve_timed(pl):
@@ -243,18 +305,40 @@ def _solve_timed(pl):
     return conv, it, res, 1e3 * (time.perf_counter() - t0)
 
 
+# iteration caps and residual-check intervals of the time-to-converge runs:
+# the p = 100 circle needs about 154,000 iterations, the p = 1024 square
+# about 830,000
+CONVERGE = {"circle4_eta4": (20000, 10), "circle100_eta8": (300000, 1000),
+            "square1024_eta16": (1200000, 10000)}
+
+
 def time_to_converge(pk, names):
     """plan_solve to the workload's tolerance (or its iteration cap) on the
-    GPU, with the plan's cost and clearance."""
+    GPU, with the plan's cost and clearances from the FP64 device check; the
+    p = 100 circle also with the rho warm-up of Section 4 (rho = eta p 1e-5
+    for 20 iterations, then 1)."""
     out = {}
-    for name in names:
+    runs = [(name, name, {}) for name in names]
+    if "circle100_eta8" in names:
+        inst = workloads.by_name("circle100_eta8")
+        runs.append(("circle100_eta8_warmup", "circle100_eta8",
+                     dict(rho0=1.0, warm_iters=20, warm_rho=inst.eta * inst.p * 1e-5)))
+    for key, name, kw in runs:
         inst = workloads.by_name(name)
-        with pk.Planner.from_instance(inst, check_every=10) as pl:
+        cap, every = CONVERGE.get(name, (inst.max_iter, 10))
+        with pk.Planner.from_instance(inst, max_iter=cap, check_every=every, **kw) as pl:
             conv, it, res, ms = _solve_timed(pl)
-            cost, coll, wall = _plan_quality(pk, inst, pl)
-        out[name] = {"converged": conv, "iterations": it, "residual": res, "tol": inst.tol,
-                     "gpu_ms": ms, "total_cost": cost, "min_clearance_ratio": coll,
-                     "min_wall_clearance_ratio": wall}
+            chk = pl.check()
+        out[key] = {"converged": conv, "iterations": it, "residual": res, "tol": inst.tol,
+                    "check_every": every, "gpu_ms": ms, "total_cost": chk["total_cost"],
+                    "min_clearance_ratio": chk["min_pair_clearance"],
+                    "min_wall_clearance_ratio": chk["min_wall_clearance"],
+                    "max_endpoint_error": chk["max_endpoint_error"],
+                    "feasible": chk["min_pair_clearance"] >= 1 - 1e-4
+                    and chk["min_wall_clearance"] >= 1 - 1e-4 and chk["max_endpoint_error"] <= 1e-6,
+                    "factor_updates_per_s": sum(factor_counts(inst).values()) * it / (ms / 1e3)}
+        if kw:
+            out[key]["rho"] = kw
     return out
 
 
@@ -264,16 +348,19 @@ def modes(pk):
     the energy problem (Section 4), a maximum-velocity limit, and recovery of
     a collision-free plan from an energy solve stopped early."""
     out = {}
+    caps = {"circle4_eta4": (20000, 10), "circle100_eta8": (2000000, 5000)}
     for name in ("circle4_eta4", "circle100_eta8"):
         inst = workloads.by_name(name)
+        cap, every = caps[name]
         rec = {}
         for label, kw in (("twa", {}), ("admm", {"flags": pk.PLAN_ADMM}),
                           ("feasibility", {"energy": False})):
-            with pk.Planner.from_instance(inst, check_every=10, **kw) as pl:
+            kw = dict(kw, max_iter=cap, check_every=every if label != "feasibility" else 10)
+            with pk.Planner.from_instance(inst, **kw) as pl:
                 conv, it, res, ms = _solve_timed(pl)
                 cost, coll, _ = _plan_quality(pk, inst, pl)
-            rec[label] = {"converged": conv, "iterations": it, "gpu_ms": ms, "total_cost": cost,
-                          "min_clearance_ratio": coll}
+            rec[label] = {"converged": conv, "iterations": it, "check_every": kw["check_every"],
+                          "gpu_ms": ms, "total_cost": cost, "min_clearance_ratio": coll}
         if rec["twa"]["converged"] and rec["admm"]["converged"]:
             rec["admm_over_twa_iterations"] = rec["admm"]["iterations"] / rec["twa"]["iterations"]
         out[name] = rec
@@ -330,16 +417,18 @@ def local_planner(pk, p=32, epochs=150, step=0.1, advance=0.5):
             "epoch_iterations": {"median": q(its, 50), "p90": q(its, 90), "max": max(its)}}
 
 
-def batching(pk, n=512, max_iter=2000, check_every=50):
+def batching(pk, n=512, tol_rel=1e-4, max_iter=20000, check_every=100):
     """Row f1: n uneven instances (p ~ U{8..256}, eta in {4, 8, 16}, circle
     swap or random square 50/50) solved as one batch (one launch per pass,
     CUDA graphs, autotuned launch shapes) against looping the plain solver
-    over the same instances, both to the same tolerance / iteration cap and
-    the same residual checks (equal accuracy: each member stops at the same
-    iteration either way)."""
+    over the same instances.  Equal accuracy: every member stops, in both
+    arms, at the first residual check below tol_rel x its layout scale (or
+    at max_iter), so both arms run each member for the same iterations."""
     import torch
     insts = workloads.batch_instances(n)
     for m in insts:
+        L = max(1.0, float(np.abs(m.start).max()), float(np.abs(m.goal).max()))
+        m.tol = tol_rel * L
         m.max_iter = max_iter
     factors = [sum(factor_counts(m).values()) for m in insts]
     # the autotuner's timing iterations are real iterations, so it tunes on a
@@ -359,7 +448,7 @@ def batching(pk, n=512, max_iter=2000, check_every=50):
         t_batch = time.perf_counter() - t0
     # the same instances, one plain planner at a time
     t_loop = 0.0
-    its_loop = []
+    its_loop, conv_loop = [], 0
     for m in insts:
         with pk.Planner.from_instance(m, check_every=check_every) as pl:
             torch.cuda.synchronize()
@@ -368,10 +457,13 @@ def batching(pk, n=512, max_iter=2000, check_every=50):
             torch.cuda.synchronize()
             t_loop += time.perf_counter() - t0
             its_loop.append(it)
+            conv_loop += int(conv)
     upd = float(sum(f * i for f, i in zip(factors, its)))
     return {"workload": f"batch{n}: p ~ U{{8..256}}, eta in {{4,8,16}}, circle/square 50/50",
-            "members": n, "max_iter": max_iter, "check_every": check_every,
-            "converged": nconv, "iterations_total": int(sum(its)),
+            "members": n, "tol": f"{tol_rel:g} x layout scale", "max_iter": max_iter,
+            "check_every": check_every, "converged": nconv, "converged_loop": conv_loop,
+            "iterations_total": int(sum(its)),
+            "iterations_median": float(np.median(its)),
             "same_iterations_as_loop": its == its_loop,
             "batch_s": t_batch, "loop_s": t_loop, "speedup_vs_loop": t_loop / t_batch,
             "batch_factor_updates_per_s": upd / t_batch, "loop_factor_updates_per_s": upd / t_loop,
@@ -520,22 +612,26 @@ def main():
             return {"bound": "hbm", "kernel": "test_kernel<dense> (with the kinetic and wall blocks)",
                     "achieved": ach,
                     "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic,
-                    "peak_kind": peak_kind,
+                    "peak_kind": f"{peak_kind} (copy bandwidth)",
                     "note": f"algorithmic bytes {b:.4g} per launch (64 B u record read+written "
                             f"and 2 bits per collision factor) / live kernel time "
                             f"{ktimes['test'] * 1e3:.1f} us"}
-        flops = 30.0 * c["coll"]
+        # gated state: the bounding-circle filter leaves no per-factor bytes or
+        # flops to speak of; the kernel is bound by warp-instruction issue
         t = ktimes["test"] / 1e3
-        ach = flops / t / 1e12
-        pk_t = fp32_peak_tflops(sm_max)
-        traffic = TRAFFIC_SQUARE1024["gated"] if inst.name == "square1024_eta16" else None
-        return {"bound": "alu", "kernel": "test_rows_kernel (gated; with the kinetic and wall blocks)",
-                "achieved": ach, "peak": pk_t,
-                "unit": "TFLOP/s", "frac": ach / pk_t, "traffic": traffic,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "note": f"algorithmic 30 FP32 flops per collision factor (the exact distance "
-                        f"test) / live kernel time {ktimes['test'] * 1e3:.1f} us; the early-out "
-                        f"skips most of them, the kernel is bound by instruction issue"}
+        winst = WARP_INST_SQUARE1024["gated"] if inst.name == "square1024_eta16" else None
+        pk_i = issue_peak_g(sm_max)
+        ach = winst / t / 1e9 if winst else None
+        own = TRAFFIC_SQUARE1024["gated"] if inst.name == "square1024_eta16" else None
+        return {"bound": "issue", "kernel": "test_rows_kernel (gated; with the kinetic and wall blocks)",
+                "achieved": ach, "peak": pk_i, "unit": "G warp-instructions/s",
+                "frac": ach / pk_i if ach else None, "traffic": own,
+                "peak_kind": f"derived: {sm_count()} SMs x 4 schedulers x 1 warp instruction/cycle "
+                             f"x {sm_max:.0f} MHz",
+                "note": f"{winst:.4g} warp instructions per launch (ncu) / live kernel time "
+                        f"{ktimes['test'] * 1e3:.1f} us" if winst else "no instruction count for "
+                        "this workload",
+                "hbm_own_bytes_frac": (own / t / 1e9) / hbm_peak if own else None}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -568,6 +664,9 @@ def main():
                        "roofline": roofline_for(other, kt_o),
                        "iteration_hbm_frac": (b / (ms_o / 1e3) / 1e9) / hbm_peak
                        if other == "dense" else None}
+        # the other state mode's roofline, visible beside the headline's
+        line["roofline"]["companion"] = dict(line[other]["roofline"], mode=other,
+                                             iteration_hbm_frac=line[other]["iteration_hbm_frac"])
 
         # end to end through the C ABI with host buffers: new endpoints in,
         # one iteration, the trajectory back to pinned host memory

@@ -244,6 +244,17 @@ plan_status plan_batch_solve(plan_batch_t batch, int* iters_done, float* residua
                              int* n_converged);
 /* Break-points of one member, as plan_get_trajectory. */
 plan_status plan_batch_get_trajectory(plan_batch_t batch, int member, float* z, int on_device);
+/* One member's state in the paper's variables, as plan_import_state /
+ * plan_export_state (DEVICE pointers, the same layouts).  An imported state
+ * becomes the member's state at the batch's current iteration (members
+ * advance together) and unfreezes the member.  Both synchronise the batch's
+ * stream.  Errors: PLAN_EINVAL (null batch or pointers, member out of
+ * range), PLAN_ECUDA. */
+plan_status plan_batch_import_state(plan_batch_t batch, int member, const float* z,
+                                    const float* u_coll, const float* u_kin, const float* u_wall);
+plan_status plan_batch_export_state(plan_batch_t batch, int member, float* z, float* u_coll,
+                                    float* u_kin, float* u_wall, uint8_t* act_coll,
+                                    uint8_t* act_wall);
 /* Time the launch-shape candidates (rows per warp of the collision test
  * {4, 8, 16}, or 32: one warp per tile with lane = row agent, gated state
  * only; minimizer CTAs per SM {1, 2, 4} x the base grid; iterations per

@@ -49,7 +49,7 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_unroll", "plan_set_velocity_limits", "plan_export_velocity_state",
                     "plan_import_velocity_state", "plan_set_energy", "plan_export_back_weights",
                     "plan_import_back_weights", "plan_vo_epoch", "plan_get_endpoints",
-                    "plan_check"]
+                    "plan_check", "plan_batch_import_state", "plan_batch_export_state"]
 
 
 class PlanError(RuntimeError):
@@ -120,6 +120,8 @@ def load_library(path: str | None = None):
     lib.plan_batch_iterate.argtypes = [c_void_p, c_int]
     lib.plan_batch_solve.argtypes = [c_void_p, POINTER(c_int), fp, POINTER(c_int)]
     lib.plan_batch_get_trajectory.argtypes = [c_void_p, c_int, c_void_p, c_int]
+    lib.plan_batch_import_state.argtypes = [c_void_p, c_int] + [c_void_p] * 4
+    lib.plan_batch_export_state.argtypes = [c_void_p, c_int] + [c_void_p] * 6
     lib.plan_batch_autotune.argtypes = [c_void_p, c_int, POINTER(c_int)]
     lib.plan_batch_set_shape.argtypes = [c_void_p, c_int, c_int, c_int]
     lib.plan_batch_destroy.argtypes = [c_void_p]
@@ -315,13 +317,11 @@ class Planner:
     def velocity_obstacle(cls, x0, dest, radius, c_prime, step, walls=None, rho0=10.0, **kw):
         """A one-epoch velocity-obstacle planner (Section 5): current
         positions x0, destinations dest, per-agent cost C'_i; step bounds
-        |x_ref - x0|.  Advance it with ``vo_epoch``."""
+        |x_ref - x0|.  Advance it with ``vo_epoch``, which sets the reference
+        points x_ref on the device at the start of every epoch (until the
+        first epoch the goal node holds x0)."""
         x0 = np.asarray(x0, dtype=np.float64).reshape(-1, 2)
-        dest = np.asarray(dest, dtype=np.float64).reshape(-1, 2)
-        d = dest - x0
-        L = np.linalg.norm(d, axis=1, keepdims=True)
-        x_ref = x0 + np.where(L > step, step / np.maximum(L, 1e-300), 1.0) * d
-        pl = cls(x0, x_ref, radius, 2, cost_w=c_prime, walls=walls, rho0=rho0, vo=True, **kw)
+        pl = cls(x0, x0, radius, 2, cost_w=c_prime, walls=walls, rho0=rho0, vo=True, **kw)
         import torch
         pl._dest = torch.as_tensor(np.ascontiguousarray(dest, dtype=np.float32)).to(pl.device)
         pl._step = float(step)
@@ -544,6 +544,35 @@ class PlannerBatch:
     def set_shape(self, rows_per_warp, prox_ctas_per_sm, iterations_per_graph):
         _check(_lib.plan_batch_set_shape(self._h, int(rows_per_warp), int(prox_ctas_per_sm),
                                          int(iterations_per_graph)))
+
+    def import_state(self, member, z, u_coll, u_kin, u_wall):
+        """Replace one member's state (oracle layouts, host arrays) at the
+        batch's current iteration."""
+        import torch
+        inst = self.instances[member]
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device)
+        keep = [t(z), t(u_coll) if inst.p > 1 else None, t(u_kin), t(u_wall) if inst.n_walls else None]
+        ptr = lambda x: c_void_p(x.data_ptr()) if x is not None else None
+        _check(_lib.plan_batch_import_state(self._h, int(member), *(ptr(x) for x in keep)))
+
+    def export_state(self, member):
+        """One member's state in the oracle's layouts (as Planner.export_state)."""
+        import torch
+        inst = self.instances[member]
+        p, eta, nw = inst.p, inst.eta, inst.n_walls
+        P = p * (p - 1) // 2
+        dev = self.device
+        out = dict(z=torch.empty((p, eta + 1, 2), dtype=torch.float32, device=dev),
+                   u_coll=torch.empty((eta, P, 4, 2), dtype=torch.float32, device=dev),
+                   u_kin=torch.empty((eta, p, 2, 2), dtype=torch.float32, device=dev),
+                   u_wall=torch.empty((nw, eta, p, 2, 2), dtype=torch.float32, device=dev),
+                   act_coll=torch.empty((eta, P), dtype=torch.uint8, device=dev),
+                   act_wall=torch.empty((nw, eta, p), dtype=torch.uint8, device=dev))
+        ptr = lambda t: c_void_p(t.data_ptr()) if t.numel() else None
+        _check(_lib.plan_batch_export_state(self._h, int(member), ptr(out["z"]), ptr(out["u_coll"]),
+                                            ptr(out["u_kin"]), ptr(out["u_wall"]),
+                                            ptr(out["act_coll"]), ptr(out["act_wall"])))
+        return out
 
     def trajectory(self, member):
         import torch

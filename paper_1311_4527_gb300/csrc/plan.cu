@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(32 * ROWS_WARPS, 40 / ROWS_WARPS) test_rows_ke
     const int s = tr % P.eta;
     if (P.vo && s != 0) return;  // no collision factors on the second segment
     blk = s * P.ntp + tr / P.eta;
-    if (P.hcap && P.tile_stamp[blk] == *P.iter) return;  // taken by a heavy warp
+    if (P.hcap && P.stamp_cur[blk] == *P.iter) return;  // taken by a heavy warp
   }
   test_tile_rows(P, blk, col[warp], nws[warp]);
 }
@@ -155,7 +155,7 @@ __global__ void consensus_kernel(Dev P) {
 // Fixed-point scale of the consensus sums: the largest power of two with
 // 8 (L + 1) x (max incoming edges) x scale <= 2^62, L the largest coordinate
 // magnitude of the endpoints and walls.  One block.
-__global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
+__device__ __forceinline__ void fix_block(const Dev& P, const float2* start, const float2* goal) {
   __shared__ float red[256];
   float L = 0.f;
   for (int k = threadIdx.x; k < P.p; k += blockDim.x)
@@ -179,6 +179,9 @@ __global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
     f[0] = ldexpf(1.f, e);
     f[1] = (float)bound;
   }
+}
+__global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
+  fix_block(P, start, goal);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,14 +417,86 @@ __global__ void reset_kernel(Dev P, float2* z0, float2* z1, const float2* start,
   }
 }
 
-// New fixed ends: overwrite the s = 0 and s = eta nodes of both z buffers.
-__global__ void endpoints_kernel(int p, int eta, float2* z0, float2* z1, const float2* start,
-                                 const float2* goal) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p) return;
-  const size_t b = (size_t)i * (eta + 1);
-  z0[b] = start[i]; z1[b] = start[i];
-  z0[b + eta] = goal[i]; z1[b + eta] = goal[i];
+// New fixed positions (plan_set_endpoints): the fixed break-points of both z
+// buffers and the fixed-point scale, which depends on the layout's extent.
+// One block.  With a check key (the device check ran first), the new
+// positions come from the staging area and are applied only if the check
+// found no violation; the key is then handed to the host (key[1]) and reset
+// to ~0 for the next call.
+__global__ void endpoints_fix_kernel(Dev P, float2* start, float2* goal, const float2* staged,
+                                     unsigned long long* key) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = key ? (key[0] == ~0ull) : 1;
+  __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) { key[1] = key[0]; key[0] = ~0ull; }
+    return;
+  }
+  const size_t E1 = (size_t)P.eta + 1;
+  float2* z0 = const_cast<float2*>(P.z);
+  for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
+    if (staged) { start[i] = staged[i]; goal[i] = staged[P.p + i]; }
+    const float2 a = start[i], b = goal[i];
+    z0[i * E1] = a; P.z_next[i * E1] = a;
+    z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
+  }
+  __syncthreads();
+  fix_block(P, start, goal);
+  if (key && threadIdx.x == 0) { key[1] = ~0ull; key[0] = ~0ull; }
+}
+
+// Feasibility of new fixed positions on the device (plan_set_endpoints), with
+// the strict test of the host check in FP64: two disks closer than
+// r_i + r_j, or a disk closer than r_i to a wall segment.  The first
+// violation in the order (start pairs, goal pairs, start-wall, goal-wall;
+// then i; then j or the wall) is kept as one 64-bit key (kind << 60 | i << 30
+// | j), ~0 when there is none.  Blocks below 'pair_blocks' take one 32 x 32
+// agent tile pair of the starts (and then of the goals); the rest the
+// agent-wall tests.
+__device__ __forceinline__ unsigned long long endpoint_key(unsigned kind, unsigned i, unsigned j) {
+  return ((unsigned long long)kind << 60) | ((unsigned long long)i << 30) | (unsigned long long)j;
+}
+
+__global__ void endpoint_check_kernel(int p, int ntp, const int2* tiles, const float2* st,
+                                      const float2* gl, const float* radius, int nw,
+                                      const float4* walls, int goals, int pair_blocks,
+                                      unsigned long long* key) {
+  unsigned long long best = ~0ull;
+  if ((int)blockIdx.x < pair_blocks) {
+    const int which = (int)blockIdx.x / ntp, tp = (int)blockIdx.x - which * ntp;
+    const int2 IJ = tiles[tp];
+    const float2* X = which ? gl : st;
+    for (int q = threadIdx.x; q < TILE * TILE; q += blockDim.x) {
+      const int i = IJ.x * TILE + (q >> 5), j = IJ.y * TILE + (q & 31);
+      if (i >= j || j >= p) continue;
+      // FP32 screen: pairs farther apart than (1 + 1e-4)(r_i + r_j) cannot
+      // fail the FP64 test (FP32 rounding here is below 1e-6 relative)
+      const float fx = X[j].x - X[i].x, fy = X[j].y - X[i].y, fR = radius[i] + radius[j];
+      if (fx * fx + fy * fy > 1.0002f * fR * fR) continue;
+      const double dx = (double)X[j].x - (double)X[i].x, dy = (double)X[j].y - (double)X[i].y;
+      const double R = (double)radius[i] + (double)radius[j];
+      if (dx * dx + dy * dy < R * R) best = min(best, endpoint_key(which, i, j));
+    }
+  } else {
+    const long long n = (long long)p * nw * (goals ? 2 : 1);
+    const long long stride = (long long)(gridDim.x - pair_blocks) * blockDim.x;
+    for (long long t = (long long)(blockIdx.x - pair_blocks) * blockDim.x + threadIdx.x; t < n;
+         t += stride) {
+      const int i = (int)(t % p);
+      const long long rw = t / p;
+      const int w = (int)(rw % nw), which = (int)(rw / nw);
+      const float2 x = which ? gl[i] : st[i];
+      const float4 W = walls[w];
+      const double ax = W.x, ay = W.y, dx = (double)W.z - W.x, dy = (double)W.w - W.y;
+      const double dd = dx * dx + dy * dy;
+      const double px = (double)x.x - ax, py = (double)x.y - ay;
+      const double t01 = dd > 0.0 ? fmin(1.0, fmax(0.0, (px * dx + py * dy) / dd)) : 0.0;
+      const double ex = t01 * dx - px, ey = t01 * dy - py;
+      const double r = radius[i];
+      if (ex * ex + ey * ey < r * r) best = min(best, endpoint_key(2 + which, i, w));
+    }
+  }
+  block_min_u64(best, key);
 }
 
 __device__ __forceinline__ size_t pair_index(int p, int i, int j) {
@@ -739,11 +814,15 @@ plan_status fail(plan_status s, const char* fmt, ...) {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// plan_set_endpoints checks new endpoints on the device up to this many
+// agents (an all-pairs test), and with the host grid above it.
+constexpr size_t kDeviceEndpointCheck = 8192;
+
 struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
   size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, sched,
       stamps, heavy, accx, accy, accc, fix,
-      res, status, count, ccost, chk;
+      res, status, count, ccost, chk, estage, ekey;
   size_t total;
 };
 
@@ -792,7 +871,7 @@ Layout layout_for(const plan_config* c) {
   L.wwork = take(nw * eta * p * 4);
   L.wcount = take(4 * 4);  // collision and wall worklist counters, by iteration parity
   L.sched = take(4 * 4);   // iteration number, heavy-tile counts by parity
-  L.stamps = take(eta * ntp * 4);
+  L.stamps = take(2 * eta * ntp * 4);
   L.heavy = take(2 * heavy_cap(eta * ntp) * 4);
   L.accx = take(p * (eta + 1) * 8);
   L.accy = take(p * (eta + 1) * 8);
@@ -803,6 +882,8 @@ Layout layout_for(const plan_config* c) {
   L.count = take(16);
   L.ccost = take(p * eta * 8);  // FP64 kinetic coefficients for plan_check
   L.chk = take(4 * 8);          // plan_check results
+  L.estage = take(p * 16);      // plan_set_endpoints: new start and goal, checked on the device
+  L.ekey = take(16);            // ... the first violation found, and its copy for the host
   L.total = o;
   return L;
 }
@@ -813,23 +894,33 @@ bool finite_all(const float* a, size_t n) {
   return true;
 }
 
-double seg_point_dist(double px, double py, double ax, double ay, double bx, double by) {
-  double dx = bx - ax, dy = by - ay, dd = dx * dx + dy * dy;
-  double t = dd > 0 ? ((px - ax) * dx + (py - ay) * dy) / dd : 0.0;
-  t = std::min(1.0, std::max(0.0, t));
-  double cx = ax + t * dx - px, cy = ay + t * dy - py;
-  return std::sqrt(cx * cx + cy * cy);
-}
 
 // Host-side input check: fixed configurations must be feasible (two disks
 // closer than r_i + r_j, or a disk closer than r_i to a wall, make the
-// fixed-end minimizers infeasible).  Pairs are found with a uniform grid of
-// cell size max(r_i + r_j), so the check is linear in p.
+// fixed-end minimizers infeasible).  Pairs are found on a uniform grid of
+// cells at least max(r_i + r_j) wide: the agents are counting-sorted by cell
+// into contiguous arrays, and each agent is compared with the later agents
+// of its own cell and with those of four neighbouring cells (every
+// neighbouring pair of cells once), so the check is linear in p.  The tests
+// only accumulate a flag; the offending pair is looked up again only for the
+// error message.  The grid's arrays are kept between calls (EndpointGrid).
+struct EndpointGrid {
+  std::vector<int> cell, start, fill, order;
+  std::vector<double> xs, ys, rs;
+};
+
 plan_status check_endpoints(int p, const float* start, const float* goal, const float* radius,
-                            int nw, const float* walls, bool goals_fixed = true) {
+                            int nw, const float* walls, bool goals_fixed = true,
+                            EndpointGrid* grid = nullptr) {
+  EndpointGrid local;
+  EndpointGrid& g = grid ? *grid : local;
   float rmax = 0.f;
   for (int i = 0; i < p; ++i) rmax = std::max(rmax, radius[i]);
-  const double cell = std::max(2.0 * rmax, 1e-6);
+  g.cell.resize(p);
+  g.order.resize(p);
+  g.xs.resize(p);
+  g.ys.resize(p);
+  g.rs.resize(p);
   // a velocity-obstacle epoch's goal node holds reference points, which the
   // factors never test against each other
   for (int which = 0; which < (goals_fixed ? 2 : 1); ++which) {
@@ -839,37 +930,80 @@ plan_status check_endpoints(int p, const float* start, const float* goal, const 
       x0 = std::min(x0, (double)X[2 * i]); x1 = std::max(x1, (double)X[2 * i]);
       y0 = std::min(y0, (double)X[2 * i + 1]); y1 = std::max(y1, (double)X[2 * i + 1]);
     }
-    // cells at least `cell` wide, so overlapping disks sit in neighbouring cells
-    const long nx = std::max<long>(1, std::min<long>(4096, (long)((x1 - x0) / cell)));
-    const long ny = std::max<long>(1, std::min<long>(4096, (long)((y1 - y0) / cell)));
-    const double sx = (x1 - x0) / nx + 1e-300, sy = (y1 - y0) / ny + 1e-300;
-    std::vector<int> head(nx * ny, -1), next(p, -1);
-    std::vector<long> cx(p), cy(p);
+    // cells at least 2 rmax wide (plus a relative 1e-9, so that rounding in
+    // the cell index cannot separate two overlapping disks by two cells), no
+    // more than about 4 per agent
+    double cw = std::max(2.0 * (double)rmax * (1.0 + 1e-9), 1e-6);
+    const double area = std::max(x1 - x0, cw) * std::max(y1 - y0, cw);
+    cw = std::max(cw, std::sqrt(area / (4.0 * p + 16.0)));
+    const int nx = (int)std::max(1.0, std::floor((x1 - x0) / cw));
+    const int ny = (int)std::max(1.0, std::floor((y1 - y0) / cw));
+    const double isx = nx / std::max(x1 - x0, 1e-300), isy = ny / std::max(y1 - y0, 1e-300);
+    g.start.assign((size_t)nx * ny + 1, 0);
     for (int i = 0; i < p; ++i) {
-      cx[i] = std::min(nx - 1, (long)((X[2 * i] - x0) / sx));
-      cy[i] = std::min(ny - 1, (long)((X[2 * i + 1] - y0) / sy));
-      const long c = cy[i] * nx + cx[i];
-      next[i] = head[c];
-      head[c] = i;
+      const int cx = std::min(nx - 1, (int)((X[2 * i] - x0) * isx));
+      const int cy = std::min(ny - 1, (int)((X[2 * i + 1] - y0) * isy));
+      g.cell[i] = cy * nx + cx;
+      g.start[g.cell[i] + 1] += 1;
     }
-    for (int i = 0; i < p; ++i) {
-      for (long dy = -1; dy <= 1; ++dy) {
-        for (long dx = -1; dx <= 1; ++dx) {
-          const long gx = cx[i] + dx, gy = cy[i] + dy;
-          if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) continue;
-          for (int j = head[gy * nx + gx]; j >= 0; j = next[j]) {
-            if (j <= i) continue;
-            const double ddx = (double)X[2 * j] - X[2 * i], ddy = (double)X[2 * j + 1] - X[2 * i + 1];
-            const double R = (double)radius[i] + radius[j];
-            if (ddx * ddx + ddy * ddy < R * R)
-              return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %d and %d overlap",
-                          which ? "goal" : "start", std::min(i, j), std::max(i, j));
+    for (size_t c = 0; c < (size_t)nx * ny; ++c) g.start[c + 1] += g.start[c];
+    g.fill.assign(g.start.begin() + 1, g.start.end());  // per-cell ends, filled downwards
+    for (int i = p - 1; i >= 0; --i) {
+      const int u = --g.fill[g.cell[i]];
+      g.order[u] = i;
+      g.xs[u] = X[2 * i];
+      g.ys[u] = X[2 * i + 1];
+      g.rs[u] = radius[i];
+    }
+    // agent u (sorted) against the sorted range [v0, v1)
+    auto range_hits = [&](int u, int v0, int v1) {
+      bool hit = false;
+      for (int v = v0; v < v1; ++v) {
+        const double dx = g.xs[v] - g.xs[u], dy = g.ys[v] - g.ys[u], R = g.rs[u] + g.rs[v];
+        hit |= dx * dx + dy * dy < R * R;
+      }
+      return hit;
+    };
+    static const int nb[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+    for (int u = 0; u < p; ++u) {
+      const int c = g.cell[g.order[u]], cx = c % nx, cy = c / nx;
+      bool hit = range_hits(u, u + 1, g.start[c + 1]);
+      int culprit_cell = c;
+      for (int q = 0; q < 4 && !hit; ++q) {
+        const int gx = cx + nb[q][0], gy = cy + nb[q][1];
+        if (gx < 0 || gx >= nx || gy >= ny) continue;
+        const int d = gy * nx + gx;
+        hit = range_hits(u, g.start[d], g.start[d + 1]);
+        culprit_cell = d;
+      }
+      if (hit) {  // find the partner for the message
+        const int v0 = culprit_cell == c ? u + 1 : g.start[culprit_cell];
+        for (int v = v0; v < g.start[culprit_cell + 1]; ++v) {
+          if (range_hits(u, v, v + 1)) {
+            const int i = g.order[u], j = g.order[v];
+            return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %d and %d overlap",
+                        which ? "goal" : "start", std::min(i, j), std::max(i, j));
           }
         }
       }
-      for (int w = 0; w < nw; ++w) {
-        const float* W = walls + 4 * w;
-        if (seg_point_dist(X[2 * i], X[2 * i + 1], W[0], W[1], W[2], W[3]) < radius[i])
+    }
+    for (int w = 0; w < nw; ++w) {
+      const float* W = walls + 4 * w;
+      const double ax = W[0], ay = W[1], dx = (double)W[2] - W[0], dy = (double)W[3] - W[1];
+      const double dd = dx * dx + dy * dy, idd = dd > 0.0 ? 1.0 / dd : 0.0;
+      bool hit = false;
+      for (int i = 0; i < p; ++i) {
+        const double px = (double)X[2 * i] - ax, py = (double)X[2 * i + 1] - ay;
+        const double t = std::min(1.0, std::max(0.0, (px * dx + py * dy) * idd));
+        const double ex = t * dx - px, ey = t * dy - py;
+        hit |= ex * ex + ey * ey < (double)radius[i] * radius[i];
+      }
+      if (!hit) continue;
+      for (int i = 0; i < p; ++i) {
+        const double px = (double)X[2 * i] - ax, py = (double)X[2 * i + 1] - ay;
+        const double t = std::min(1.0, std::max(0.0, (px * dx + py * dy) * idd));
+        const double ex = t * dx - px, ey = t * dy - py;
+        if (ex * ex + ey * ey < (double)radius[i] * radius[i])
           return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %d is within its radius of wall %d",
                       which ? "goal" : "start", i, w);
       }
@@ -903,7 +1037,9 @@ struct plan_s {
   cudaGraphExec_t gexec8[4] = {}; // ... and runs of ITERS_PER_GRAPH iterations
   double ptime[4] = {0, 0, 0, 0};
   int pcount = 0;
-  unsigned* h_res;  // pinned host word for residual readback
+  unsigned* h_res;  // pinned host words: residual readback (0), endpoint check key (2..3)
+  float* h_stage = nullptr;  // pinned staging of new endpoints (plan_set_endpoints)
+  EndpointGrid grid;         // the host check's arrays, kept between calls
   std::vector<float> h_radius;
   std::vector<float> h_walls;
   std::vector<float> h_start, h_goal;
@@ -970,7 +1106,9 @@ struct plan_s {
       P.hcount_next = at<unsigned>(L.sched) + 1 + ((kk + 1) & 1);
       P.heavy_cur = at<uint32_t>(L.heavy) + (kk & 1) * cap;
       P.heavy_next = at<uint32_t>(L.heavy) + ((kk + 1) & 1) * cap;
-      P.tile_stamp = at<unsigned>(L.stamps);
+      const size_t ntiles = (size_t)eta * ntp;
+      P.stamp_cur = at<unsigned>(L.stamps) + (kk & 1) * ntiles;
+      P.stamp_next = at<unsigned>(L.stamps) + ((kk + 1) & 1) * ntiles;
     }
     P.accx = at<unsigned long long>(L.accx);
     P.accy = at<unsigned long long>(L.accy);
@@ -1214,7 +1352,8 @@ plan_status plan_reset(plan_t h) {
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
-  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.ekey), 0xff, 16, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, 2 * (size_t)h->eta * h->ntp * 4, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1306,7 +1445,10 @@ plan_status create_plan(const plan_config* cfg, const float* start, const float*
   }
   if (!member) {
     cudaError_t e = cudaMallocHost(&h->h_res, 16);
+    if (e == cudaSuccess && (size_t)cfg->p <= kDeviceEndpointCheck)
+      e = cudaMallocHost(&h->h_stage, (size_t)cfg->p * 16);
     if (e != cudaSuccess) {
+      if (h->h_res) cudaFreeHost(h->h_res);
       if (h->own_ws) cudaFree(h->ws);
       delete h;
       return fail(PLAN_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
@@ -1349,6 +1491,7 @@ void plan_destroy(plan_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_res) cudaFreeHost(h->h_res);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
   for (int q = 0; q < 6; ++q)
     if (h->pev[q]) cudaEventDestroy(h->pev[q]);
   for (int q = 0; q < 4; ++q)
@@ -1363,23 +1506,56 @@ void plan_destroy(plan_t h) {
 
 plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) {
   if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
-  if (!finite_all(start, 2 * (size_t)h->p) || !finite_all(goal, 2 * (size_t)h->p))
-    return fail(PLAN_EINVAL, "non-finite input");
-  plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(),
-                                   !h->vo);
-  if (st != PLAN_OK) return st;
+  const size_t p = h->p;
+  if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
+  float2* d_start = h->at<float2>(h->L.start);
+  float2* d_goal = h->at<float2>(h->L.goal);
+  if (!h->h_stage || p > kDeviceEndpointCheck) {
+    // the host grid check, then the copies
+    plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(),
+                                     !h->vo, &h->grid);
+    if (st != PLAN_OK) return st;
+    CK(cudaMemcpyAsync(d_start, start, p * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_goal, goal, p * 8, cudaMemcpyHostToDevice, h->stream));
+    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, nullptr, nullptr);
+    CK(cudaGetLastError());
+    // the caller's host buffers may be reused once this returns
+    CK(cudaStreamSynchronize(h->stream));
+  } else {
+    // through a pinned staging buffer, checked on the device; the new
+    // endpoints are applied on the device only if the check passed, so the
+    // whole update is enqueued before the one readback
+    std::memcpy(h->h_stage, start, p * 8);
+    std::memcpy(h->h_stage + 2 * p, goal, p * 8);
+    float2* staged = h->at<float2>(h->L.estage);
+    unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
+    CK(cudaMemcpyAsync(staged, h->h_stage, p * 16, cudaMemcpyHostToDevice, h->stream));
+    const int goals = h->vo ? 0 : 1;
+    const int pair_blocks = (int)h->ntp * (1 + goals);
+    const long long nwall = (long long)p * h->nw * (1 + goals);
+    const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
+    endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->stream>>>(
+        h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
+        h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
+    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, staged, key);
+    CK(cudaGetLastError());
+    unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
+    CK(cudaMemcpyAsync(hk, key + 1, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const unsigned long long k = *hk;
+    if (k != ~0ull) {
+      const unsigned kind = (unsigned)(k >> 60), i = (unsigned)((k >> 30) & 0x3fffffffu),
+                     j = (unsigned)(k & 0x3fffffffu);
+      if (kind < 2)
+        return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %u and %u overlap",
+                    kind ? "goal" : "start", i, j);
+      return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %u is within its radius of wall %u",
+                  kind == 3 ? "goal" : "start", i, j);
+    }
+  }
   h->adj_valid = false;
-  h->h_start.assign(start, start + 2 * (size_t)h->p);
-  h->h_goal.assign(goal, goal + 2 * (size_t)h->p);
-  CK(cudaMemcpyAsync(h->at<void>(h->L.start), start, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->at<void>(h->L.goal), goal, (size_t)h->p * 8, cudaMemcpyHostToDevice, h->stream));
-  endpoints_kernel<<<(h->p + 255) / 256, 256, 0, h->stream>>>(
-      h->p, h->eta, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1), h->at<float2>(h->L.start),
-      h->at<float2>(h->L.goal));
-  fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
-  CK(cudaGetLastError());
-  // the caller's host buffers may be reused once this returns
-  CK(cudaStreamSynchronize(h->stream));
+  h->h_start.assign(start, start + 2 * p);
+  h->h_goal.assign(goal, goal + 2 * p);
   return PLAN_OK;
 }
 
@@ -1467,7 +1643,7 @@ plan_status plan_import_state(plan_t h, const float* z, const float* u_coll, con
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
-  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
+  CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, 2 * (size_t)h->eta * h->ntp * 4, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
@@ -1710,7 +1886,7 @@ plan_status snapshot(plan_t h, const AdjLayout& A, int idx, bool save) {
     // the pass-1 heavy-tile lists belong to the iteration order that ran, not
     // to the restored state: start over with none (results do not depend on it)
     CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
-    CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, (size_t)h->eta * h->ntp * 4, h->stream));
+    CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, 2 * (size_t)h->eta * h->ntp * 4, h->stream));
   }
   return PLAN_OK;
 }
@@ -2550,6 +2726,29 @@ plan_status plan_batch_create(int n, const plan_config* cfgs, const float* const
   if (st == PLAN_OK) { B->prox_grid = std::max(1, B->m[0]->prox_grid / 4); st = batch_tables(B); }
   if (st != PLAN_OK) { plan_batch_destroy(B); return st; }
   *out = B;
+  return PLAN_OK;
+}
+
+plan_status plan_batch_import_state(plan_batch_t B, int member, const float* z, const float* u_coll,
+                                    const float* u_kin, const float* u_wall) {
+  if (!B || member < 0 || member >= B->n) return fail(PLAN_EINVAL, "null batch or member out of range");
+  plan_t h = B->m[member];
+  plan_status st = plan_import_state(h, z, u_coll, u_kin, u_wall, B->k);
+  if (st != PLAN_OK) return st;
+  // the member follows the batch's iteration: its z buffer is the parity's
+  h->k = B->k;
+  h->cur = (h->eta > 1) ? (B->k & 1) : 0;
+  CK(cudaMemsetAsync(B->frozen + member, 0, 1, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  return PLAN_OK;
+}
+
+plan_status plan_batch_export_state(plan_batch_t B, int member, float* z, float* u_coll, float* u_kin,
+                                    float* u_wall, uint8_t* act_coll, uint8_t* act_wall) {
+  if (!B || member < 0 || member >= B->n) return fail(PLAN_EINVAL, "null batch or member out of range");
+  plan_status st = plan_export_state(B->m[member], z, u_coll, u_kin, u_wall, act_coll, act_wall, nullptr);
+  if (st != PLAN_OK) return st;
+  CK(cudaStreamSynchronize(B->stream));
   return PLAN_OK;
 }
 

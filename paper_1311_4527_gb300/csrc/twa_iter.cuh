@@ -1,6 +1,6 @@
 // twa_iter.cuh -- the per-block work of one TWA iteration (Appendix B steps
 // 1-7 over the factor graph of Section 3.3 of Bento et al., NIPS 2013), shared
-// by the single-planner kernels (plan.cu) and the batched ones (batch.cu).
+// by the single-planner kernels and the batched ones (both in plan.cu).
 //
 // Pass 1, test_block: one block per (segment s, agent tiles I <= J) of 32 x 32
 //   collision factors: finish the deferred dual update of the pairs that were
@@ -81,7 +81,11 @@ struct Dev {
   unsigned* hcount_cur;        // their number (cleared by the consensus pass for reuse)
   uint32_t* heavy_next;        // the next iteration's heavy tiles (built by this pass 1)
   unsigned* hcount_next;
-  unsigned* tile_stamp;        // [eta ntp] iteration number for which the tile is listed heavy
+  // [eta ntp] iteration number for which the tile is listed heavy, one array
+  // per iteration parity: this iteration's list is only read (ordinary warps
+  // skip the tiles listed in it) while the next one's is written
+  const unsigned* stamp_cur;
+  unsigned* stamp_next;
   unsigned* iter;              // iteration number (advanced by the consensus pass)
   uint32_t* wwork;       // active wall factors ((w eta + s) p + i) of this iteration whose
                          // minimizer runs in pass 2 (wall_prox_item_warp)
@@ -112,12 +116,15 @@ __device__ __forceinline__ float2 finish_u(bool bprev, bool pinned, bool keep, f
   return keep ? u_prev : mk(0.f, 0.f);
 }
 
-// Step 5's sums in 64-bit fixed point: each FP32 m converts exactly (the scale
-// is a power of two chosen from the layout's extent), integer addition does not
-// depend on the order of the atomics, so z is deterministic: the exact sum
-// rounded once to FP32 and divided by the count in FP32 (within 1.5 units in
-// the last place of the exact mean).  A non-finite or out-of-range m
-// sets status bit 1, which the consensus pass turns into a NaN residual.
+// Step 5's sums in 64-bit fixed point: each FP32 m is scaled by a power of
+// two 2^e chosen from the layout's extent and rounded to an integer (an
+// absolute error of at most 2^-(e+1), about 1e-13 at p = 1024 on the 40 x 40
+// square, far below the FP32 ulp of m itself), then the integers are summed
+// exactly; integer addition does not depend on the order of the atomics, so z
+// is deterministic: the integer sum rounded once to FP32 and divided by the
+// count in FP32 (within 1.5 units in the last place of the mean of the
+// quantised messages).  A non-finite or out-of-range m sets status bit 1,
+// which the consensus pass turns into a NaN residual.
 __device__ __forceinline__ void contribute(const Dev& P, float scale, float bound, int i, int s,
                                            float2 m) {
   if (!(fabsf(m.x) <= bound && fabsf(m.y) <= bound)) {
@@ -647,7 +654,7 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
       const unsigned k = atomicAdd(P.hcount_next, 1u);
       if (k < (unsigned)P.hcap) {
         P.heavy_next[k] = (uint32_t)blk;
-        P.tile_stamp[blk] = *P.iter + 1u;
+        P.stamp_next[blk] = *P.iter + 1u;
       }
     }
   }

@@ -444,16 +444,24 @@ TWA_DEV float capsule_E(float2 a, float2 b, float wl, float wh, float2 c0, float
 // kink energies at c = +-1; with both targets on one side of the wall's line
 // (beta_a, beta_b of one sign) G is monotone in c, so nothing in that
 // half-plane is below the better kink and the circle's candidates can be
-// skipped.  False for a zero-length wall.
+// skipped.  False for a zero-length wall.  The signs are decided in FP32, so
+// each coordinate must clear a margin of 1e-6 |e| |x - c_ci| (a few units in
+// the last place of the products): a target on the wall's line, on the
+// perpendicular through the end or at the end centre keeps the circle's
+// candidates (which are then computed exactly) instead of trusting a sign
+// that rounding may have flipped.
 TWA_DEV bool capsule_end_dominated(float2 a, float2 b, float2 c0, float2 c1, int ci) {
   const float2 e = c1 - c0;
-  if (e.x == 0.f && e.y == 0.f) return false;
+  const float ee = dot(e, e);
+  if (!(ee > 0.f)) return false;
   const float2 cc = ci ? c1 : c0;
   const float2 out = ci ? e : -e;
   const float2 nu = perp(e);
-  const float ga = dot(a - cc, out), gb = dot(b - cc, out);
-  const float ba = dot(a - cc, nu), bb = dot(b - cc, nu);
-  return ga <= 0.f && gb <= 0.f && ((ba >= 0.f && bb >= 0.f) || (ba <= 0.f && bb <= 0.f));
+  const float2 da = a - cc, db = b - cc;
+  const float ta = 1e-6f * sqrtf(ee * dot(da, da)), tb = 1e-6f * sqrtf(ee * dot(db, db));
+  const float ga = dot(da, out), gb = dot(db, out);
+  const float ba = dot(da, nu), bb = dot(db, nu);
+  return ga < -ta && gb < -tb && ((ba > ta && bb > tb) || (ba < -ta && bb < -tb));
 }
 
 // Kinds of winning capsule direction (Best::tag): 0 the (1, 0) fallback,

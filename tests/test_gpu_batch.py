@@ -1,12 +1,16 @@
-"""Batches of uneven problems: every member of a batch follows exactly the
-iterates of the same problem solved alone (bit for bit: the per-factor
-arithmetic is the same and the consensus sums are exact), whatever launch
-shape the autotuner picks, and a batch solve stops each member where its own
-solve stops."""
+"""Batches of uneven problems: members imported at an oracle iterate match the
+FP64 oracle's next iterate entry by entry; every member of a batch follows
+exactly the iterates of the same problem solved alone (bit for bit: the
+per-factor arithmetic is the same and the consensus sums are exact), whatever
+launch shape the autotuner picks; and a batch solve stops each member where
+its own solve stops."""
 import numpy as np
 import pytest
 
 import workloads
+from oracle import twa
+
+import _parity as par
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +80,31 @@ def test_every_test_pass_shape_gives_the_same_iterates(rows):
         zb = [B.trajectory(b).cpu().numpy() for b in range(len(insts))]
     for b, inst in enumerate(insts):
         assert np.array_equal(zb[b], _alone(inst, 24)), b
+
+
+def test_batch_members_match_the_oracle_from_an_imported_iterate():
+    """A mixed batch (walls, eta = 1, p = 1, the p = 100 circle and two
+    uneven members): the walled member and the p = 100 member get the
+    oracle's iterate 6, the batch takes one iteration (every member moves),
+    and both are compared with the oracle's next iterate entry by entry.
+    Back weights are those of the energy problem (rho0 inside, infinite at
+    the fixed ends; batches run no other), so the oracle's are used."""
+    import paper_1311_4527_gb300 as pk
+    insts = [workloads.small_square(40, 5, seed=12), workloads.circle_swap(6, 1, 0.1, 0.01, 13),
+             workloads.circle_swap(1, 4, 0.1, 0.0, 14), workloads.circle100()]
+    insts += [m for m in workloads.batch_instances(20, seed=31) if m.p <= 64][:2]
+    probs = [twa.Problem.from_instance(m) for m in insts]
+    chosen = (0, 3)
+    states = {b: par.oracle_state(probs[b], 6) for b in chosen}
+    with pk.PlannerBatch(insts) as B:
+        B.iterate(3)
+        for b in chosen:
+            st = states[b]
+            B.import_state(b, st.z, st.u_coll, st.u_kin, st.u_wall)
+        B.iterate(1)
+        got = {b: {k: v.cpu().numpy() for k, v in B.export_state(b).items()} for b in chosen}
+    for b in chosen:
+        new, info = twa.iterate(probs[b], states[b], record_branches=True)
+        gpu = dict(got[b], wback=new.wback)
+        stats = par.compare(probs[b], new, info, gpu)
+        assert stats["coll_active"] > 0 and stats["coll_compared_active"] > 0, (b, stats)

@@ -123,6 +123,34 @@ def test_full_size_square1024_one_iteration():
         assert s["coll_excluded"] < 0.01 * s["coll_active"], s
 
 
+def test_full_size_square1024_from_a_crowded_iterate():
+    """The state the benchmark times: p = 1024, eta = 16 with walls from the
+    oracle's iterate 20 (about 19,000 active pairs, previously active pairs
+    dealt over each warp).  One GPU step from that iterate, then a second
+    from the GPU's own state, in which the tiles that needed many exact
+    tests in the first step are dispatched first, each against the oracle's
+    next iterate (the second step leaves out the break-points where the two
+    states it starts from differ, and everything that reads them)."""
+    prob = _prob(workloads.square1024())
+    st = par.oracle_state(prob, 20)
+    new1, info1 = twa.iterate(prob, st, record_branches=True)
+    new2, info2 = twa.iterate(prob, new1, record_branches=True)
+    with par.make_planner(prob) as pl:
+        g1 = par.gpu_step(prob, st, planner=pl)
+        s1 = par.compare(prob, new1, info1, g1)
+        pl.iterate(1)
+        g2 = par.gpu_export(prob, pl)
+        s2 = par.compare(prob, new2, info2, g2, prior_bad=par.differing_nodes(prob, new1, g1))
+    for s in (s1, s2):
+        assert s["coll_active"] > 10000, s
+    assert s1["coll_excluded"] < 0.01 * s1["coll_active"], s1
+    assert s1["coll_compared_active"] > 0.5 * s1["coll_active"], s1
+    # at this density the first step's near-ties reach many neighbours in the
+    # second (every factor reading a break-point that differs is left out, and
+    # every u reading a break-point so reached), so fewer pairs remain
+    assert s2["coll_compared_active"] > 500, s2
+
+
 def test_standard_admm_mode_parity():
     prob = _prob(workloads.circle4(), admm=True)
     _run(prob, [0, 4, 40])

@@ -178,3 +178,69 @@ def test_admm_and_twa_converge_on_circle4_like_the_oracle():
         assert abs(it - o_it) <= 0.05 * o_it + 5
         its[admm] = it
     assert its[False] < its[True]
+
+
+def _first_violation(start, goal, radius, walls):
+    """Brute force, in the device check's order: start pairs, goal pairs,
+    start-wall, goal-wall; then the lower agent, then the partner."""
+    p = start.shape[0]
+    X32 = [np.asarray(start, np.float32).astype(np.float64), np.asarray(goal, np.float32).astype(np.float64)]
+    r = np.asarray(radius, np.float32).astype(np.float64)
+    for which in (0, 1):
+        X = X32[which]
+        for i in range(p):
+            d2 = np.sum((X[i + 1:] - X[i]) ** 2, axis=1)
+            hit = np.nonzero(d2 < (r[i] + r[i + 1:]) ** 2)[0]
+            if hit.size:
+                return f"{'goal' if which else 'start'} positions of agents {i} and {i + 1 + hit[0]} overlap"
+    W = np.asarray(walls, np.float32).astype(np.float64)
+    for which in (0, 1):
+        X = X32[which]
+        for i in range(p):
+            for w in range(W.shape[0]):
+                a, b = W[w, :2], W[w, 2:]
+                d = b - a
+                t = np.clip(np.dot(X[i] - a, d) / np.dot(d, d), 0.0, 1.0)
+                if np.sum((a + t * d - X[i]) ** 2) < r[i] ** 2:
+                    return f"{'goal' if which else 'start'} of agent {i} is within its radius of wall {w}"
+    return None
+
+
+def test_set_endpoints_checks_new_positions_on_the_device():
+    """plan_set_endpoints refuses overlapping starts or goals and positions
+    within a wall's reach (checked on the device), names the first violation
+    like a brute-force enumeration, and leaves the plan unchanged; feasible
+    new endpoints are applied."""
+    import torch
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(72, 6, seed=11)
+    rng = np.random.default_rng(4)
+    with pk.Planner.from_instance(inst) as pl:
+        pl.iterate(5)
+        z0 = pl.trajectory().clone()
+        cases = []
+        for _ in range(4):
+            st, gl = inst.start.copy(), inst.goal.copy()
+            i, j = rng.choice(inst.p, size=2, replace=False)
+            ang = rng.uniform(0, 2 * np.pi)
+            X = st if rng.uniform() < 0.5 else gl
+            X[j] = X[i] + 0.9 * (inst.radius[i] + inst.radius[j]) * np.array([np.cos(ang), np.sin(ang)])
+            cases.append((st, gl))
+        st = inst.start.copy()
+        st[7] = [0.5 * inst.radius[7], 3.0]          # inside the x = 0 wall's reach
+        cases.append((st, inst.goal.copy()))
+        for st, gl in cases:
+            expect = _first_violation(st, gl, inst.radius, inst.walls)
+            assert expect is not None
+            with pytest.raises(pk.PlanError) as e:
+                pl.set_endpoints(st, gl)
+            assert e.value.status == "PLAN_EINFEASIBLE_INPUT"
+            assert expect in str(e.value), (expect, str(e.value))
+            assert torch.equal(pl.trajectory(), z0)
+        new_goal = inst.goal.copy()
+        new_goal[0] += 0.05
+        assert _first_violation(inst.start, new_goal, inst.radius, inst.walls) is None
+        pl.set_endpoints(inst.start, new_goal)
+        z = pl.trajectory().cpu().numpy()
+        assert np.array_equal(z[:, -1], new_goal.astype(np.float32))
+        assert np.array_equal(z[:, 0], inst.start.astype(np.float32))

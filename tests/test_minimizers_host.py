@@ -118,6 +118,50 @@ def test_capsule_minimizer_matches_the_oracle(H):
     assert n > 500
 
 
+def test_capsule_minimizer_on_the_wall_line_and_at_an_end_centre(H):
+    """Targets where the end-circle skip decides signs near zero: on the
+    wall's line beyond an end, on the perpendicular through an end, and at an
+    end centre (an exact energy tie between directions), against the
+    oracle's minimizer; the skip rule keeps the circle's candidates for the
+    targets beyond the end or at its centre."""
+    rng = np.random.default_rng(31)
+    n = 0
+    for k in range(600):
+        L = float(np.float32(rng.uniform(0.5, 40.0)))
+        ang = rng.uniform(0, 2 * np.pi)
+        e = np.array([np.cos(ang), np.sin(ang)])
+        c0 = _f32(rng.normal(size=2) * 3)
+        c1 = _f32(c0 + L * e)
+        r = float(np.float32(rng.uniform(0.1, 0.5)))
+        ci = k % 2
+        cc, out = (c1, e) if ci else (c0, -e)
+        kind = (k // 2) % 3
+        if kind == 0:        # on the line through the wall, a little beyond the end
+            a = _f32(cc + rng.uniform(0.0, r) * out)
+        elif kind == 1:      # on the perpendicular through the end
+            a = _f32(cc + rng.uniform(-r, r) * np.array([-e[1], e[0]]))
+        else:                # at the end centre
+            a = _f32(cc)
+        b = _f32(a + rng.normal(size=2) * 0.5)
+        wl, wh = (0.5, 0.5) if k % 3 else tuple(_f32(rng.uniform(0.2, 3.0, size=2)))
+        A, pa = _a(a)
+        B, pb = _a(b)
+        C0, p0 = _a(c0)
+        C1, p1 = _a(c1)
+        if kind != 1:  # beyond the end, or at its centre: that circle is never skipped
+            assert not H.h_capsule_end_dominated(pa, pb, p0, p1, ci), (a, b, ci, kind)
+        if prox.dist_segment_segment(a, b, c0, c1) >= r:
+            continue
+        vl, vh = _capsule(H, a, b, wl, wh, c0, c1, r)
+        ol, oh, _ = prox.region_prox(a, b, wl, wh, c0, c1, r)
+        scale = float(np.abs(np.concatenate([c0, c1, a, b])).max()) + 1.0
+        assert prox.dist_segment_segment(vl, vh, c0, c1) >= r * (1 - 1e-5) - 1e-6 * scale
+        e_g, e_o = _E(vl, vh, a, b, wl, wh), _E(ol, oh, a, b, wl, wh)
+        assert e_g <= e_o + _tol(e_o, scale), (a, b, wl, wh, c0, c1, r, e_g, e_o)
+        n += 1
+    assert n > 200
+
+
 def test_capsule_end_circle_skip_is_sound(H):
     """Where the FP32 wall minimizer skips an end circle's candidates, no
     direction of that circle's half-plane (where it gives the capsule's
