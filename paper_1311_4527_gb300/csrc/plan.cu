@@ -155,6 +155,17 @@ __global__ void consensus_kernel(Dev P) {
 // Fixed-point scale of the consensus sums: the largest power of two with
 // 8 (L + 1) x (max incoming edges) x scale <= 2^62, L the largest coordinate
 // magnitude of the endpoints and walls.  One block.
+// The scale from the largest coordinate magnitude L of endpoints and walls.
+__device__ __forceinline__ void set_fix(const Dev& P, float L) {
+  const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * (P.nw + P.nv);
+  const double bound = 8.0 * ((double)L + 1.0);
+  int e = (int)floor(log2(4.611686018427388e18 / (bound * edges)));
+  e = e < 8 ? 8 : (e > 60 ? 60 : e);
+  float* f = const_cast<float*>(P.fix);
+  f[0] = ldexpf(1.f, e);
+  f[1] = (float)bound;
+}
+
 __device__ __forceinline__ void fix_block(const Dev& P, const float2* start, const float2* goal) {
   __shared__ float red[256];
   float L = 0.f;
@@ -170,15 +181,7 @@ __device__ __forceinline__ void fix_block(const Dev& P, const float2* start, con
     if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * (P.nw + P.nv);
-    const double bound = 8.0 * ((double)red[0] + 1.0);
-    int e = (int)floor(log2(4.611686018427388e18 / (bound * edges)));
-    e = e < 8 ? 8 : (e > 60 ? 60 : e);
-    float* f = const_cast<float*>(P.fix);
-    f[0] = ldexpf(1.f, e);
-    f[1] = (float)bound;
-  }
+  if (threadIdx.x == 0) set_fix(P, red[0]);
 }
 __global__ void fix_kernel(Dev P, const float2* start, const float2* goal) {
   fix_block(P, start, goal);
@@ -419,30 +422,60 @@ __global__ void reset_kernel(Dev P, float2* z0, float2* z1, const float2* start,
 
 // New fixed positions (plan_set_endpoints): the fixed break-points of both z
 // buffers and the fixed-point scale, which depends on the layout's extent.
-// One block.  With a check key (the device check ran first), the new
-// positions come from the staging area and are applied only if the check
-// found no violation; the key is then handed to the host (key[1]) and reset
-// to ~0 for the next call.
+// Host-checked endpoints (no key): one block, the scale from a reduction over
+// the new endpoints.  Device-checked ones: one thread per agent copies them
+// from the staging area only if the check found no violation (key[0] clear);
+// the check kernel has reduced their largest coordinate into key[1], from
+// which thread 0 derives the scale; the verdict goes to the host's word.
+// Every block reads key[0], then counts itself in key[2]; the last block to
+// count resets the three words for the next call, once every block has read
+// them.
 __global__ void endpoints_fix_kernel(Dev P, float2* start, float2* goal, const float2* staged,
-                                     unsigned long long* key) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) ok = key ? (key[0] == ~0ull) : 1;
-  __syncthreads();
-  if (!ok) {
-    if (threadIdx.x == 0) { key[1] = key[0]; key[0] = ~0ull; }
-    return;
-  }
+                                     unsigned long long* key, unsigned long long* verdict) {
   const size_t E1 = (size_t)P.eta + 1;
   float2* z0 = const_cast<float2*>(P.z);
-  for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
-    if (staged) { start[i] = staged[i]; goal[i] = staged[P.p + i]; }
-    const float2 a = start[i], b = goal[i];
+  if (!key) {
+    for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
+      const float2 a = start[i], b = goal[i];
+      z0[i * E1] = a; P.z_next[i * E1] = a;
+      z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
+    }
+    __syncthreads();
+    fix_block(P, start, goal);
+    return;
+  }
+  __shared__ unsigned long long sk;
+  __shared__ float sL;
+  if (threadIdx.x == 0) {
+    sk = key[0];
+    sL = __uint_as_float((unsigned)key[1]);
+    __threadfence();
+    if (atomicAdd(key + 2, 1ull) == gridDim.x - 1) {  // every block has read the words
+      key[0] = ~0ull;
+      key[1] = 0ull;
+      key[2] = 0ull;
+    }
+  }
+  __syncthreads();
+  const unsigned long long k = sk;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == ~0ull && i < P.p) {
+    const float2 a = staged[i], b = staged[P.p + i];
+    start[i] = a; goal[i] = b;
     z0[i * E1] = a; P.z_next[i * E1] = a;
     z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
   }
-  __syncthreads();
-  fix_block(P, start, goal);
-  if (key && threadIdx.x == 0) { key[1] = ~0ull; key[0] = ~0ull; }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (k == ~0ull) {
+      float L = sL;
+      for (int w = 0; w < P.nw; ++w) {
+        const float4 W = P.walls[w];
+        L = fmaxf(L, fmaxf(fmaxf(fabsf(W.x), fabsf(W.y)), fmaxf(fabsf(W.z), fabsf(W.w))));
+      }
+      set_fix(P, L);
+    }
+    *verdict = k;
+  }
 }
 
 // Feasibility of new fixed positions on the device (plan_set_endpoints), with
@@ -461,20 +494,35 @@ __global__ void endpoint_check_kernel(int p, int ntp, const int2* tiles, const f
                                       const float2* gl, const float* radius, int nw,
                                       const float4* walls, int goals, int pair_blocks,
                                       unsigned long long* key) {
+  __shared__ float2 xr[TILE], xc[TILE];
+  __shared__ float rr[TILE], rc[TILE];
   unsigned long long best = ~0ull;
+  float ext = 0.f;  // largest coordinate magnitude seen (the new layout's extent)
   if ((int)blockIdx.x < pair_blocks) {
     const int which = (int)blockIdx.x / ntp, tp = (int)blockIdx.x - which * ntp;
     const int2 IJ = tiles[tp];
     const float2* X = which ? gl : st;
+    // the tile's row and column agents, one load round
+    if (threadIdx.x < 2 * TILE) {
+      const int c = threadIdx.x & 31, k = (threadIdx.x < TILE ? IJ.x : IJ.y) * TILE + c;
+      const float2 x = k < p ? X[k] : mk(0.f, 0.f);
+      const float r = k < p ? radius[k] : 0.f;
+      if (threadIdx.x < TILE) { xr[c] = x; rr[c] = r; } else { xc[c] = x; rc[c] = r; }
+      if (IJ.x == IJ.y || threadIdx.x >= TILE) ext = fmaxf(fabsf(x.x), fabsf(x.y));
+      if (!goals && threadIdx.x >= TILE && k < p)  // unchecked goals still set the extent
+        ext = fmaxf(ext, fmaxf(fabsf(gl[k].x), fabsf(gl[k].y)));
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < TILE * TILE; q += blockDim.x) {
-      const int i = IJ.x * TILE + (q >> 5), j = IJ.y * TILE + (q & 31);
+      const int r = q >> 5, c = q & 31;
+      const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
       if (i >= j || j >= p) continue;
       // FP32 screen: pairs farther apart than (1 + 1e-4)(r_i + r_j) cannot
       // fail the FP64 test (FP32 rounding here is below 1e-6 relative)
-      const float fx = X[j].x - X[i].x, fy = X[j].y - X[i].y, fR = radius[i] + radius[j];
+      const float fx = xc[c].x - xr[r].x, fy = xc[c].y - xr[r].y, fR = rr[r] + rc[c];
       if (fx * fx + fy * fy > 1.0002f * fR * fR) continue;
-      const double dx = (double)X[j].x - (double)X[i].x, dy = (double)X[j].y - (double)X[i].y;
-      const double R = (double)radius[i] + (double)radius[j];
+      const double dx = (double)xc[c].x - (double)xr[r].x, dy = (double)xc[c].y - (double)xr[r].y;
+      const double R = (double)rr[r] + (double)rc[c];
       if (dx * dx + dy * dy < R * R) best = min(best, endpoint_key(which, i, j));
     }
   } else {
@@ -497,6 +545,9 @@ __global__ void endpoint_check_kernel(int p, int ntp, const int2* tiles, const f
     }
   }
   block_min_u64(best, key);
+  // the extent: a non-negative float orders like its bits
+  for (int o = 16; o > 0; o >>= 1) ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
+  if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicMax(key + 1, (unsigned long long)__float_as_uint(ext));
 }
 
 __device__ __forceinline__ size_t pair_index(int p, int i, int j) {
@@ -822,7 +873,7 @@ struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
   size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, sched,
       stamps, heavy, accx, accy, accc, fix,
-      res, status, count, ccost, chk, estage, ekey;
+      res, status, count, ccost, chk, ekey;
   size_t total;
 };
 
@@ -882,8 +933,7 @@ Layout layout_for(const plan_config* c) {
   L.count = take(16);
   L.ccost = take(p * eta * 8);  // FP64 kinetic coefficients for plan_check
   L.chk = take(4 * 8);          // plan_check results
-  L.estage = take(p * 16);      // plan_set_endpoints: new start and goal, checked on the device
-  L.ekey = take(16);            // ... the first violation found, and its copy for the host
+  L.ekey = take(24);            // plan_set_endpoints: first violation, extent, fix-up blocks done
   L.total = o;
   return L;
 }
@@ -1039,6 +1089,7 @@ struct plan_s {
   int pcount = 0;
   unsigned* h_res;  // pinned host words: residual readback (0), endpoint check key (2..3)
   float* h_stage = nullptr;  // pinned staging of new endpoints (plan_set_endpoints)
+  cudaGraphExec_t gset = nullptr;  // plan_set_endpoints' device work (fixed pointers)
   EndpointGrid grid;         // the host check's arrays, kept between calls
   std::vector<float> h_radius;
   std::vector<float> h_walls;
@@ -1352,10 +1403,13 @@ plan_status plan_reset(plan_t h) {
   CK(cudaMemsetAsync(h->at<void>(h->L.res), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.wcount), 0, 16, h->stream));
   CK(cudaMemsetAsync(h->at<void>(h->L.sched), 0, 16, h->stream));
-  CK(cudaMemsetAsync(h->at<void>(h->L.ekey), 0xff, 16, h->stream));
+
   CK(cudaMemsetAsync(h->at<void>(h->L.stamps), 0xff, 2 * (size_t)h->eta * h->ntp * 4, h->stream));
   CK(clear_sums(h));
   CK(cudaMemsetAsync(h->at<void>(h->L.status), 0, 4, h->stream));
+  // plan_set_endpoints' words: no violation, extent 0, no fix-up block done
+  CK(cudaMemsetAsync(h->at<void>(h->L.ekey), 0xff, 8, h->stream));
+  CK(cudaMemsetAsync(h->at<char>(h->L.ekey) + 8, 0, 16, h->stream));
   fix_kernel<<<1, 256, 0, h->stream>>>(P, h->at<float2>(h->L.start), h->at<float2>(h->L.goal));
   const int n = std::max(h->p * (h->eta + 1), h->eta * h->p);
   reset_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(P, h->at<float2>(h->L.z0), h->at<float2>(h->L.z1),
@@ -1499,6 +1553,7 @@ void plan_destroy(plan_t h) {
   for (int q = 0; q < 4; ++q)
     if (h->gexec8[q]) cudaGraphExecDestroy(h->gexec8[q]);
   if (h->pend) cudaEventDestroy(h->pend);
+  if (h->gset) cudaGraphExecDestroy(h->gset);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->adj) cudaFree(h->adj);
   delete h;
@@ -1517,7 +1572,8 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
     if (st != PLAN_OK) return st;
     CK(cudaMemcpyAsync(d_start, start, p * 8, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(d_goal, goal, p * 8, cudaMemcpyHostToDevice, h->stream));
-    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, nullptr, nullptr);
+    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, nullptr, nullptr,
+                                                   nullptr);
     CK(cudaGetLastError());
     // the caller's host buffers may be reused once this returns
     CK(cudaStreamSynchronize(h->stream));
@@ -1527,20 +1583,39 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
     // whole update is enqueued before the one readback
     std::memcpy(h->h_stage, start, p * 8);
     std::memcpy(h->h_stage + 2 * p, goal, p * 8);
-    float2* staged = h->at<float2>(h->L.estage);
-    unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
-    CK(cudaMemcpyAsync(staged, h->h_stage, p * 16, cudaMemcpyHostToDevice, h->stream));
-    const int goals = h->vo ? 0 : 1;
-    const int pair_blocks = (int)h->ntp * (1 + goals);
-    const long long nwall = (long long)p * h->nw * (1 + goals);
-    const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
-    endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->stream>>>(
-        h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
-        h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
-    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, staged, key);
-    CK(cudaGetLastError());
     unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
-    CK(cudaMemcpyAsync(hk, key + 1, 8, cudaMemcpyDeviceToHost, h->stream));
+    if (!h->gset) {
+      // check, apply if the check passed, hand the verdict back: the kernels
+      // read the new endpoints from the pinned staging buffer and write the
+      // verdict into pinned host memory directly (both are mapped into the
+      // device's address space), and every pointer is fixed for the plan's
+      // life (both z buffers get the new fixed ends, whichever is current),
+      // so one graph serves every call
+      float2* staged = nullptr;
+      unsigned long long* verdict = nullptr;
+      CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&staged), h->h_stage, 0));
+      CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&verdict), hk, 0));
+      unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
+      const int goals = h->vo ? 0 : 1;
+      const int pair_blocks = (int)h->ntp * (1 + goals);
+      const long long nwall = (long long)p * h->nw * (1 + goals);
+      const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->cap>>>(
+          h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
+          h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
+      endpoints_fix_kernel<<<(unsigned)((p + 255) / 256), 256, 0, h->cap>>>(h->dev(h->k), d_start, d_goal,
+                                                                           staged, key, verdict);
+      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gset, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        h->gset = nullptr;
+        return fail(PLAN_ECUDA, "endpoint graph: %s", cudaGetErrorString(e));
+      }
+    }
+    CK(cudaGraphLaunch(h->gset, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const unsigned long long k = *hk;
     if (k != ~0ull) {
