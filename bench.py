@@ -278,6 +278,24 @@ def timed_iterations(pl, stream, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev) / steps
 
 
+def by_iterate(pk, inst, flush, stream, points=(20, 1000, 10000, 100000), steps=10):
+    """The same timed iteration (L2 flushed before each, CUDA events) at
+    several points of one solve: the benchmark's iteration-20 state is the
+    crowded start, where the last segment still spans each agent's whole
+    path; later iterates are nearer the converged plan."""
+    import torch
+    out = {}
+    with pk.Planner.from_instance(inst) as pl:
+        done = 0
+        for k in points:
+            pl.iterate(k - done)
+            done = k
+            ms = timed_iterations(pl, stream, steps, flush)
+            done += steps
+            out[str(k)] = {"ms_per_step": ms, "active_coll": pl.info()["active_coll"]}
+    return out
+
+
 def kernel_times(pl, stream, steps, flush):
     """Average per-kernel ms over `steps` iterations (events inside the
     library, on the streams the kernels run on), L2 flushed before each."""
@@ -698,6 +716,7 @@ def main():
                        "path": "plan_set_endpoints(host) + plan_iterate(1) + "
                                "plan_get_trajectory(host), pinned buffers"}
     if rank == 0 and world == 1 and not args.quick:
+        line["by_iterate"] = by_iterate(pk, inst, flush, stream)
         line["batching"] = batching(pk)
         line["differentiation"] = differentiation(pk)
         line["time_to_converge"] = time_to_converge(
