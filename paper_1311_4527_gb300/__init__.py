@@ -49,7 +49,8 @@ EXPORTED_SYMBOLS = ["plan_workspace_size", "plan_create", "plan_reset", "plan_se
                     "plan_unroll", "plan_set_velocity_limits", "plan_export_velocity_state",
                     "plan_import_velocity_state", "plan_set_energy", "plan_export_back_weights",
                     "plan_import_back_weights", "plan_vo_epoch", "plan_get_endpoints",
-                    "plan_check", "plan_batch_import_state", "plan_batch_export_state"]
+                    "plan_check", "plan_batch_import_state", "plan_batch_export_state",
+                    "plan_set_endpoints_async"]
 
 
 class PlanError(RuntimeError):
@@ -91,6 +92,7 @@ def load_library(path: str | None = None):
                                 c_void_p, POINTER(c_void_p)]
     lib.plan_reset.argtypes = [c_void_p]
     lib.plan_set_endpoints.argtypes = [c_void_p, fp, fp]
+    lib.plan_set_endpoints_async.argtypes = [c_void_p, fp, fp]
     lib.plan_iterate.argtypes = [c_void_p, c_int, fp]
     lib.plan_solve.argtypes = [c_void_p, POINTER(c_int), fp]
     lib.plan_get_trajectory.argtypes = [c_void_p, c_void_p, c_int]
@@ -259,10 +261,14 @@ class Planner:
             _check(code)
         return code == 0, int(it.value), float(r.value)
 
-    def set_endpoints(self, start, goal):
+    def set_endpoints(self, start, goal, wait=True):
+        """New fixed endpoints, keeping the current iterate.  wait=False
+        returns before the device check: an infeasible update is then
+        reported (and not applied) by the next call that synchronises."""
         st, st_p = _f32(start, (self.p, 2))
         gl, gl_p = _f32(goal, (self.p, 2))
-        _check(_lib.plan_set_endpoints(self._h, st_p, gl_p))
+        f = _lib.plan_set_endpoints if wait else _lib.plan_set_endpoints_async
+        _check(f(self._h, st_p, gl_p))
 
     def set_params(self, radius=None, cost_w=None):
         """Replace the radii and/or cost weights (same layout as at creation)."""

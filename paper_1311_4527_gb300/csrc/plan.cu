@@ -1090,6 +1090,9 @@ struct plan_s {
   unsigned* h_res;  // pinned host words: residual readback (0), endpoint check key (2..3)
   float* h_stage = nullptr;  // pinned staging of new endpoints (plan_set_endpoints)
   cudaGraphExec_t gset = nullptr;  // plan_set_endpoints' device work (fixed pointers)
+  cudaEvent_t ep_event = nullptr;  // after the last endpoint update's graph
+  bool ep_pending = false;         // an asynchronous endpoint update's verdict not yet read
+  std::vector<float> ep_start, ep_goal;  // its endpoints, taken on the host once it passed
   EndpointGrid grid;         // the host check's arrays, kept between calls
   std::vector<float> h_radius;
   std::vector<float> h_walls;
@@ -1172,6 +1175,11 @@ struct plan_s {
     return P;
   }
 };
+
+namespace {
+// an asynchronous endpoint update's verdict, read by every call that synchronises
+plan_status settle_endpoints(plan_t h);
+}  // namespace
 
 namespace {
 
@@ -1554,22 +1562,112 @@ void plan_destroy(plan_t h) {
     if (h->gexec8[q]) cudaGraphExecDestroy(h->gexec8[q]);
   if (h->pend) cudaEventDestroy(h->pend);
   if (h->gset) cudaGraphExecDestroy(h->gset);
+  if (h->ep_event) cudaEventDestroy(h->ep_event);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->adj) cudaFree(h->adj);
   delete h;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The endpoint update's graph (built on first use): check the staged
+// endpoints, apply them if the check passed, hand the verdict back.  The
+// kernels read the new endpoints from the pinned staging buffer and write the
+// verdict into pinned host memory directly (both are mapped into the
+// device's address space), and every pointer is fixed for the plan's life
+// (both z buffers get the new fixed ends, whichever is current), so one
+// graph serves every call.
+plan_status endpoint_graph(plan_t h) {
+  if (h->gset) return PLAN_OK;
+  const size_t p = h->p;
+  float2* staged = nullptr;
+  unsigned long long* verdict = nullptr;
+  unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&staged), h->h_stage, 0));
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&verdict), hk, 0));
+  unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
+  const int goals = h->vo ? 0 : 1;
+  const int pair_blocks = (int)h->ntp * (1 + goals);
+  const long long nwall = (long long)p * h->nw * (1 + goals);
+  const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
+  if (!h->ep_event) CK(cudaEventCreateWithFlags(&h->ep_event, cudaEventDisableTiming));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->cap>>>(
+      h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
+      h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
+  endpoints_fix_kernel<<<(unsigned)((p + 255) / 256), 256, 0, h->cap>>>(
+      h->dev(h->k), h->at<float2>(h->L.start), h->at<float2>(h->L.goal), staged, key, verdict);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gset, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->gset = nullptr;
+    return fail(PLAN_ECUDA, "endpoint graph: %s", cudaGetErrorString(e));
+  }
+  return PLAN_OK;
+}
+
+// Enqueue a device-checked endpoint update (p <= kDeviceEndpointCheck):
+// stage the endpoints and launch the graph; the verdict is pending until
+// settled.
+plan_status launch_endpoint_update(plan_t h, const float* start, const float* goal) {
+  const size_t p = h->p;
+  plan_status st = endpoint_graph(h);
+  if (st != PLAN_OK) return st;
+  std::memcpy(h->h_stage, start, p * 8);
+  std::memcpy(h->h_stage + 2 * p, goal, p * 8);
+  CK(cudaGraphLaunch(h->gset, h->stream));
+  CK(cudaEventRecord(h->ep_event, h->stream));
+  h->ep_start.assign(start, start + 2 * p);
+  h->ep_goal.assign(goal, goal + 2 * p);
+  h->ep_pending = true;
+  h->adj_valid = false;
+  return PLAN_OK;
+}
+
+// Read a pending endpoint verdict once its graph has run (the caller has
+// synchronised, or this waits for the graph): keep the endpoints on the host
+// if they passed, else report the violation (the device kept the previous
+// endpoints).
+plan_status settle_endpoints(plan_t h) {
+  if (!h->ep_pending) return PLAN_OK;
+  CK(cudaEventSynchronize(h->ep_event));
+  h->ep_pending = false;
+  const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(h->h_res + 2);
+  if (k == ~0ull) {
+    h->h_start.swap(h->ep_start);
+    h->h_goal.swap(h->ep_goal);
+    return PLAN_OK;
+  }
+  const unsigned kind = (unsigned)(k >> 60), i = (unsigned)((k >> 30) & 0x3fffffffu),
+                 j = (unsigned)(k & 0x3fffffffu);
+  if (kind < 2)
+    return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %u and %u overlap",
+                kind ? "goal" : "start", i, j);
+  return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %u is within its radius of wall %u",
+              kind == 3 ? "goal" : "start", i, j);
+}
+
+}  // namespace
+
+extern "C" {
+
 plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) {
   if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
   const size_t p = h->p;
   if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
-  float2* d_start = h->at<float2>(h->L.start);
-  float2* d_goal = h->at<float2>(h->L.goal);
+  plan_status st = settle_endpoints(h);  // an earlier asynchronous update's verdict
+  if (st != PLAN_OK) return st;
   if (!h->h_stage || p > kDeviceEndpointCheck) {
     // the host grid check, then the copies
-    plan_status st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(),
-                                     !h->vo, &h->grid);
+    st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(), !h->vo,
+                         &h->grid);
     if (st != PLAN_OK) return st;
+    float2* d_start = h->at<float2>(h->L.start);
+    float2* d_goal = h->at<float2>(h->L.goal);
     CK(cudaMemcpyAsync(d_start, start, p * 8, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(d_goal, goal, p * 8, cudaMemcpyHostToDevice, h->stream));
     endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, nullptr, nullptr,
@@ -1577,61 +1675,29 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
     CK(cudaGetLastError());
     // the caller's host buffers may be reused once this returns
     CK(cudaStreamSynchronize(h->stream));
-  } else {
-    // through a pinned staging buffer, checked on the device; the new
-    // endpoints are applied on the device only if the check passed, so the
-    // whole update is enqueued before the one readback
-    std::memcpy(h->h_stage, start, p * 8);
-    std::memcpy(h->h_stage + 2 * p, goal, p * 8);
-    unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
-    if (!h->gset) {
-      // check, apply if the check passed, hand the verdict back: the kernels
-      // read the new endpoints from the pinned staging buffer and write the
-      // verdict into pinned host memory directly (both are mapped into the
-      // device's address space), and every pointer is fixed for the plan's
-      // life (both z buffers get the new fixed ends, whichever is current),
-      // so one graph serves every call
-      float2* staged = nullptr;
-      unsigned long long* verdict = nullptr;
-      CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&staged), h->h_stage, 0));
-      CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&verdict), hk, 0));
-      unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
-      const int goals = h->vo ? 0 : 1;
-      const int pair_blocks = (int)h->ntp * (1 + goals);
-      const long long nwall = (long long)p * h->nw * (1 + goals);
-      const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
-      cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-      endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->cap>>>(
-          h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
-          h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
-      endpoints_fix_kernel<<<(unsigned)((p + 255) / 256), 256, 0, h->cap>>>(h->dev(h->k), d_start, d_goal,
-                                                                           staged, key, verdict);
-      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gset, g, 0);
-      if (g) cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        h->gset = nullptr;
-        return fail(PLAN_ECUDA, "endpoint graph: %s", cudaGetErrorString(e));
-      }
-    }
-    CK(cudaGraphLaunch(h->gset, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    const unsigned long long k = *hk;
-    if (k != ~0ull) {
-      const unsigned kind = (unsigned)(k >> 60), i = (unsigned)((k >> 30) & 0x3fffffffu),
-                     j = (unsigned)(k & 0x3fffffffu);
-      if (kind < 2)
-        return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %u and %u overlap",
-                    kind ? "goal" : "start", i, j);
-      return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %u is within its radius of wall %u",
-                  kind == 3 ? "goal" : "start", i, j);
-    }
+    h->adj_valid = false;
+    h->h_start.assign(start, start + 2 * p);
+    h->h_goal.assign(goal, goal + 2 * p);
+    return PLAN_OK;
   }
-  h->adj_valid = false;
-  h->h_start.assign(start, start + 2 * p);
-  h->h_goal.assign(goal, goal + 2 * p);
-  return PLAN_OK;
+  // checked on the device: the whole update is enqueued before the one wait
+  st = launch_endpoint_update(h, start, goal);
+  if (st != PLAN_OK) return st;
+  return settle_endpoints(h);
+}
+
+plan_status plan_set_endpoints_async(plan_t h, const float* start, const float* goal) {
+  if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
+  const size_t p = h->p;
+  if (!h->h_stage || p > kDeviceEndpointCheck)
+    return fail(PLAN_EUNSUPPORTED, "asynchronous endpoint updates need the device check (p <= %zu)",
+                kDeviceEndpointCheck);
+  if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
+  // the previous update must have consumed the staging buffer, and its
+  // verdict is read before this one can overwrite it
+  plan_status st = settle_endpoints(h);
+  if (st != PLAN_OK) return st;
+  return launch_endpoint_update(h, start, goal);
 }
 
 plan_status plan_iterate(plan_t h, int k_iters, float* max_residual) {
@@ -1640,7 +1706,10 @@ plan_status plan_iterate(plan_t h, int k_iters, float* max_residual) {
   if (k_iters > 0) h->adj_valid = false;
   plan_status st = run_iterations(h, k_iters);
   if (st != PLAN_OK) return st;
-  if (max_residual) return read_residual(h, max_residual);
+  if (max_residual) {
+    st = read_residual(h, max_residual);
+    return st == PLAN_OK ? settle_endpoints(h) : st;
+  }
   return PLAN_OK;
 }
 
@@ -1667,7 +1736,10 @@ plan_status plan_get_trajectory(plan_t h, float* z, int on_device) {
   const size_t bytes = (size_t)h->p * (h->eta + 1) * 8;
   const void* src = h->cur ? h->at<void>(h->L.z1) : h->at<void>(h->L.z0);
   CK(cudaMemcpyAsync(z, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
-  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  if (!on_device) {
+    CK(cudaStreamSynchronize(h->stream));
+    return settle_endpoints(h);
+  }
   return PLAN_OK;
 }
 
@@ -1752,7 +1824,7 @@ plan_status plan_check(plan_t h, double* total_cost, double* min_pair_clearance,
   if (min_pair_clearance) *min_pair_clearance = std::sqrt(v[1]);
   if (min_wall_clearance) *min_wall_clearance = std::sqrt(v[2]);
   if (max_endpoint_error) *max_endpoint_error = v[3];
-  return PLAN_OK;
+  return settle_endpoints(h);
 }
 
 plan_status plan_get_info(plan_t h, plan_info* info) {
@@ -1775,7 +1847,7 @@ plan_status plan_get_info(plan_t h, plan_info* info) {
   CK(cudaStreamSynchronize(h->stream));
   info->active_coll = (long long)hc[0];
   info->active_wall = (long long)hc[1];
-  return PLAN_OK;
+  return settle_endpoints(h);
 }
 
 plan_status plan_profile(plan_t h, int enable, float* ms, int* iterations) {
@@ -2097,7 +2169,7 @@ plan_status plan_get_endpoints(plan_t h, float* start, float* goal) {
   if (start) CK(cudaMemcpyAsync(start, h->at<void>(h->L.start), (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
   if (goal) CK(cudaMemcpyAsync(goal, h->at<void>(h->L.goal), (size_t)h->p * 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return PLAN_OK;
+  return settle_endpoints(h);
 }
 
 plan_status plan_vo_epoch(plan_t h, const float* dest, float step, float advance, int* iters,
@@ -2162,6 +2234,10 @@ plan_status plan_set_energy(plan_t h, int on) {
 
 plan_status plan_set_params(plan_t h, const float* radius, const float* cost_w) {
   if (!h) return fail(PLAN_EINVAL, "null plan");
+  {  // new radii are checked against the endpoints on the host: settle them first
+    plan_status st = settle_endpoints(h);
+    if (st != PLAN_OK) return st;
+  }
   const size_t p = h->p, eta = h->eta;
   const size_t ncost = (h->cfg.flags & PLAN_COST_PER_SEGMENT) ? p * eta : p;
   if (radius) {

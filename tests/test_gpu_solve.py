@@ -244,3 +244,40 @@ def test_set_endpoints_checks_new_positions_on_the_device():
         z = pl.trajectory().cpu().numpy()
         assert np.array_equal(z[:, -1], new_goal.astype(np.float32))
         assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
+
+
+def test_asynchronous_endpoint_updates_report_at_the_next_synchronising_call():
+    """plan_set_endpoints_async: a feasible update is applied before the next
+    iteration; an infeasible one is not applied and is reported by the next
+    call that synchronises (here the trajectory to the host), after which
+    the plan takes further updates."""
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(72, 6, seed=11)
+    with pk.Planner.from_instance(inst) as pl:
+        pl.iterate(5)
+        g1 = inst.goal.copy()
+        g1[0] += 0.05
+        assert _first_violation(inst.start, g1, inst.radius, inst.walls) is None
+        pl.set_endpoints(inst.start, g1, wait=False)
+        pl.iterate(3)
+        z = pl.trajectory_host()
+        assert np.array_equal(z[:, -1], g1.astype(np.float32))
+        bad = inst.start.copy()
+        bad[9] = bad[5] + 0.5 * (inst.radius[5] + inst.radius[9]) * np.array([1.0, 0.0])
+        expect = _first_violation(bad, g1, inst.radius, inst.walls)
+        assert expect is not None
+        pl.set_endpoints(bad, g1, wait=False)          # returns before the check
+        pl.iterate(2)
+        with pytest.raises(pk.PlanError) as e:
+            pl.trajectory_host()
+        assert e.value.status == "PLAN_EINFEASIBLE_INPUT" and expect in str(e.value)
+        z = pl.trajectory_host()                        # settled: no error any more
+        assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
+        assert np.array_equal(z[:, -1], g1.astype(np.float32))
+        st, gl = pl.endpoints()
+        assert np.array_equal(st, inst.start.astype(np.float32)) and np.array_equal(gl, g1.astype(np.float32))
+        g2 = g1.copy()
+        g2[1] += 0.05
+        pl.set_endpoints(inst.start, g2, wait=False)
+        assert pl.iterate(1, residual=True) >= 0.0
+        assert np.array_equal(pl.trajectory_host()[:, -1], g2.astype(np.float32))
