@@ -109,7 +109,11 @@ def test_bad_parameters_are_rejected(lib):
 
 
 def test_differentiation_entry_points_reject_null_plans(lib):
+    f = ctypes.POINTER(ctypes.c_float)
     assert lib.plan_check(None, None, None, None, None) == 1
+    assert lib.plan_set_endpoints_async(None, None, None) == 1
+    assert lib.plan_batch_import_state(None, 0, None, None, None, None) == 1
+    assert lib.plan_batch_export_state(None, 0, None, None, None, None, None, None) == 1
     assert lib.plan_backward(None, 1, None, None, None, None, None) == 1
     assert lib.plan_unroll(None, 10, 0) == 1
     assert lib.plan_set_params(None, None, None) == 1
