@@ -217,7 +217,7 @@ __device__ __forceinline__ void block_min_u64(unsigned long long v, unsigned lon
       const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
       v = w < v ? w : v;
     }
-    if (lane == 0) atomicMin(out, v);
+    if (lane == 0 && v != ~0ull) atomicMin(out, v);  // nothing to report: no atomic
   }
 }
 
@@ -545,9 +545,17 @@ __global__ void endpoint_check_kernel(int p, int ntp, const int2* tiles, const f
     }
   }
   block_min_u64(best, key);
-  // the extent: a non-negative float orders like its bits
+  // the extent, reduced over the block first (a non-negative float orders
+  // like its bits), then one global update, and only if it raises the value:
+  // thousands of atomics on one word would serialise
+  __shared__ unsigned bext;
+  if (threadIdx.x == 0) bext = 0u;
+  __syncthreads();
   for (int o = 16; o > 0; o >>= 1) ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
-  if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicMax(key + 1, (unsigned long long)__float_as_uint(ext));
+  if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicMax(&bext, __float_as_uint(ext));
+  __syncthreads();
+  if (threadIdx.x == 0 && bext > (unsigned)*reinterpret_cast<volatile unsigned long long*>(key + 1))
+    atomicMax(key + 1, (unsigned long long)bext);
 }
 
 __device__ __forceinline__ size_t pair_index(int p, int i, int j) {
@@ -1879,6 +1887,7 @@ namespace {
 __global__ void record_kernel(Dev P, const float2* zk, float2* tz, float4* tukin, uint32_t* tfid,
                               float4* tucl, float4* tuch, unsigned* tcount, uint32_t* tsidx,
                               float4* tsu, unsigned* tscount) {
+  pdl_begin();
   const unsigned cnt = *P.work_count;
   const unsigned nz = (unsigned)P.p * (P.eta + 1), nk = (unsigned)P.eta * P.p;
   const unsigned nseg = (unsigned)(P.nw + P.nv) * nk;
@@ -1904,18 +1913,30 @@ __global__ void record_kernel(Dev P, const float2* zk, float2* tz, float4* tukin
   }
 }
 
+// Zeroes n 32-bit counters spaced stride bytes apart (the compaction counter
+// of every tape slot of a segment, before its replay).
+__global__ void zero_strided_kernel(char* base, size_t stride, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) *reinterpret_cast<unsigned*>(base + i * stride) = 0u;
+}
+
+// The adjoint passes run with programmatic dependent launch, like the
+// forward ones: each waits (griddepcontrol.wait) for its predecessor's
+// writes, but its CTAs are scheduled while the predecessor drains.
 __global__ void __launch_bounds__(256) bw_scatter_kernel(AdjDev A) {
+  pdl_begin();
   const unsigned n = (unsigned)(A.eta * A.p) + *A.count + *A.scount;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     bw_scatter_item(A, t);
 }
 
 __global__ void bw_node_kernel(AdjDev A) {
+  pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < A.p * (A.eta + 1)) bw_node(A, t);
 }
 
 __global__ void __launch_bounds__(256) bw_factor_kernel(AdjDev A) {
+  pdl_begin();
   const unsigned n = (unsigned)(A.eta * A.p) + *A.count + *A.scount;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     bw_factor_item(A, t);
@@ -2346,25 +2367,25 @@ plan_status plan_backward(plan_t h, int K, const float* dL_dz, float* d_start, f
     if ((st = snapshot(h, A, seg, false)) != PLAN_OK) return st;
     h->k = c0;
     h->cur = h->ck_cur[seg];
+    zero_strided_kernel<<<1, 64, 0, h->stream>>>(h->adj + A.tape0 + A.t_scount, A.slot_bytes, c1 - c0);
+    CK(cudaGetLastError());
     for (int k = c0; k < c1; ++k) {
       const float2* zk = h->cur ? h->at<float2>(h->L.z1) : h->at<float2>(h->L.z0);
       if ((st = run_iteration(h)) != PLAN_OK) return st;
       char* t = h->adj + A.tape0 + (size_t)(k - c0) * A.slot_bytes;
-      CK(cudaMemsetAsync(t + A.t_scount, 0, 4, h->stream));
-      record_kernel<<<h->prox_grid, 256, 0, h->stream>>>(
-          h->dev(k), zk, reinterpret_cast<float2*>(t + A.t_z), reinterpret_cast<float4*>(t + A.t_ukin),
-          reinterpret_cast<uint32_t*>(t + A.t_fid), reinterpret_cast<float4*>(t + A.t_ucl),
-          reinterpret_cast<float4*>(t + A.t_uch), reinterpret_cast<unsigned*>(t + A.t_count),
-          reinterpret_cast<uint32_t*>(t + A.t_sidx), reinterpret_cast<float4*>(t + A.t_su),
-          reinterpret_cast<unsigned*>(t + A.t_scount));
-      CK(cudaGetLastError());
+      CK(launch_pdl(record_kernel, (unsigned)h->prox_grid, 256u, h->stream, h->dev(k), zk,
+                    reinterpret_cast<float2*>(t + A.t_z), reinterpret_cast<float4*>(t + A.t_ukin),
+                    reinterpret_cast<uint32_t*>(t + A.t_fid), reinterpret_cast<float4*>(t + A.t_ucl),
+                    reinterpret_cast<float4*>(t + A.t_uch), reinterpret_cast<unsigned*>(t + A.t_count),
+                    reinterpret_cast<uint32_t*>(t + A.t_sidx), reinterpret_cast<float4*>(t + A.t_su),
+                    reinterpret_cast<unsigned*>(t + A.t_scount)));
     }
     // the adjoint steps of the segment, last iteration first
     for (int k = c1 - 1; k >= c0; --k) {
       const AdjDev D = adj_dev(h, A, k - c0, k, zb_in, zb_out);
-      bw_scatter_kernel<<<h->prox_grid, 256, 0, h->stream>>>(D);
-      bw_node_kernel<<<node_grid, 256, 0, h->stream>>>(D);
-      bw_factor_kernel<<<h->prox_grid, 256, 0, h->stream>>>(D);
+      CK(launch_pdl(bw_scatter_kernel, (unsigned)h->prox_grid, 256u, h->stream, D));
+      CK(launch_pdl(bw_node_kernel, node_grid, 256u, h->stream, D));
+      CK(launch_pdl(bw_factor_kernel, (unsigned)h->prox_grid, 256u, h->stream, D));
       CK(cudaGetLastError());
       std::swap(zb_in, zb_out);
     }
