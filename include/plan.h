@@ -124,22 +124,27 @@ plan_status plan_reset(plan_t plan);
 
 /* Replace the fixed start and goal positions (host, p x 2 each) and keep the
  * current iterate as the warm start (the re-planning use of Appendix J).  The
- * new endpoints are checked like in plan_create.  Copies are enqueued on the
- * plan's stream; the call returns once the host buffers may be reused. */
+ * new endpoints are checked like in plan_create (on the device for
+ * p <= 8192, on the host above); a failed check leaves the plan unchanged.
+ * Copies are enqueued on the plan's stream; the call returns once the host
+ * buffers may be reused.  Errors: PLAN_EINVAL (null pointers, a non-finite
+ * coordinate), PLAN_EINFEASIBLE_INPUT (overlapping starts or goals, an
+ * endpoint within its radius of a wall), PLAN_ECUDA. */
 plan_status plan_set_endpoints(plan_t plan, const float* start, const float* goal);
 
 /* plan_set_endpoints without waiting for the check (p <= 8192, where the
  * check runs on the device; else PLAN_EUNSUPPORTED): the new endpoints are
  * checked and, only if they pass, applied on the device in stream order
  * before any work enqueued later; the call returns once the host buffers may
- * be reused.  A failed check is reported as PLAN_EINFEASIBLE_INPUT by the
+ * be reused.  A failed check is reported as PLAN_EINFEASIBLE_INPUT (or
+ * PLAN_EINVAL for a non-finite coordinate) by the
  * next call on this plan that synchronises its stream (plan_iterate with a
  * residual, plan_solve, plan_get_trajectory to the host, plan_check,
  * plan_get_info, plan_get_endpoints, plan_set_params, plan_set_endpoints, or
  * the next plan_set_endpoints_async, which then takes no new endpoints); the
  * plan keeps its previous endpoints, and the iterations enqueued in between
- * ran with them.  Errors returned directly: PLAN_EINVAL (null or non-finite
- * input), PLAN_EUNSUPPORTED, PLAN_ECUDA. */
+ * ran with them.  Errors returned directly: PLAN_EINVAL (null input),
+ * PLAN_EUNSUPPORTED, PLAN_ECUDA. */
 plan_status plan_set_endpoints_async(plan_t plan, const float* start, const float* goal);
 
 /* Run k_iters TWA iterations (Appendix B steps 1-7 over every factor).  When

@@ -91,8 +91,8 @@ def load_library(path: str | None = None):
     lib.plan_create.argtypes = [POINTER(plan_config), fp, fp, fp, fp, fp, c_void_p, c_size_t,
                                 c_void_p, POINTER(c_void_p)]
     lib.plan_reset.argtypes = [c_void_p]
-    lib.plan_set_endpoints.argtypes = [c_void_p, fp, fp]
-    lib.plan_set_endpoints_async.argtypes = [c_void_p, fp, fp]
+    lib.plan_set_endpoints.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.plan_set_endpoints_async.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.plan_iterate.argtypes = [c_void_p, c_int, fp]
     lib.plan_solve.argtypes = [c_void_p, POINTER(c_int), fp]
     lib.plan_get_trajectory.argtypes = [c_void_p, c_void_p, c_int]
@@ -143,6 +143,14 @@ def _check(code):
     if code != 0:
         msg = _lib.plan_last_error().decode(errors="replace")
         raise PlanError(code, msg)
+
+
+def _f32_host(a, shape, n):
+    """a as a C-contiguous float32 array of the given shape (n entries; no
+    copy when it already is one)."""
+    if type(a) is np.ndarray and a.dtype == np.float32 and a.size == n and a.flags.c_contiguous:
+        return a
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
 
 
 def _f32(a, shape):
@@ -199,6 +207,8 @@ class Planner:
         _check(lib.plan_workspace_size(byref(self.cfg), byref(nbytes)))
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         self._keep = []
+        self._ep_ptrs = None  # (start, goal, address, address) of the last in-place endpoints
+        self._z_ptr = None    # (out, address) of the last trajectory_host destination
         st, st_p = _f32(start, (p, 2))
         gl, gl_p = _f32(goal, (p, 2))
         rd, rd_p = _f32(radius, (p,))
@@ -265,10 +275,19 @@ class Planner:
         """New fixed endpoints, keeping the current iterate.  wait=False
         returns before the device check: an infeasible update is then
         reported (and not applied) by the next call that synchronises."""
-        st, st_p = _f32(start, (self.p, 2))
-        gl, gl_p = _f32(goal, (self.p, 2))
+        # raw addresses: this call sits in per-step control loops, where
+        # building ctypes pointer objects costs more than the call itself;
+        # the addresses of arrays passed again (refilled in place) are kept
         f = _lib.plan_set_endpoints if wait else _lib.plan_set_endpoints_async
-        _check(f(self._h, st_p, gl_p))
+        c = self._ep_ptrs
+        if c is not None and c[0] is start and c[1] is goal:
+            _check(f(self._h, c[2], c[3]))
+            return
+        st = _f32_host(start, (self.p, 2), 2 * self.p)
+        gl = _f32_host(goal, (self.p, 2), 2 * self.p)
+        sp, gp = st.ctypes.data, gl.ctypes.data
+        self._ep_ptrs = (start, goal, sp, gp) if (st is start and gl is goal) else None
+        _check(f(self._h, sp, gp))
 
     def set_params(self, radius=None, cost_w=None):
         """Replace the radii and/or cost weights (same layout as at creation)."""
@@ -406,9 +425,19 @@ class Planner:
         return z
 
     def trajectory_host(self, out: np.ndarray | None = None):
+        c = self._z_ptr
+        if c is not None and out is c[0]:
+            _check(_lib.plan_get_trajectory(self._h, c[1], 0))
+            return out
         if out is None:
             out = np.empty((self.p, self.eta + 1, 2), dtype=np.float32)
-        _check(_lib.plan_get_trajectory(self._h, out.ctypes.data_as(c_void_p), 0))
+        elif (type(out) is not np.ndarray or out.dtype != np.float32 or not out.flags.c_contiguous
+              or not out.flags.writeable or out.size != self.p * (self.eta + 1) * 2):
+            raise ValueError("out must be a writeable C-contiguous float32 array of "
+                             f"{self.p * (self.eta + 1) * 2} entries")
+        else:
+            self._z_ptr = (out, out.ctypes.data)
+        _check(_lib.plan_get_trajectory(self._h, out.ctypes.data, 0))
         return out
 
     def n_pairs(self):

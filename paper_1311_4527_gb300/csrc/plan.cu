@@ -155,11 +155,18 @@ __global__ void consensus_kernel(Dev P) {
 // Fixed-point scale of the consensus sums: the largest power of two with
 // 8 (L + 1) x (max incoming edges) x scale <= 2^62, L the largest coordinate
 // magnitude of the endpoints and walls.  One block.
-// The scale from the largest coordinate magnitude L of endpoints and walls.
+// The scale from the largest coordinate magnitude L of endpoints and walls:
+// with y = 8 (L + 1) x edges (exact in double: a 27-bit mantissa times an
+// integer below 2^17), e = floor(log2(2^62 / y)) = 62 - ceil(log2 y), and
+// ceil(log2 y) is read off y's exponent and mantissa bits (no FP64 maths
+// library call: a single thread runs this on the update's critical path).
 __device__ __forceinline__ void set_fix(const Dev& P, float L) {
   const double edges = 2.0 + 2.0 * (P.p - 1) + 2.0 * (P.nw + P.nv);
   const double bound = 8.0 * ((double)L + 1.0);
-  int e = (int)floor(log2(4.611686018427388e18 / (bound * edges)));
+  const unsigned long long yb = (unsigned long long)__double_as_longlong(bound * edges);
+  const int ex = (int)((yb >> 52) & 0x7ff) - 1023;
+  const int clog2 = ex + ((yb & 0xfffffffffffffull) ? 1 : 0);
+  int e = 62 - clog2;
   e = e < 8 ? 8 : (e > 60 ? 60 : e);
   float* f = const_cast<float*>(P.fix);
   f[0] = ldexpf(1.f, e);
@@ -420,142 +427,184 @@ __global__ void reset_kernel(Dev P, float2* z0, float2* z1, const float2* start,
   }
 }
 
-// New fixed positions (plan_set_endpoints): the fixed break-points of both z
-// buffers and the fixed-point scale, which depends on the layout's extent.
-// Host-checked endpoints (no key): one block, the scale from a reduction over
-// the new endpoints.  Device-checked ones: one thread per agent copies them
-// from the staging area only if the check found no violation (key[0] clear);
-// the check kernel has reduced their largest coordinate into key[1], from
-// which thread 0 derives the scale; the verdict goes to the host's word.
-// Every block reads key[0], then counts itself in key[2]; the last block to
-// count resets the three words for the next call, once every block has read
-// them.
-__global__ void endpoints_fix_kernel(Dev P, float2* start, float2* goal, const float2* staged,
-                                     unsigned long long* key, unsigned long long* verdict) {
+// New fixed positions after the host check (plan_set_endpoints, large p):
+// one block writes the fixed break-points of both z buffers and derives the
+// fixed-point scale, which depends on the layout's extent.
+__global__ void endpoints_fix_kernel(Dev P, const float2* start, const float2* goal) {
   const size_t E1 = (size_t)P.eta + 1;
   float2* z0 = const_cast<float2*>(P.z);
-  if (!key) {
-    for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
-      const float2 a = start[i], b = goal[i];
-      z0[i * E1] = a; P.z_next[i * E1] = a;
-      z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
-    }
-    __syncthreads();
-    fix_block(P, start, goal);
-    return;
-  }
-  __shared__ unsigned long long sk;
-  __shared__ float sL;
-  if (threadIdx.x == 0) {
-    sk = key[0];
-    sL = __uint_as_float((unsigned)key[1]);
-    __threadfence();
-    if (atomicAdd(key + 2, 1ull) == gridDim.x - 1) {  // every block has read the words
-      key[0] = ~0ull;
-      key[1] = 0ull;
-      key[2] = 0ull;
-    }
-  }
-  __syncthreads();
-  const unsigned long long k = sk;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == ~0ull && i < P.p) {
-    const float2 a = staged[i], b = staged[P.p + i];
-    start[i] = a; goal[i] = b;
+  for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
+    const float2 a = start[i], b = goal[i];
     z0[i * E1] = a; P.z_next[i * E1] = a;
     z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  __syncthreads();
+  fix_block(P, start, goal);
+}
+
+// A device-checked endpoint update (plan_set_endpoints), one launch.
+// Feasibility of the new fixed positions uses the strict test of the host
+// check in FP64: two disks closer than r_i + r_j, or a disk closer than r_i
+// to a wall segment; a non-finite coordinate fails it before anything else.
+// The first violation in the order (non-finite agents, start pairs, goal
+// pairs, start-wall, goal-wall; then i; then j or the wall) is kept in key[0]
+// as kind << 60 | i << 30 | j (~0 when there is none), and the largest
+// coordinate magnitude of the new starts and goals (the layout's extent, for
+// the fixed-point scale) in key[1].  One warp takes 8 rows of one 32 x 32
+// agent tile pair of the starts (then of the goals) at a time: lane c holds
+// column agent c and the row agents come by shuffles; then every thread takes
+// agent-wall tests, grid-stride.  Each agent's new start and goal are also
+// copied to a device shadow on the way.  The last block to finish (counted in
+// key[2]) writes the verdict (key[0]) to the host's word, resets the three
+// key words for the next update and, if key[0] is clear, applies the update
+// from the shadow: the new endpoints, the fixed break-points of both z
+// buffers and the fixed-point scale.
+__device__ __forceinline__ unsigned long long endpoint_key(unsigned kind, unsigned i, unsigned j) {
+  return ((unsigned long long)kind << 60) | ((unsigned long long)i << 30) | (unsigned long long)j;
+}
+
+constexpr int EP_ROWS = 8;  // rows of a tile pair per warp task
+
+__global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float2* __restrict__ staged,
+                                                              int goals, float2* __restrict__ start,
+                                                              float2* __restrict__ goal,
+                                                              float2* __restrict__ shadow,
+                                                              unsigned long long* key,
+                                                              unsigned long long* verdict) {
+  pdl_begin();
+  const int p = P.p, ntp = P.ntp, nw = P.nw;
+  const float2* __restrict__ st = staged;
+  const float2* __restrict__ gl = staged + p;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const long long nwt = (long long)p * nw * (goals ? 2 : 1);
+  constexpr int QUARTERS = TILE / EP_ROWS;
+  // the staged endpoints may sit in host memory: the reads of the extent
+  // and of the first agent-wall test are issued here, ahead of the tile
+  // tasks', so that their latencies overlap (the launch has at least p
+  // threads, so the extent needs one agent a thread)
+  const bool has_e = gid < p;
+  const float2 ea = has_e ? st[gid] : mk(0.f, 0.f), eb = has_e ? gl[gid] : mk(0.f, 0.f);
+  const bool has_w = gid < nwt;
+  const int wi = has_w ? (int)(gid % p) : 0;
+  const float2 wx = has_w ? (gid / p >= nw ? gl[wi] : st[wi]) : mk(0.f, 0.f);
+  unsigned long long best = ~0ull;
+  if (has_e) {  // the device copy the last block applies from
+    shadow[gid] = ea;
+    shadow[p + gid] = eb;
+    if (!(isfinite(ea.x) && isfinite(ea.y) && isfinite(eb.x) && isfinite(eb.y)))
+      best = endpoint_key(0, (unsigned)gid, 0);
+  }
+  const int tasks = ntp * (1 + goals) * QUARTERS;
+  for (int task = warp; task < tasks; task += nwarps) {
+    const int tq = task / QUARTERS, q = task - tq * QUARTERS;
+    const int which = tq / ntp;
+    const int2 IJ = P.tiles[tq - which * ntp];
+    const float2* X = which ? gl : st;
+    const int i0 = IJ.x * TILE + q * EP_ROWS, j = IJ.y * TILE + lane;
+    const bool rowok = lane < EP_ROWS && i0 + lane < p;
+    const float2 xi = rowok ? X[i0 + lane] : mk(0.f, 0.f);
+    const float ri = rowok ? P.radius[i0 + lane] : 0.f;
+    const float2 xj = j < p ? X[j] : mk(0.f, 0.f);
+    const float rj = j < p ? P.radius[j] : 0.f;
+#pragma unroll
+    for (int r = 0; r < EP_ROWS; ++r) {
+      const float xr = __shfl_sync(0xffffffffu, xi.x, r), yr = __shfl_sync(0xffffffffu, xi.y, r);
+      const float rr = __shfl_sync(0xffffffffu, ri, r);
+      const int i = i0 + r;
+      // FP32 screen: pairs farther apart than (1 + 1e-4)(r_i + r_j) cannot
+      // fail the FP64 test (FP32 rounding here is below 1e-6 relative)
+      const float fx = xj.x - xr, fy = xj.y - yr, fR = rr + rj;
+      if (i < j && j < p && fx * fx + fy * fy <= 1.0002f * fR * fR) {
+        const double dx = (double)xj.x - (double)xr, dy = (double)xj.y - (double)yr;
+        const double R = (double)rr + (double)rj;
+        if (dx * dx + dy * dy < R * R) best = min(best, endpoint_key(1 + which, i, j));
+      }
+    }
+  }
+  for (long long t = gid; t < nwt; t += nthreads) {
+    const int i = (int)(t % p);
+    const long long rw = t / p;
+    const int w = (int)(rw % nw), which = (int)(rw / nw);
+    const float2 x = t == gid ? wx : (which ? gl[i] : st[i]);
+    const float4 W = P.walls[w];
+    // FP32 screen: the distance to the segment computed in FP32 is within
+    // a few 1e-7 x L of the exact one (L the largest coordinate magnitude
+    // involved), so a disk clear of the wall by 1e-4 (1 + L) cannot fail
+    // the FP64 test
+    {
+      const float fdx = W.z - W.x, fdy = W.w - W.y, fpx = x.x - W.x, fpy = x.y - W.y;
+      const float fdd = fdx * fdx + fdy * fdy;
+      const float ft = fdd > 0.f ? fminf(1.f, fmaxf(0.f, (fpx * fdx + fpy * fdy) / fdd)) : 0.f;
+      const float fex = ft * fdx - fpx, fey = ft * fdy - fpy;
+      const float Lw = fmaxf(fmaxf(fmaxf(fabsf(W.x), fabsf(W.y)), fmaxf(fabsf(W.z), fabsf(W.w))), maxabs2(x));
+      const float rm = P.radius[i] + 1e-4f * (1.f + Lw);
+      if (fex * fex + fey * fey > rm * rm) continue;
+    }
+    const double ax = W.x, ay = W.y, dx = (double)W.z - W.x, dy = (double)W.w - W.y;
+    const double dd = dx * dx + dy * dy;
+    const double px = (double)x.x - ax, py = (double)x.y - ay;
+    const double t01 = dd > 0.0 ? fmin(1.0, fmax(0.0, (px * dx + py * dy) / dd)) : 0.0;
+    const double ex = t01 * dx - px, ey = t01 * dy - py;
+    const double r = P.radius[i];
+    if (ex * ex + ey * ey < r * r) best = min(best, endpoint_key(3 + which, i, w));
+  }
+  // the extent: every agent's start and goal once (also when goals are not
+  // checked); only the warps holding agents publish it
+  float ext = has_e ? fmaxf(maxabs2(ea), maxabs2(eb)) : 0.f;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+    best = w < best ? w : best;
+    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
+  }
+  if (lane == 0) {
+    if (best != ~0ull) atomicMin(key, best);
+    // a non-negative float orders like its bits
+    if (ext > 0.f && __float_as_uint(ext) > (unsigned)__ldcg(key + 1))
+      atomicMax(key + 1, (unsigned long long)__float_as_uint(ext));
+  }
+  // last block done: every block's shadow stores and atomics are ordered
+  // before its count
+  __shared__ int last;
+  if (has_e) __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(key + 2, 1ull) == (unsigned long long)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const unsigned long long k = __ldcg(key);
+  const float L0 = __uint_as_float((unsigned)__ldcg(key + 1));
+  __syncthreads();  // every thread has read the words before they are reset
+  if (threadIdx.x == 0) {  // first, so that the store to the host drains under the copy
+    *verdict = k;
+    key[0] = ~0ull;
+    key[1] = 0ull;
+    key[2] = 0ull;
     if (k == ~0ull) {
-      float L = sL;
-      for (int w = 0; w < P.nw; ++w) {
+      float L = L0;
+      for (int w = 0; w < nw; ++w) {
         const float4 W = P.walls[w];
         L = fmaxf(L, fmaxf(fmaxf(fabsf(W.x), fabsf(W.y)), fmaxf(fabsf(W.z), fabsf(W.w))));
       }
       set_fix(P, L);
     }
-    *verdict = k;
   }
-}
-
-// Feasibility of new fixed positions on the device (plan_set_endpoints), with
-// the strict test of the host check in FP64: two disks closer than
-// r_i + r_j, or a disk closer than r_i to a wall segment.  The first
-// violation in the order (start pairs, goal pairs, start-wall, goal-wall;
-// then i; then j or the wall) is kept as one 64-bit key (kind << 60 | i << 30
-// | j), ~0 when there is none.  Blocks below 'pair_blocks' take one 32 x 32
-// agent tile pair of the starts (and then of the goals); the rest the
-// agent-wall tests.
-__device__ __forceinline__ unsigned long long endpoint_key(unsigned kind, unsigned i, unsigned j) {
-  return ((unsigned long long)kind << 60) | ((unsigned long long)i << 30) | (unsigned long long)j;
-}
-
-__global__ void endpoint_check_kernel(int p, int ntp, const int2* tiles, const float2* st,
-                                      const float2* gl, const float* radius, int nw,
-                                      const float4* walls, int goals, int pair_blocks,
-                                      unsigned long long* key) {
-  __shared__ float2 xr[TILE], xc[TILE];
-  __shared__ float rr[TILE], rc[TILE];
-  unsigned long long best = ~0ull;
-  float ext = 0.f;  // largest coordinate magnitude seen (the new layout's extent)
-  if ((int)blockIdx.x < pair_blocks) {
-    const int which = (int)blockIdx.x / ntp, tp = (int)blockIdx.x - which * ntp;
-    const int2 IJ = tiles[tp];
-    const float2* X = which ? gl : st;
-    // the tile's row and column agents, one load round
-    if (threadIdx.x < 2 * TILE) {
-      const int c = threadIdx.x & 31, k = (threadIdx.x < TILE ? IJ.x : IJ.y) * TILE + c;
-      const float2 x = k < p ? X[k] : mk(0.f, 0.f);
-      const float r = k < p ? radius[k] : 0.f;
-      if (threadIdx.x < TILE) { xr[c] = x; rr[c] = r; } else { xc[c] = x; rc[c] = r; }
-      if (IJ.x == IJ.y || threadIdx.x >= TILE) ext = fmaxf(fabsf(x.x), fabsf(x.y));
-      if (!goals && threadIdx.x >= TILE && k < p)  // unchecked goals still set the extent
-        ext = fmaxf(ext, fmaxf(fabsf(gl[k].x), fabsf(gl[k].y)));
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < TILE * TILE; q += blockDim.x) {
-      const int r = q >> 5, c = q & 31;
-      const int i = IJ.x * TILE + r, j = IJ.y * TILE + c;
-      if (i >= j || j >= p) continue;
-      // FP32 screen: pairs farther apart than (1 + 1e-4)(r_i + r_j) cannot
-      // fail the FP64 test (FP32 rounding here is below 1e-6 relative)
-      const float fx = xc[c].x - xr[r].x, fy = xc[c].y - xr[r].y, fR = rr[r] + rc[c];
-      if (fx * fx + fy * fy > 1.0002f * fR * fR) continue;
-      const double dx = (double)xc[c].x - (double)xr[r].x, dy = (double)xc[c].y - (double)xr[r].y;
-      const double R = (double)rr[r] + (double)rc[c];
-      if (dx * dx + dy * dy < R * R) best = min(best, endpoint_key(which, i, j));
-    }
-  } else {
-    const long long n = (long long)p * nw * (goals ? 2 : 1);
-    const long long stride = (long long)(gridDim.x - pair_blocks) * blockDim.x;
-    for (long long t = (long long)(blockIdx.x - pair_blocks) * blockDim.x + threadIdx.x; t < n;
-         t += stride) {
-      const int i = (int)(t % p);
-      const long long rw = t / p;
-      const int w = (int)(rw % nw), which = (int)(rw / nw);
-      const float2 x = which ? gl[i] : st[i];
-      const float4 W = walls[w];
-      const double ax = W.x, ay = W.y, dx = (double)W.z - W.x, dy = (double)W.w - W.y;
-      const double dd = dx * dx + dy * dy;
-      const double px = (double)x.x - ax, py = (double)x.y - ay;
-      const double t01 = dd > 0.0 ? fmin(1.0, fmax(0.0, (px * dx + py * dy) / dd)) : 0.0;
-      const double ex = t01 * dx - px, ey = t01 * dy - py;
-      const double r = radius[i];
-      if (ex * ex + ey * ey < r * r) best = min(best, endpoint_key(2 + which, i, w));
+  if (k == ~0ull) {
+    const size_t E1 = (size_t)P.eta + 1;
+    float2* z0 = const_cast<float2*>(P.z);
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      const float2 a = __ldcg(shadow + i), b = __ldcg(shadow + p + i);
+      start[i] = a; goal[i] = b;
+      z0[i * E1] = a; P.z_next[i * E1] = a;
+      z0[i * E1 + P.eta] = b; P.z_next[i * E1 + P.eta] = b;
     }
   }
-  block_min_u64(best, key);
-  // the extent, reduced over the block first (a non-negative float orders
-  // like its bits), then one global update, and only if it raises the value:
-  // thousands of atomics on one word would serialise
-  __shared__ unsigned bext;
-  if (threadIdx.x == 0) bext = 0u;
-  __syncthreads();
-  for (int o = 16; o > 0; o >>= 1) ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
-  if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicMax(&bext, __float_as_uint(ext));
-  __syncthreads();
-  if (threadIdx.x == 0 && bext > (unsigned)*reinterpret_cast<volatile unsigned long long*>(key + 1))
-    atomicMax(key + 1, (unsigned long long)bext);
 }
 
 __device__ __forceinline__ size_t pair_index(int p, int i, int j) {
@@ -881,7 +930,7 @@ struct Layout {
   size_t z0, z1, start, goal, radius, cost, walls, vlim, wnode, tiles;
   size_t ulo, uhi, xlo, xhi, bits, ukin, xkin, uwall, xwall, wbits, work, wwork, wcount, sched,
       stamps, heavy, accx, accy, accc, fix,
-      res, status, count, ccost, chk, ekey;
+      res, status, count, ccost, chk, ekey, eshadow;
   size_t total;
 };
 
@@ -942,6 +991,9 @@ Layout layout_for(const plan_config* c) {
   L.ccost = take(p * eta * 8);  // FP64 kinetic coefficients for plan_check
   L.chk = take(4 * 8);          // plan_check results
   L.ekey = take(24);            // plan_set_endpoints: first violation, extent, fix-up blocks done
+  // a device copy of the endpoints of a device-checked update, made while
+  // they are checked
+  L.eshadow = take(p <= kDeviceEndpointCheck ? p * 16 : 0);
   L.total = o;
   return L;
 }
@@ -1590,6 +1642,8 @@ namespace {
 plan_status endpoint_graph(plan_t h) {
   if (h->gset) return PLAN_OK;
   const size_t p = h->p;
+  // the kernel reads the pinned staging area in place: for a few tens of
+  // KB a copy-engine transfer first costs more than the reads over the link
   float2* staged = nullptr;
   unsigned long long* verdict = nullptr;
   unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
@@ -1597,18 +1651,20 @@ plan_status endpoint_graph(plan_t h) {
   CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&verdict), hk, 0));
   unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
   const int goals = h->vo ? 0 : 1;
-  const int pair_blocks = (int)h->ntp * (1 + goals);
-  const long long nwall = (long long)p * h->nw * (1 + goals);
-  const int wall_blocks = h->nw ? (int)std::min<long long>((nwall + 255) / 256, 1024) : 0;
+  // one warp per 8 rows of a tile pair (8 warps a block), at most 1,024
+  // blocks; enough threads for one agent-wall test or one agent's extent each
+  // up to that
+  const long long tasks = (long long)h->ntp * (1 + goals) * (TILE / EP_ROWS);
+  const long long nwall = std::max<long long>((long long)p * h->nw * (1 + goals), (long long)p);
+  const int blocks = (int)std::min<long long>(std::max<long long>((tasks + 7) / 8, (nwall + 255) / 256), 1024);
   if (!h->ep_event) CK(cudaEventCreateWithFlags(&h->ep_event, cudaEventDisableTiming));
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  endpoint_check_kernel<<<pair_blocks + wall_blocks, 256, 0, h->cap>>>(
-      h->p, (int)h->ntp, h->at<int2>(h->L.tiles), staged, staged + p, h->at<float>(h->L.radius),
-      h->nw, h->at<float4>(h->L.walls), goals, pair_blocks, key);
-  endpoints_fix_kernel<<<(unsigned)((p + 255) / 256), 256, 0, h->cap>>>(
-      h->dev(h->k), h->at<float2>(h->L.start), h->at<float2>(h->L.goal), staged, key, verdict);
+  cudaError_t ce = launch_pdl(endpoint_update_kernel, (unsigned)blocks, 256u, h->cap, h->dev(h->k), (const float2*)staged,
+                    goals, h->at<float2>(h->L.start), h->at<float2>(h->L.goal),
+                    h->at<float2>(h->L.eshadow), key, verdict);
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (e == cudaSuccess) e = ce;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gset, g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -1652,11 +1708,12 @@ plan_status settle_endpoints(plan_t h) {
   }
   const unsigned kind = (unsigned)(k >> 60), i = (unsigned)((k >> 30) & 0x3fffffffu),
                  j = (unsigned)(k & 0x3fffffffu);
-  if (kind < 2)
+  if (kind == 0) return fail(PLAN_EINVAL, "non-finite input (the start or goal of agent %u)", i);
+  if (kind < 3)
     return fail(PLAN_EINFEASIBLE_INPUT, "%s positions of agents %u and %u overlap",
-                kind ? "goal" : "start", i, j);
+                kind == 2 ? "goal" : "start", i, j);
   return fail(PLAN_EINFEASIBLE_INPUT, "%s of agent %u is within its radius of wall %u",
-              kind == 3 ? "goal" : "start", i, j);
+              kind == 4 ? "goal" : "start", i, j);
 }
 
 }  // namespace
@@ -1666,11 +1723,12 @@ extern "C" {
 plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) {
   if (!h || !start || !goal) return fail(PLAN_EINVAL, "null argument");
   const size_t p = h->p;
-  if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
   plan_status st = settle_endpoints(h);  // an earlier asynchronous update's verdict
   if (st != PLAN_OK) return st;
   if (!h->h_stage || p > kDeviceEndpointCheck) {
-    // the host grid check, then the copies
+    // the host grid check, then the copies (the device check rejects
+    // non-finite coordinates itself)
+    if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
     st = check_endpoints(h->p, start, goal, h->h_radius.data(), h->nw, h->h_walls.data(), !h->vo,
                          &h->grid);
     if (st != PLAN_OK) return st;
@@ -1678,8 +1736,7 @@ plan_status plan_set_endpoints(plan_t h, const float* start, const float* goal) 
     float2* d_goal = h->at<float2>(h->L.goal);
     CK(cudaMemcpyAsync(d_start, start, p * 8, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(d_goal, goal, p * 8, cudaMemcpyHostToDevice, h->stream));
-    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal, nullptr, nullptr,
-                                                   nullptr);
+    endpoints_fix_kernel<<<1, 256, 0, h->stream>>>(h->dev(h->k), d_start, d_goal);
     CK(cudaGetLastError());
     // the caller's host buffers may be reused once this returns
     CK(cudaStreamSynchronize(h->stream));
@@ -1700,7 +1757,6 @@ plan_status plan_set_endpoints_async(plan_t h, const float* start, const float* 
   if (!h->h_stage || p > kDeviceEndpointCheck)
     return fail(PLAN_EUNSUPPORTED, "asynchronous endpoint updates need the device check (p <= %zu)",
                 kDeviceEndpointCheck);
-  if (!finite_all(start, 2 * p) || !finite_all(goal, 2 * p)) return fail(PLAN_EINVAL, "non-finite input");
   // the previous update must have consumed the staging buffer, and its
   // verdict is read before this one can overwrite it
   plan_status st = settle_endpoints(h);

@@ -281,3 +281,91 @@ def test_asynchronous_endpoint_updates_report_at_the_next_synchronising_call():
         pl.set_endpoints(inst.start, g2, wait=False)
         assert pl.iterate(1, residual=True) >= 0.0
         assert np.array_equal(pl.trajectory_host()[:, -1], g2.astype(np.float32))
+
+
+def test_device_endpoint_check_at_large_p():
+    """p = 4100 (129 agent tiles, the last holding four agents): every warp of
+    the check takes several tile-pair tasks, and the update is applied by
+    whichever block finishes last.  Violations planted in the last tile pair,
+    in the goals only, among both starts and goals, and against a wall, are
+    each reported as the brute-force enumeration's first; a feasible update
+    is applied."""
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(4100, 2, seed=23)
+    p = inst.p
+    assert _first_violation(inst.start, inst.goal, inst.radius, inst.walls) is None
+    with pk.Planner.from_instance(inst) as pl:
+        pl.iterate(2)
+        z0 = pl.trajectory_host()
+        cases = []
+        gl = inst.goal.copy()
+        gl[p - 1] = gl[p - 2] + 0.5 * (inst.radius[p - 2] + inst.radius[p - 1]) * np.array([0.0, 1.0])
+        cases.append((inst.start.copy(), gl))
+        st = inst.start.copy()
+        st[p - 1] = st[3] + 0.5 * (inst.radius[3] + inst.radius[p - 1]) * np.array([1.0, 0.0])
+        cases.append((st, gl))
+        gl2 = inst.goal.copy()
+        gl2[p - 1] = [inst.walls[:, [0, 2]].max() - 0.5 * inst.radius[p - 1], gl2[p - 1][1]]
+        cases.append((inst.start.copy(), gl2))
+        for st, g in cases:
+            expect = _first_violation(st, g, inst.radius, inst.walls)
+            assert expect is not None
+            with pytest.raises(pk.PlanError) as e:
+                pl.set_endpoints(st, g)
+            assert e.value.status == "PLAN_EINFEASIBLE_INPUT" and expect in str(e.value), (expect, str(e.value))
+            assert np.array_equal(pl.trajectory_host(), z0)
+        g3 = inst.goal.copy()
+        g3[:, 1] += 1e-3
+        if _first_violation(inst.start, g3, inst.radius, inst.walls) is None:
+            pl.set_endpoints(inst.start, g3)
+            z = pl.trajectory_host()
+            assert np.array_equal(z[:, -1], g3.astype(np.float32))
+            assert np.array_equal(z[:, 0], inst.start.astype(np.float32))
+
+
+def test_trajectory_to_pinned_and_pageable_host_memory():
+    """plan_get_trajectory into page-locked host memory (16-byte aligned and
+    misaligned destinations, nothing written outside them) and into pageable
+    memory gives the device trajectory bit for bit."""
+    import torch
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(72, 6, seed=11)
+    with pk.Planner.from_instance(inst) as pl:
+        pl.iterate(7)
+        ref = pl.trajectory().cpu().numpy()
+        n = ref.size
+        pinned = torch.zeros(n + 8, dtype=torch.float32).pin_memory()
+        for off in (0, 1, 3):
+            pinned.fill_(-1.0)
+            view = pinned.numpy()[off:off + n].reshape(ref.shape)
+            pl.trajectory_host(view)
+            assert np.array_equal(view, ref), off
+            assert np.all(pinned.numpy()[:off] == -1.0) and np.all(pinned.numpy()[off + n:] == -1.0)
+        pageable = np.full(ref.shape, -1.0, dtype=np.float32)
+        pl.trajectory_host(pageable)
+        assert np.array_equal(pageable, ref)
+
+
+def test_non_finite_endpoints_are_refused():
+    """A NaN or infinite coordinate in the new starts or goals is refused with
+    PLAN_EINVAL (by the device check: waiting, or at the next synchronising
+    call), naming the first such agent, and the plan keeps its endpoints."""
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(72, 6, seed=11)
+    with pk.Planner.from_instance(inst) as pl:
+        pl.iterate(3)
+        z0 = pl.trajectory_host()
+        for bad_val, which, agent in ((np.nan, 0, 40), (np.inf, 1, 5), (-np.inf, 0, 71)):
+            st, gl = inst.start.copy(), inst.goal.copy()
+            (st if which == 0 else gl)[agent, 1] = bad_val
+            # an overlap further on must not hide it
+            gl[70] = gl[69]
+            with pytest.raises(pk.PlanError) as e:
+                pl.set_endpoints(st, gl)
+            assert e.value.status == "PLAN_EINVAL" and f"agent {agent}" in str(e.value), str(e.value)
+            assert np.array_equal(pl.trajectory_host(), z0)
+            pl.set_endpoints(st, gl, wait=False)
+            with pytest.raises(pk.PlanError) as e:
+                pl.trajectory_host()
+            assert e.value.status == "PLAN_EINVAL" and f"agent {agent}" in str(e.value), str(e.value)
+            assert np.array_equal(pl.trajectory_host(), z0)
