@@ -990,7 +990,7 @@ Layout layout_for(const plan_config* c) {
   L.count = take(16);
   L.ccost = take(p * eta * 8);  // FP64 kinetic coefficients for plan_check
   L.chk = take(4 * 8);          // plan_check results
-  L.ekey = take(24);            // plan_set_endpoints: first violation, extent, fix-up blocks done
+  L.ekey = take(24);            // plan_set_endpoints: first violation, extent, finished blocks
   // a device copy of the endpoints of a device-checked update, made while
   // they are checked
   L.eshadow = take(p <= kDeviceEndpointCheck ? p * 16 : 0);
