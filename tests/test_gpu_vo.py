@@ -85,3 +85,37 @@ def test_vo_circle_swap_reaches_the_destinations():
             break
     pl.close()
     assert md < 1e-3, md
+
+
+def test_endpoint_update_of_the_local_planner_checks_starts_only():
+    """plan_set_endpoints on a PLAN_VO plan (checked on the device): the goals
+    are reference points and may overlap, so only starts are tested; an
+    overlap among the starts is refused and leaves the plan unchanged; a goal
+    far outside the old layout is applied and the iteration stays finite
+    (the new extent sets the fixed-point scale)."""
+    import paper_1311_4527_gb300 as pk
+    x0 = np.array([[-0.5, 0.01], [0.5, -0.01], [0.0, 0.6]])
+    r = np.array([0.2, 0.2, 0.15])
+    prob = vo.problem(x0, vo.targets(x0, np.array([[2.0, 0.0], [-2.0, 0.0], [0.0, -2.0]]), 0.8), r,
+                      np.array([1.0, 1.001, 1.002]), rho0=RHO)
+    with _vo_planner(prob) as pl:
+        pl.iterate(5)
+        z0 = pl.trajectory_host()
+        goal = prob.goal.copy()
+        goal[1] = goal[0]                       # overlapping reference points: allowed
+        pl.set_endpoints(prob.start, goal)
+        z = pl.trajectory_host()
+        assert np.array_equal(z[:, -1], goal.astype(np.float32))
+        bad = prob.start.copy()
+        bad[2] = bad[0] + np.array([0.1, 0.0])  # starts 0 and 2 overlap
+        with pytest.raises(pk.PlanError) as e:
+            pl.set_endpoints(bad, goal)
+        assert e.value.status == "PLAN_EINFEASIBLE_INPUT" and "start positions of agents 0 and 2" in str(e.value)
+        assert np.array_equal(pl.trajectory_host(), z)
+        far = goal.copy()
+        far[2] = [0.0, -500.0]
+        pl.set_endpoints(prob.start, far)
+        pl.iterate(20)
+        zf = pl.trajectory_host()
+        assert np.all(np.isfinite(zf)) and np.array_equal(zf[:, -1], far.astype(np.float32))
+        assert not np.array_equal(z0, zf)
