@@ -369,3 +369,38 @@ def test_non_finite_endpoints_are_refused():
                 pl.trajectory_host()
             assert e.value.status == "PLAN_EINVAL" and f"agent {agent}" in str(e.value), str(e.value)
             assert np.array_equal(pl.trajectory_host(), z0)
+
+
+def test_endpoint_update_above_the_device_check_size():
+    """p = 8200 (more than the 8192 agents the device check takes): the host
+    grid check refuses an overlap and a position within a wall's reach, and
+    leaves the plan unchanged; feasible endpoints are copied and applied by
+    the single-block update kernel (fixed break-points of both z buffers,
+    the fixed-point scale), after which iterations stay finite; the
+    asynchronous form is refused."""
+    import paper_1311_4527_gb300 as pk
+    inst = workloads.small_square(8200, 1, seed=29)
+    p = inst.p
+    with pk.Planner.from_instance(inst) as pl:
+        z0 = pl.trajectory_host()
+        st = inst.start.copy()
+        st[p - 1] = st[p - 2] + 0.5 * (inst.radius[p - 2] + inst.radius[p - 1]) * np.array([1.0, 0.0])
+        with pytest.raises(pk.PlanError) as e:
+            pl.set_endpoints(st, inst.goal)
+        assert e.value.status == "PLAN_EINFEASIBLE_INPUT" and "overlap" in str(e.value)
+        gl = inst.goal.copy()
+        gl[5] = [0.5 * inst.radius[5], gl[5][1]]  # within the x = 0 wall's reach
+        with pytest.raises(pk.PlanError) as e:
+            pl.set_endpoints(inst.start, gl)
+        assert e.value.status == "PLAN_EINFEASIBLE_INPUT" and "wall" in str(e.value)
+        assert np.array_equal(pl.trajectory_host(), z0)
+        with pytest.raises(pk.PlanError) as e:
+            pl.set_endpoints(inst.start, inst.goal, wait=False)
+        assert e.value.status == "PLAN_EUNSUPPORTED"
+        # starts and goals exchanged: both configurations were feasible
+        pl.set_endpoints(inst.goal, inst.start)
+        pl.iterate(3)
+        z = pl.trajectory_host()
+        assert np.all(np.isfinite(z))
+        assert np.array_equal(z[:, 0], inst.goal.astype(np.float32))
+        assert np.array_equal(z[:, -1], inst.start.astype(np.float32))
