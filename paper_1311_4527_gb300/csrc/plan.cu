@@ -119,18 +119,28 @@ __global__ void __launch_bounds__(256) prox_kernel(Dev P) {
   const unsigned long long wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31;
   unsigned long long v, Wc;  // this warp's place among the collision warps, their number
+  // The wall items of this warp: first, first + stride, ... below nwl.  Both
+  // dealings go through this one call of the wall minimizer: with two call
+  // sites the compiler inlined two copies whose floating-point contractions
+  // differed, so the result of a wall factor depended on whether the active
+  // walls outnumbered the CTAs (that is, on the GPU's SM count).
+  unsigned long long first, stride;
+  bool wall_only;
   if (nwl <= G) {
-    if (b < nwl && wib == 0) {
-      wall_prox_item_warp(P, P.wwork[b]);
-      return;
-    }
+    wall_only = b < nwl && wib == 0;
+    first = wall_only ? b : nwl;
+    stride = G;
     Wc = G * wpb - nwl;
     v = wib == 0 ? b - nwl : (G - nwl) + (wib - 1) * G + b;
   } else {
-    for (unsigned long long t = b * wpb + wib; t < nwl; t += G * wpb) wall_prox_item_warp(P, P.wwork[t]);
+    wall_only = false;
+    first = b * wpb + wib;
+    stride = G * wpb;
     Wc = G * wpb;
     v = wib * G + b;
   }
+  for (unsigned long long t = first; t < nwl; t += stride) wall_prox_item_warp(P, P.wwork[t]);
+  if (wall_only) return;
   for (unsigned long long t = 32ull * v + lane; t < nc; t += 32ull * Wc) prox_item(P, P.work[t]);
 }
 

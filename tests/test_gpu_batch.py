@@ -108,3 +108,4 @@ def test_batch_members_match_the_oracle_from_an_imported_iterate():
         gpu = dict(got[b], wback=new.wback)
         stats = par.compare(probs[b], new, info, gpu)
         assert stats["coll_active"] > 0 and stats["coll_compared_active"] > 0, (b, stats)
+

@@ -166,3 +166,16 @@ def test_interior_wall_segments_parity():
     prob = _prob(inst, cost_unnorm=True)
     stats = _run(prob, [0, 3, 30, 150])
     assert sum(s.get("wall_active", 0) for s in stats) > 0, stats
+
+
+def test_more_active_walls_than_minimizer_ctas_parity():
+    """An obstacle course (p = 300, eta = 8, the four sides and 60 interior
+    walls) with about 1,600 active wall factors: more than the minimizer pass
+    has CTAs, so it deals the walls over all its warps before the collision
+    groups.  Parity at the oracle's iterates 0 and 3."""
+    inst = workloads.obstacle_square(300, 8, 25.0, 60, 3)
+    prob = _prob(inst)
+    stats = _run(prob, [0, 3])
+    for s in stats:
+        assert s.get("wall_active", 0) > 1000, s
+        assert s["coll_excluded"] <= 0.02 * s["coll_active"], s
