@@ -81,18 +81,23 @@ __global__ void __launch_bounds__(32 * ROWS_WARPS, 40 / ROWS_WARPS) test_rows_ke
   // the listed ones
   const int t = ((int)blockIdx.x - nseg) * ROWS_WARPS + warp;
   int blk;
+  bool check_stamp = false;
   if (t < P.hcap) {
-    if (t >= (int)*P.hcount_cur) return;  // warp-uniform
-    blk = (int)P.heavy_cur[t];
+    // the list's length and this warp's entry are loaded together (t < hcap
+    // keeps the entry in bounds; it is used only below the length)
+    const unsigned hc = ld_now(P.hcount_cur);
+    const unsigned hb = ld_now(P.heavy_cur + t);
+    if (t >= (int)hc) return;  // warp-uniform
+    blk = (int)hb;
   } else {
     const int tr = t - P.hcap;
     if (tr >= P.eta * P.ntp) return;  // warp-uniform
     const int s = tr % P.eta;
     if (P.vo && s != 0) return;  // no collision factors on the second segment
     blk = s * P.ntp + tr / P.eta;
-    if (P.hcap && P.stamp_cur[blk] == *P.iter) return;  // taken by a heavy warp
+    check_stamp = P.hcap != 0;  // skipped there if a heavy warp takes it
   }
-  test_tile_rows(P, blk, col[warp], nws[warp]);
+  test_tile_rows(P, blk, col[warp], nws[warp], check_stamp);
 }
 
 // Worklist items are dealt to warps round-robin (item t to warp t mod W,

@@ -158,6 +158,27 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned* slot, float v) {
   atomicMax(slot, __float_as_uint(v));
 }
 
+// Global loads issued where they stand.  A volatile asm is never moved into
+// a later branch, so loads placed ahead of an early exit are in flight
+// together with the loads after it: one memory round trip instead of two on
+// a warp's dependent chain.  For data that no other thread of the launch
+// writes (and that the loading thread writes, if at all, only afterwards).
+__device__ __forceinline__ float2 ld_now(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_now(const float* p) {
+  float v;
+  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_now(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
@@ -513,7 +534,10 @@ __device__ __forceinline__ float bounding_offset(float2 m, float b) {
 // filter plus pairs active before) is listed heavy for the next iteration.
 constexpr unsigned HEAVY_TESTS = 160;
 
-__device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col, uint32_t* nws) {
+// check_stamp: the tile is skipped when the heavy-tile stamps show that a
+// heavy warp takes it in this iteration.
+__device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* col, uint32_t* nws,
+                                               bool check_stamp = false) {
   const int lane = threadIdx.x & 31;
   const int E1 = P.eta + 1;
   float res = 0.f;
@@ -521,14 +545,29 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   int I, J;
   tile_of(P.nt, blk - s * P.ntp, I, J);
   const bool pin_lo = (s == 0), pin_hi = (s == P.eta - 1);
-  // column agents: (midpoint, bounding radius, bounding_offset), (z lo, z hi)
-  // and r_j (col holds 72 float4: the last 8 are the 32 radii)
-  float* rcol = reinterpret_cast<float*>(col + 64);
+  // Every load the tile starts from is issued here, before any is used: the
+  // column agent and the row agent of this lane, the row's activity word,
+  // the iteration number and the tile's stamp.
   const int j = J * TILE + lane;
   const bool vj = j < P.p;
   float2 zjl = mk(0.f, 0.f), zjh = zjl;
   float rj = 0.f;
-  if (vj) { zjl = P.z[(size_t)j * E1 + s]; zjh = P.z[(size_t)j * E1 + s + 1]; rj = P.radius[j]; }
+  if (vj) { zjl = ld_now(P.z + (size_t)j * E1 + s); zjh = ld_now(P.z + (size_t)j * E1 + s + 1); rj = ld_now(P.radius + j); }
+  const int i = I * TILE + lane;
+  const bool vi = i < P.p;
+  const size_t row = (size_t)blk * TILE + lane;
+  float2 zil = mk(0.f, 0.f), zih = zil;
+  float ri = 0.f;
+  uint32_t word = 0u;
+  if (vi) {
+    zil = ld_now(P.z + (size_t)i * E1 + s); zih = ld_now(P.z + (size_t)i * E1 + s + 1); ri = ld_now(P.radius + i);
+    word = ld_now(P.bits + row);
+  }
+  const unsigned it = P.hcap ? ld_now(P.iter) : 0u;
+  if (check_stamp && ld_now(P.stamp_cur + blk) == it) return;  // warp-uniform: taken by a heavy warp
+  // column agents: (midpoint, bounding radius, bounding_offset), (z lo, z hi)
+  // and r_j (col holds 72 float4: the last 8 are the 32 radii)
+  float* rcol = reinterpret_cast<float*>(col + 64);
   {
     const float2 m = 0.5f * (zjl + zjh);
     const float b = 0.5f * sqrtf(dot(zjh - zjl, zjh - zjl)) + rj;
@@ -538,17 +577,6 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
   }
   const uint32_t vmask = __ballot_sync(FULL, vj);
   __syncwarp();
-  // the row agent of this lane
-  const int i = I * TILE + lane;
-  const bool vi = i < P.p;
-  const size_t row = (size_t)blk * TILE + lane;
-  float2 zil = mk(0.f, 0.f), zih = zil;
-  float ri = 0.f;
-  uint32_t word = 0u;
-  if (vi) {
-    zil = P.z[(size_t)i * E1 + s]; zih = P.z[(size_t)i * E1 + s + 1]; ri = P.radius[i];
-    word = P.bits[row];
-  }
   uint32_t valid = vi ? vmask : 0u;
   if (I == J) valid &= (lane == 31) ? 0u : (~0u << (lane + 1));  // pairs i < j
   uint32_t nword = 0u;
@@ -629,6 +657,13 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
     }
   }
   if (vi && nword != word) P.bits[row] = nword;
+  // a heavy tile goes first in the next iteration: its slot is claimed here,
+  // so that this atomic and the worklist's below are in flight together
+  unsigned hk = ~0u;
+  if (P.hcap) {
+    const unsigned total = __reduce_add_sync(FULL, work);
+    if (lane == 0 && total >= HEAVY_TESTS) hk = atomicAdd(P.hcount_next, 1u);
+  }
   // worklist: warp prefix sum of the rows' active counts, one atomic per warp
   if (__any_sync(FULL, nword != 0u)) {
     const unsigned cnt = __popc(nword);
@@ -648,15 +683,9 @@ __device__ __forceinline__ void test_tile_rows(const Dev& P, int blk, float4* co
     res = warp_max(res);
     if (lane == 0 && P.res_prev) atomic_max_nonneg(P.res_prev, res);
   }
-  if (P.hcap) {  // a heavy tile goes first in the next iteration
-    const unsigned total = __reduce_add_sync(FULL, work);
-    if (lane == 0 && total >= HEAVY_TESTS) {
-      const unsigned k = atomicAdd(P.hcount_next, 1u);
-      if (k < (unsigned)P.hcap) {
-        P.heavy_next[k] = (uint32_t)blk;
-        P.stamp_next[blk] = *P.iter + 1u;
-      }
-    }
+  if (hk < (unsigned)P.hcap) {  // lane 0 of a heavy tile with a free slot
+    P.heavy_next[hk] = (uint32_t)blk;
+    P.stamp_next[blk] = it + 1u;
   }
 }
 
