@@ -457,7 +457,7 @@ __global__ void endpoints_fix_kernel(Dev P, const float2* start, const float2* g
   fix_block(P, start, goal);
 }
 
-// A device-checked endpoint update (plan_set_endpoints), one launch.
+// A device-checked endpoint update (plan_set_endpoints), two launches.
 // Feasibility of the new fixed positions uses the strict test of the host
 // check in FP64: two disks closer than r_i + r_j, or a disk closer than r_i
 // to a wall segment; a non-finite coordinate fails it before anything else.
@@ -465,31 +465,65 @@ __global__ void endpoints_fix_kernel(Dev P, const float2* start, const float2* g
 // pairs, start-wall, goal-wall; then i; then j or the wall) is kept in key[0]
 // as kind << 60 | i << 30 | j (~0 when there is none), and the largest
 // coordinate magnitude of the new starts and goals (the layout's extent, for
-// the fixed-point scale) in key[1].  One warp takes 8 rows of one 32 x 32
-// agent tile pair of the starts (then of the goals) at a time: lane c holds
-// column agent c and the row agents come by shuffles; then every thread takes
-// agent-wall tests, grid-stride.  Each agent's new start and goal are also
-// copied to a device shadow on the way.  The last block to finish (counted in
-// key[2]) writes the verdict (key[0]) to the host's word, resets the three
-// key words for the next update and, if key[0] is clear, applies the update
-// from the shadow: the new endpoints, the fixed break-points of both z
-// buffers and the fixed-point scale.
+// the fixed-point scale) in key[1].
+// endpoint_stage_kernel, one thread per agent: reads the agent's new start
+// and goal from the staging area once (it may sit in pinned host memory, so
+// the whole update crosses the link in one coalesced pass), copies them to a
+// device shadow and takes the non-finite test and the extent.
+// endpoint_update_kernel, launched behind it with programmatic serialization
+// (its griddepcontrol.wait makes the shadow visible): one warp takes 8 rows
+// of one 32 x 32 agent tile pair of the starts (then of the goals) at a time
+// from the shadow, lane c holding column agent c and the row agents coming by
+// shuffles; then every thread takes agent-wall tests, grid-stride.  The last
+// block to finish (counted in key[2]) writes the verdict (key[0]) to the
+// host's word, resets the three key words for the next update and, if key[0]
+// is clear, applies the update from the shadow: the new endpoints, the fixed
+// break-points of both z buffers and the fixed-point scale.
 __device__ __forceinline__ unsigned long long endpoint_key(unsigned kind, unsigned i, unsigned j) {
   return ((unsigned long long)kind << 60) | ((unsigned long long)i << 30) | (unsigned long long)j;
 }
 
 constexpr int EP_ROWS = 8;  // rows of a tile pair per warp task
 
-__global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float2* __restrict__ staged,
+__global__ void __launch_bounds__(256) endpoint_stage_kernel(Dev P, const float2* __restrict__ staged,
+                                                             float2* __restrict__ shadow,
+                                                             unsigned long long* key) {
+  pdl_begin();
+  const int p = P.p;
+  const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const bool has_e = gid < p;
+  const float2 ea = has_e ? staged[gid] : mk(0.f, 0.f), eb = has_e ? staged[p + gid] : mk(0.f, 0.f);
+  unsigned long long best = ~0ull;
+  float ext = 0.f;
+  if (has_e) {
+    shadow[gid] = ea;
+    shadow[p + gid] = eb;
+    if (!(isfinite(ea.x) && isfinite(ea.y) && isfinite(eb.x) && isfinite(eb.y)))
+      best = endpoint_key(0, (unsigned)gid, 0);
+    ext = fmaxf(maxabs2(ea), maxabs2(eb));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+    best = w < best ? w : best;
+    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (best != ~0ull) atomicMin(key, best);
+    // a non-negative float orders like its bits
+    if (ext > 0.f && __float_as_uint(ext) > (unsigned)__ldcg(key + 1))
+      atomicMax(key + 1, (unsigned long long)__float_as_uint(ext));
+  }
+}
+
+__global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float2* __restrict__ shadow,
                                                               int goals, float2* __restrict__ start,
                                                               float2* __restrict__ goal,
-                                                              float2* __restrict__ shadow,
                                                               unsigned long long* key,
                                                               unsigned long long* verdict) {
   pdl_begin();
   const int p = P.p, ntp = P.ntp, nw = P.nw;
-  const float2* __restrict__ st = staged;
-  const float2* __restrict__ gl = staged + p;
+  const float2* __restrict__ st = shadow;
+  const float2* __restrict__ gl = shadow + p;
   const int lane = threadIdx.x & 31;
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -497,22 +531,7 @@ __global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   const long long nwt = (long long)p * nw * (goals ? 2 : 1);
   constexpr int QUARTERS = TILE / EP_ROWS;
-  // the staged endpoints may sit in host memory: the reads of the extent
-  // and of the first agent-wall test are issued here, ahead of the tile
-  // tasks', so that their latencies overlap (the launch has at least p
-  // threads, so the extent needs one agent a thread)
-  const bool has_e = gid < p;
-  const float2 ea = has_e ? st[gid] : mk(0.f, 0.f), eb = has_e ? gl[gid] : mk(0.f, 0.f);
-  const bool has_w = gid < nwt;
-  const int wi = has_w ? (int)(gid % p) : 0;
-  const float2 wx = has_w ? (gid / p >= nw ? gl[wi] : st[wi]) : mk(0.f, 0.f);
   unsigned long long best = ~0ull;
-  if (has_e) {  // the device copy the last block applies from
-    shadow[gid] = ea;
-    shadow[p + gid] = eb;
-    if (!(isfinite(ea.x) && isfinite(ea.y) && isfinite(eb.x) && isfinite(eb.y)))
-      best = endpoint_key(0, (unsigned)gid, 0);
-  }
   const int tasks = ntp * (1 + goals) * QUARTERS;
   for (int task = warp; task < tasks; task += nwarps) {
     const int tq = task / QUARTERS, q = task - tq * QUARTERS;
@@ -544,7 +563,7 @@ __global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float
     const int i = (int)(t % p);
     const long long rw = t / p;
     const int w = (int)(rw % nw), which = (int)(rw / nw);
-    const float2 x = t == gid ? wx : (which ? gl[i] : st[i]);
+    const float2 x = which ? gl[i] : st[i];
     const float4 W = P.walls[w];
     // FP32 screen: the distance to the segment computed in FP32 is within
     // a few 1e-7 x L of the exact one (L the largest coordinate magnitude
@@ -567,24 +586,13 @@ __global__ void __launch_bounds__(256) endpoint_update_kernel(Dev P, const float
     const double r = P.radius[i];
     if (ex * ex + ey * ey < r * r) best = min(best, endpoint_key(3 + which, i, w));
   }
-  // the extent: every agent's start and goal once (also when goals are not
-  // checked); only the warps holding agents publish it
-  float ext = has_e ? fmaxf(maxabs2(ea), maxabs2(eb)) : 0.f;
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
     best = w < best ? w : best;
-    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
   }
-  if (lane == 0) {
-    if (best != ~0ull) atomicMin(key, best);
-    // a non-negative float orders like its bits
-    if (ext > 0.f && __float_as_uint(ext) > (unsigned)__ldcg(key + 1))
-      atomicMax(key + 1, (unsigned long long)__float_as_uint(ext));
-  }
-  // last block done: every block's shadow stores and atomics are ordered
-  // before its count
+  if (lane == 0 && best != ~0ull) atomicMin(key, best);
+  // last block done: every block's atomics are ordered before its count
   __shared__ int last;
-  if (has_e) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1657,8 +1665,9 @@ namespace {
 plan_status endpoint_graph(plan_t h) {
   if (h->gset) return PLAN_OK;
   const size_t p = h->p;
-  // the kernel reads the pinned staging area in place: for a few tens of
-  // KB a copy-engine transfer first costs more than the reads over the link
+  // the stage kernel reads the pinned staging area in place, once per
+  // agent: for a few tens of KB a copy-engine transfer first costs more than
+  // one coalesced pass over the link
   float2* staged = nullptr;
   unsigned long long* verdict = nullptr;
   unsigned long long* hk = reinterpret_cast<unsigned long long*>(h->h_res + 2);
@@ -1667,17 +1676,19 @@ plan_status endpoint_graph(plan_t h) {
   unsigned long long* key = h->at<unsigned long long>(h->L.ekey);
   const int goals = h->vo ? 0 : 1;
   // one warp per 8 rows of a tile pair (8 warps a block), at most 1,024
-  // blocks; enough threads for one agent-wall test or one agent's extent each
-  // up to that
+  // blocks; enough threads for one agent-wall test each up to that
   const long long tasks = (long long)h->ntp * (1 + goals) * (TILE / EP_ROWS);
-  const long long nwall = std::max<long long>((long long)p * h->nw * (1 + goals), (long long)p);
+  const long long nwall = (long long)p * h->nw * (1 + goals);
   const int blocks = (int)std::min<long long>(std::max<long long>((tasks + 7) / 8, (nwall + 255) / 256), 1024);
   if (!h->ep_event) CK(cudaEventCreateWithFlags(&h->ep_event, cudaEventDisableTiming));
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = launch_pdl(endpoint_update_kernel, (unsigned)blocks, 256u, h->cap, h->dev(h->k), (const float2*)staged,
-                    goals, h->at<float2>(h->L.start), h->at<float2>(h->L.goal),
-                    h->at<float2>(h->L.eshadow), key, verdict);
+  float2* shadow = h->at<float2>(h->L.eshadow);
+  cudaError_t ce = launch_pdl(endpoint_stage_kernel, (unsigned)((p + 255) / 256), 256u, h->cap, h->dev(h->k),
+                              (const float2*)staged, shadow, key);
+  if (ce == cudaSuccess)
+    ce = launch_pdl(endpoint_update_kernel, (unsigned)blocks, 256u, h->cap, h->dev(h->k), (const float2*)shadow,
+                    goals, h->at<float2>(h->L.start), h->at<float2>(h->L.goal), key, verdict);
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (e == cudaSuccess) e = ce;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gset, g, 0);
