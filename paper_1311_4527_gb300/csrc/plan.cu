@@ -1168,6 +1168,7 @@ struct plan_s {
   cudaEvent_t pend = nullptr;
   cudaGraphExec_t gexec[4] = {};  // captured iterations by (k parity, z buffer)
   cudaGraphExec_t gexec8[4] = {}; // ... and runs of ITERS_PER_GRAPH iterations
+  cudaGraphExec_t gexec64[4] = {}; // ... and of ITERS_PER_LONG_GRAPH iterations
   double ptime[4] = {0, 0, 0, 0};
   int pcount = 0;
   unsigned* h_res;  // pinned host words: residual readback (0), endpoint check key (2..3)
@@ -1367,22 +1368,23 @@ plan_status run_iteration(plan_t h) {
   return PLAN_OK;
 }
 
-// Runs of ITERS_PER_GRAPH iterations replayed from one graph (an even count,
-// so the run ends at the parity and z buffer it started from): fewer launches
-// for problems small enough that launching is the cost.
+// Runs of ITERS_PER_LONG_GRAPH, then ITERS_PER_GRAPH iterations replayed
+// from one graph each (even counts, so a run ends at the parity and z buffer
+// it started from): fewer launches for problems small enough that launching
+// is the cost, and fewer graph boundaries, where the programmatic-launch
+// chain of the kernels starts over, in long runs.
 constexpr int ITERS_PER_GRAPH = 8;
+constexpr int ITERS_PER_LONG_GRAPH = 64;
 
-plan_status run_iterations(plan_t h, int n) {
-  plan_status st = ensure_prox_grid(h);
-  if (st != PLAN_OK) return st;
-  while (n >= ITERS_PER_GRAPH && h->cap && !h->profiling && h->k >= h->graph_from()) {
+plan_status run_graph_runs(plan_t h, int& n, int len, cudaGraphExec_t* execs) {
+  while (n >= len && h->cap && !h->profiling && h->k >= h->graph_from()) {
     const int key = ((h->k & 1) << 1) | h->cur;
-    if (!h->gexec8[key]) {
+    if (!execs[key]) {
       const int k0 = h->k, c0 = h->cur;
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
       plan_status cst = PLAN_OK;
-      for (int q = 0; q < ITERS_PER_GRAPH && cst == PLAN_OK; ++q) {
+      for (int q = 0; q < len && cst == PLAN_OK; ++q) {
         cst = enqueue_iteration(h, h->cap);
         if (h->eta > 1) h->cur ^= 1;
         h->k += 1;
@@ -1392,14 +1394,22 @@ plan_status run_iterations(plan_t h, int n) {
       cudaError_t e = cudaStreamEndCapture(h->cap, &g);
       if (cst != PLAN_OK) { if (g) cudaGraphDestroy(g); return cst; }
       if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&h->gexec8[key], g, 0);
+      e = cudaGraphInstantiate(&execs[key], g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return fail(PLAN_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
-    CK(cudaGraphLaunch(h->gexec8[key], h->stream));
-    h->k += ITERS_PER_GRAPH;
-    n -= ITERS_PER_GRAPH;
+    CK(cudaGraphLaunch(execs[key], h->stream));
+    h->k += len;
+    n -= len;
   }
+  return PLAN_OK;
+}
+
+plan_status run_iterations(plan_t h, int n) {
+  plan_status st = ensure_prox_grid(h);
+  if (st != PLAN_OK) return st;
+  if ((st = run_graph_runs(h, n, ITERS_PER_LONG_GRAPH, h->gexec64)) != PLAN_OK) return st;
+  if ((st = run_graph_runs(h, n, ITERS_PER_GRAPH, h->gexec8)) != PLAN_OK) return st;
   for (; n > 0; --n)
     if ((st = run_iteration(h)) != PLAN_OK) return st;
   return PLAN_OK;
@@ -1643,6 +1653,8 @@ void plan_destroy(plan_t h) {
     if (h->gexec[q]) cudaGraphExecDestroy(h->gexec[q]);
   for (int q = 0; q < 4; ++q)
     if (h->gexec8[q]) cudaGraphExecDestroy(h->gexec8[q]);
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec64[q]) cudaGraphExecDestroy(h->gexec64[q]);
   if (h->pend) cudaEventDestroy(h->pend);
   if (h->gset) cudaGraphExecDestroy(h->gset);
   if (h->ep_event) cudaEventDestroy(h->ep_event);
@@ -2322,6 +2334,8 @@ plan_status plan_set_energy(plan_t h, int on) {
     if (h->gexec[q]) { cudaGraphExecDestroy(h->gexec[q]); h->gexec[q] = nullptr; }
   for (int q = 0; q < 4; ++q)
     if (h->gexec8[q]) { cudaGraphExecDestroy(h->gexec8[q]); h->gexec8[q] = nullptr; }
+  for (int q = 0; q < 4; ++q)
+    if (h->gexec64[q]) { cudaGraphExecDestroy(h->gexec64[q]); h->gexec64[q] = nullptr; }
   h->noenergy = off;
   Dev P = h->dev(h->k);
   if (off) {
